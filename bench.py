@@ -1,0 +1,372 @@
+"""Benchmark of the multi-RHS Dirac mat-vec on GB300.
+
+Default workload (one step = one sweep): Wilson D_W, 32^4 periodic lattice,
+Nc = 3, Nv = 12, FP32, kappa = 0.125, links exp(0.3 i H), Gaussian source,
+internal site-fastest layout, inputs resident in HBM.  Each step reads and
+writes 2.7 GB, far more than the 129 MB L2, so no flush is needed between
+steps.  The JSON line reports model Gflop/s (1368 flop per site and
+right-hand side), the HBM roofline of the kernel, the end-to-end rate through
+the C ABI with host buffers, the FP64 CPU oracle timed on a bounded sample,
+and the clocks seen during the timed region.  Extra lines in "extra" time the
+staggered and Brillouin sweeps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-extra]
+
+With N > 1 (torchrun, one rank per GPU) every rank runs its own replica of
+the workload (the sweeps do not shard without a halo exchange); the value is
+the sum over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "Dirac-apply Gflop/s & HBM GB/s (Nc=3,Nv=12); mixed-vs-FP32 solve time @1e-10"
+WORKLOAD = {"op": "wilson", "L": (32, 32, 32, 32), "Nv": 12, "mass": 0.125, "prec": "f32",
+            "links": "near_identity", "eps": 0.3, "seed_links": 1002, "seed_source": 2002}
+PAPER_CONTEXT = {"wilson_sp_knl_gflops": 345, "staggered_sp_knl_gflops": 475,
+                 "brillouin_sp_knl_gflops": 790, "note": "one 68-core KNL node, Nc=3, Nv=12 (abstract)"}
+KERNEL_SOURCES = ["paper_1808_05506_gb300/csrc/dirac_kernels.cuh",
+                  "paper_1808_05506_gb300/csrc/dirac_common.cuh",
+                  "paper_1808_05506_gb300/csrc/apply_wilson.cu"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "wilson_apply_traffic.json")
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def gen_inputs(w):
+    L, Nv = w["L"], w["Nv"]
+    ns = 1 if w["op"] == "staggered" else 4
+    V = synth.gauge_links(L, 3, w["links"], w["seed_links"], eps=w.get("eps", 0.3))
+    psi = synth.spinor(L, Nv, ns, 3, w["seed_source"], dtype=np.complex64)
+    return V.astype(np.complex64), psi
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                out, _ = self.p.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_id_for_smi(torch) -> str:
+    try:
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        return vis.split(",")[torch.cuda.current_device()] if vis else str(torch.cuda.current_device())
+
+
+def time_kernel(torch, fn, steps, warmup):
+    """Per-launch CUDA-event timing on the current stream; returns (total_ms, [per-launch ms])."""
+    st = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(st)
+    for a, b in ev:
+        a.record(st)
+        fn()
+        b.record(st)
+    t1.record(st)
+    t1.synchronize()
+    return t0.elapsed_time(t1), [a.elapsed_time(b) for a, b in ev]
+
+
+def sweep_rate(dg, torch, w, steps, warmup):
+    """Time one sweep workload on the internal layout; returns a dict of rates."""
+    V, psi = gen_inputs(w)
+    D = dg.Dirac(w["op"], w["L"], w["Nv"], w["mass"], w["prec"])
+    D.set_links(torch.from_numpy(V).cuda())
+    x = D.pack(torch.from_numpy(psi).cuda())
+    y = D.new_internal()
+    total, per = time_kernel(torch, lambda: D.apply(x, out=y), steps, warmup)
+    vol = int(np.prod(w["L"]))
+    t = statistics.mean(per) * 1e-3
+    flops = dg.flops_per_site_rhs(w["op"]) * vol * w["Nv"]
+    byts = dg.bytes_per_site(w["op"], w["Nv"], w["prec"]) * vol
+    cfg = D.kernel_config()
+    D.close()
+    return {"gflops": flops / t / 1e9, "gbs": byts / t / 1e9, "ms": t * 1e3, "R": cfg[0], "block": cfg[1]}
+
+
+class OracleSample:
+    """The FP64 oracle (as it stands) on a bounded random sample of output sites."""
+
+    def __init__(self, w, inputs=None):
+        import oracle
+        self.oracle = oracle
+        V, psi = inputs if inputs is not None else gen_inputs(w)
+        self.V = np.ascontiguousarray(V, dtype=np.complex128)
+        self.psi = np.ascontiguousarray(psi, dtype=np.complex128)
+        self.w = w
+        self.m0 = oracle.kappa_to_m0(w["mass"]) if w["op"] == "wilson" else w["mass"]
+        self.vol = int(np.prod(w["L"]))
+        self.rng = np.random.default_rng(0)
+        self.cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+    def run(self, n):
+        sites = self.rng.integers(0, self.vol, n)
+        t = time.perf_counter()
+        self.oracle.apply(self.w["op"], self.V, self.psi, self.m0, sites=sites)
+        return time.perf_counter() - t
+
+    def calibrate(self, seconds):
+        n = 64
+        while True:
+            dt = self.run(n)
+            if dt > seconds / 2 or n >= self.vol:
+                break
+            n = min(self.vol, int(n * min(16.0, max(2.0, seconds / max(dt, 1e-4)))))
+        return max(1, min(self.vol, int(n * seconds / max(dt, 1e-6))))
+
+    def rate(self, n, dt):
+        from paper_1808_05506_gb300 import flops_per_site_rhs   # flop model only; no library load
+        return flops_per_site_rhs(self.w["op"]) * n * self.w["Nv"] / dt / 1e9
+
+    def describe(self, n, dt):
+        return (f"{n} random output sites of the {self.w['op']} {'x'.join(map(str, self.w['L']))} "
+                f"Nv={self.w['Nv']} workload (FP64 gather oracle, OpenMP), {dt:.2f} s")
+
+
+def cpu_oracle_rate(w, inputs=None, seconds=15.0):
+    s = OracleSample(w, inputs)
+    n = s.calibrate(seconds)
+    dt = s.run(n)
+    return {"value": s.rate(n, dt), "unit": "Gflop/s", "cores": s.cores, "kind": "oracle",
+            "sample": s.describe(n, dt)}
+
+
+def dist_init(torch):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return rank, ws, dist
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as the reference arm (host cores, bounded sample per step)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = WORKLOAD
+    s = OracleSample(w)
+    per_step = max(0.05, min(5.0, 150.0 / (args.steps + args.warmup)))
+    n = s.calibrate(per_step)
+    for _ in range(args.warmup):
+        s.run(n)
+    dts = [s.run(n) for _ in range(args.steps)]
+    dt = statistics.mean(dts)
+    v = s.rate(n, dt)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gflop/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "wilson_apply_32x32x32x32_nv12_f32", "lattice": list(w["L"]), "Nc": 3,
+                       "Nv": w["Nv"], "kappa": w["mass"]},
+            "cpu_baseline": {"value": v, "unit": "Gflop/s", "cores": s.cores, "kind": "oracle",
+                             "sample": s.describe(n, dt) + " per step"},
+            "e2e": {"value": v, "unit": "Gflop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    args.warmup = max(3, args.warmup)
+
+    import torch
+    rank, ws, dist = dist_init(torch)
+    if ws == 1:
+        torch.cuda.set_device(0)
+    import paper_1808_05506_gb300 as dg
+
+    w = WORKLOAD
+    V, psi = gen_inputs(w)
+    D = dg.Dirac(w["op"], w["L"], w["Nv"], w["mass"], w["prec"])
+    D.set_links(torch.from_numpy(V).cuda())
+    xin = torch.from_numpy(psi).cuda()
+    x = D.pack(xin)
+    y = D.new_internal()
+    vol = int(np.prod(w["L"]))
+    flops_step = dg.flops_per_site_rhs("wilson") * vol * w["Nv"]
+    bytes_step = dg.bytes_per_site("wilson", w["Nv"], w["prec"]) * vol
+
+    step = lambda: D.apply(x, out=y)   # noqa: E731  one launch of the sweep kernel
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_id_for_smi(torch)) as clk:
+        total_ms, per = time_kernel(torch, step, args.steps, 0)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = total_ms / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = flops_step * ws / (ms * 1e-3) / 1e9
+    kern_ms = statistics.mean(per)
+    hbm_peak, peak_kind = peaks()
+    achieved = bytes_step / (kern_ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers: H2D of the canonical source,
+    # dirac_apply on canonical device buffers (pack, sweep, unpack), D2H of the result
+    host_in = torch.from_numpy(psi).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    dev_in = torch.empty_like(host_in, device="cuda")
+    dev_out = torch.empty_like(host_in, device="cuda")
+
+    def e2e_step():
+        dev_in.copy_(host_in, non_blocking=True)
+        D.apply(dev_in, out=dev_out)
+        host_out.copy_(dev_out, non_blocking=True)
+
+    e2e_steps = max(3, min(50, args.steps // 20))
+    e2e_total, _ = time_kernel(torch, e2e_step, e2e_steps, 2)
+    e2e_ms = e2e_total / e2e_steps
+    h2d = host_in.numel() * host_in.element_size()
+
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        tf = json.load(open(TRAFFIC_FILE))
+        if tf.get("kernel_hash") == kernel_hash() and tf.get("workload") == "wilson_apply_32x32x32x32_nv12_f32":
+            traffic = tf.get("dram_bytes_per_launch")
+    cfg = D.kernel_config()
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gflop/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "wilson_apply_32x32x32x32_nv12_f32", "op": "wilson", "lattice": list(w["L"]),
+                   "Nc": 3, "Nv": w["Nv"], "kappa": w["mass"], "links": "exp(0.3 i H), H traceless Gaussian",
+                   "source": "complex Gaussian N(0,1)", "layout": "internal site-fastest SoA",
+                   "l2": "no flush: each step streams 2.7 GB > 129 MB L2",
+                   "kernel": {"rhs_per_thread": cfg[0], "block": cfg[1]},
+                   "parallelism": f"replicas x{ws}"},
+        "hbm_gbs": achieved,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": traffic,
+                     "peak_kind": f"{peak_kind} copy bandwidth", "kernel": "k_wilson<float,R,false>",
+                     "algorithmic_bytes_per_launch": bytes_step},
+        "clocks": clk.summary(),
+        "e2e": {"value": flops_step / (e2e_ms * 1e-3) / 1e9, "unit": "Gflop/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+                "path": "pinned host -> device, dirac_apply(canonical), device -> pinned host"},
+        "gpu_launches": args.steps,
+        "paper_context": PAPER_CONTEXT,
+    }
+    D.close()
+    del x, y, xin, dev_in, dev_out
+    torch.cuda.empty_cache()
+    if not args.no_extra:
+        extra = {}
+        sw = dict(WORKLOAD, op="staggered", mass=0.0)
+        extra["staggered_32x32x32x32_nv12_f32"] = sweep_rate(dg, torch, sw, 200, 5)
+        bw = dict(WORKLOAD, op="brillouin", L=(24, 24, 24, 48), mass=0.05, seed_links=1003, seed_source=2003)
+        extra["brillouin_24x24x24x48_nv12_f32"] = sweep_rate(dg, torch, bw, 20, 3)
+        extra["brillouin_24x24x24x48_nv12_bf16"] = sweep_rate(dg, torch, dict(bw, prec="bf16"), 20, 3)
+        extra["wilson_32x32x32x32_nv12_bf16"] = sweep_rate(dg, torch, dict(WORKLOAD, prec="bf16"), 200, 5)
+        line["extra"] = extra
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_rate(w, inputs=(V, psi))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+/*
+ * dirac.h -- C ABI of the GB300 multi-right-hand-side Dirac mat-vec library
+ * (libdirac_gb300.so).
+ *
+ * The library computes out = D in for Nv right-hand sides at once, for the
+ * three discretisations of S. Duerr, "Three Dirac operators on two
+ * architectures with one piece of code and no hassle" (arXiv:1808.05506):
+ *   DIRAC_STAGGERED  D_S, Sec. 3 (one-hop stencil with smeared links V_mu and
+ *                    phases eta_mu), plus a mass term m
+ *   DIRAC_WILSON     D_W, Sec. 4, Eq. def_wils at c_SW = 0
+ *   DIRAC_BRILLOUIN  D_B, Sec. 5, Eqs. def_bril, def_der, def_lap at c_SW = 0,
+ *                    with the off-axis links W_dir of Tab. tab:off-axis
+ * Only Nc = 3 is built.  The clover term (c_SW != 0) is not offered.
+ *
+ * Conventions (fixed readings where the paper is silent):
+ *   - site index s = x + Nx (y + Ny (z + Nz t)), coordinates 0-based,
+ *     mu = 0..3 <-> x, y, z, t; periodic boundaries in all directions.
+ *   - eta_0 = 1, eta_1 = (-1)^x, eta_2 = (-1)^(x+y), eta_3 = (-1)^(x+y+z).
+ *   - V_mu(x) is the transporter from x+mu to x; V_{-mu}(x) = V_mu(x-mu)^+.
+ *   - Euclidean chiral gamma basis: gamma_k = [[0, -i sigma_k], [i sigma_k, 0]],
+ *     gamma_4 = [[0, 1], [1, 0]], gamma_5 = diag(1, 1, -1, -1).
+ *   - lattice spacing a = 1.
+ *
+ * Canonical layouts (C order, complex numbers as interleaved re, im):
+ *   links   V[s][mu][a][b]                     (the transpose of the paper's
+ *                                               Fortran U(Nc,Nc,4,...) matrix order)
+ *   spinor  Wilson / Brillouin [s][v][spin][colour]  == the paper's vec(Nc,4,Nv,...)
+ *           staggered          [s][v][colour]        == the paper's suv(Nc,Nv,...)
+ *   Canonical spinors are complex double for DIRAC_F64 handles and complex
+ *   float for every other precision.
+ * Internal layout (site-fastest structure of arrays, in the storage
+ * precision; allocate with dirac_field_bytes, convert with dirac_pack /
+ * dirac_unpack):
+ *   spinor  [v][k][s] with k over 16-byte elements of one right-hand side
+ *           (Wilson/Brillouin: 12 complex per site split into elements of
+ *           2 complex (F32), 1 (F64) or 4 (BF16/F16); staggered: 3 elements
+ *           of one complex each).
+ *
+ * Pointers: unless a function says otherwise, spinor and field pointers are
+ * DEVICE pointers owned by the caller; the library never frees them.  Work is
+ * enqueued on the handle's CUDA stream and is asynchronous with respect to
+ * the host unless stated.  One handle must not be used from two host threads
+ * at once.
+ *
+ * Errors: every function returns a dirac_status; none aborts, throws or traps.
+ * After an error, dirac_last_error(h) gives a one-line description.
+ */
+#ifndef DIRAC_GB300_H
+#define DIRAC_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define DIRAC_API __attribute__((visibility("default")))
+#else
+#define DIRAC_API
+#endif
+
+typedef enum {
+    DIRAC_OK = 0,
+    DIRAC_ERR_INVALID_ARG = 1,   /* bad pointer, size, aliasing, or call order */
+    DIRAC_ERR_UNSUPPORTED = 2,   /* valid request this build does not offer (e.g. Nc != 3) */
+    DIRAC_ERR_OOM = 3,           /* device allocation failed */
+    DIRAC_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    DIRAC_NOT_CONVERGED = 5,     /* solver hit its iteration limit */
+    DIRAC_BREAKDOWN = 6,         /* solver met a zero/NaN/Inf scalar */
+    DIRAC_TIMEOUT = 7            /* a bounded device-side wait ran out */
+} dirac_status;
+
+typedef enum { DIRAC_STAGGERED = 0, DIRAC_WILSON = 1, DIRAC_BRILLOUIN = 2 } dirac_op;
+
+/* storage precision of links and internal spinors (arithmetic is FP64 for
+ * DIRAC_F64 and FP32 otherwise) */
+typedef enum { DIRAC_F64 = 0, DIRAC_F32 = 1, DIRAC_BF16 = 2, DIRAC_F16 = 3 } dirac_prec;
+
+typedef enum { DIRAC_CANONICAL = 0, DIRAC_INTERNAL = 1 } dirac_layout;
+
+typedef struct dirac_handle dirac_handle;
+
+/* Library version string (static storage). */
+DIRAC_API const char* dirac_version(void);
+
+/* Human-readable name of a status code (static storage). */
+DIRAC_API const char* dirac_status_string(dirac_status st);
+
+/* Create a handle for one operator on one lattice.
+ *   op            DIRAC_STAGGERED / DIRAC_WILSON / DIRAC_BRILLOUIN
+ *   Nc            number of colours; only 3 is supported (else UNSUPPORTED)
+ *   Nx..Nt        lattice extents, each >= 2 (else INVALID_ARG); odd extents
+ *                 are accepted (the staggered phases are then not
+ *                 translation invariant across the boundary)
+ *   Nv            right-hand sides per sweep, >= 1
+ *   mass          staggered: m;  Wilson: the hopping parameter kappa > 0
+ *                 (m0 = 1/(2 kappa) - 4, Sec. 4 def_wils);  Brillouin: m0
+ *   prec          storage precision
+ *   stream        cudaStream_t to enqueue on (NULL = the legacy default stream)
+ * The handle is bound to the CUDA device current at creation.  It owns its
+ * link storage and workspaces.  Returns INVALID_ARG for a NULL h. */
+DIRAC_API dirac_status dirac_create(dirac_handle** h, dirac_op op, int Nc, int Nx, int Ny, int Nz,
+                          int Nt, int Nv, double mass, dirac_prec prec, void* stream);
+
+/* Release a handle and everything it owns (NULL is a no-op). */
+DIRAC_API dirac_status dirac_destroy(dirac_handle* h);
+
+/* Change the mass parameter (same meaning as in dirac_create). */
+DIRAC_API dirac_status dirac_set_mass(dirac_handle* h, double mass);
+
+/* Change the stream the handle enqueues on. */
+DIRAC_API dirac_status dirac_set_stream(dirac_handle* h, void* stream);
+
+/* Load the gauge links V_mu(x) (Sec. 2 array U, Sec. 3 smeared links).
+ *   V          canonical links [s][mu][a][b], complex, Nx Ny Nz Nt * 4 * 9 entries
+ *   V_prec     DIRAC_F64 (complex double) or DIRAC_F32 (complex float)
+ *   on_device  1: V is a device pointer; 0: a host pointer (copied)
+ * Converts to the internal layout in the storage precision and, for
+ * Brillouin, builds the 40 stored off-axis links W_dir of Tab. tab:off-axis
+ * (the average over the k! hop orderings, computed in FP64 by the recursion
+ * W_dir(x) = (1/k) sum_{hops a} V_a(x) W_{dir-a}(x+a), then rounded).
+ * Synchronous: returns after the links are in place.  The caller keeps
+ * ownership of V. */
+DIRAC_API dirac_status dirac_set_links(dirac_handle* h, const void* V, dirac_prec V_prec, int on_device);
+
+/* Bytes of one spinor field with the handle's Nv right-hand sides. */
+DIRAC_API dirac_status dirac_field_bytes(const dirac_handle* h, dirac_layout layout, size_t* bytes);
+
+/* Convert a canonical spinor field (complex double for F64 handles, complex
+ * float otherwise) into the internal layout and storage precision, and back.
+ * Device pointers; out must not alias in. */
+DIRAC_API dirac_status dirac_pack(dirac_handle* h, void* internal_out, const void* canonical_in);
+DIRAC_API dirac_status dirac_unpack(dirac_handle* h, void* canonical_out, const void* internal_in);
+
+/* out = D in for all Nv right-hand sides (Sec. 3 / def_wils / def_bril).
+ * layout DIRAC_CANONICAL: in/out canonical (packed to the internal layout in
+ * a handle-owned workspace, applied, unpacked); DIRAC_INTERNAL: in/out in the
+ * internal layout and storage precision.  Device pointers, out != in.
+ * Requires dirac_set_links first (else INVALID_ARG).  Asynchronous. */
+DIRAC_API dirac_status dirac_apply(dirac_handle* h, void* out, const void* in, dirac_layout layout);
+
+/* out = D^+ in.  Staggered: D_S^+ = m - (hopping part of D_S) (the hopping
+ * part is anti-hermitian, Sec. 3); Wilson, Brillouin: D^+ = gamma5 D gamma5.
+ * Same contract as dirac_apply. */
+DIRAC_API dirac_status dirac_apply_dagger(dirac_handle* h, void* out, const void* in, dirac_layout layout);
+
+/* Kernel configuration: R = right-hand sides per thread (1..4 for Wilson and
+ * Brillouin, 1, 2, 4 or 6 for staggered), block = threads per block (a
+ * multiple of 32, 32..256).  UNSUPPORTED for other values. */
+DIRAC_API dirac_status dirac_set_kernel_config(dirac_handle* h, int R, int block);
+DIRAC_API dirac_status dirac_get_kernel_config(const dirac_handle* h, int* R, int* block);
+
+/* One-line description of the last error on h (or of the last failed
+ * dirac_create when h is NULL).  Static or handle-owned storage. */
+DIRAC_API const char* dirac_last_error(const dirac_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIRAC_GB300_H */

@@ -1,0 +1,248 @@
+"""GB300 multi-right-hand-side Dirac mat-vec (arXiv:1808.05506): Python binding.
+
+A thin ctypes layer over the C ABI of libdirac_gb300.so (include/dirac.h).
+The functions dirac_* carry the same names and arguments as the C entry
+points (plain integers and pointers); the Dirac class marshals torch tensors
+(device memory, the current CUDA stream) onto them.  Every step of the
+computation runs in the library's CUDA kernels; there is no CPU fallback, and
+loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdirac_gb300.so")
+
+STAGGERED, WILSON, BRILLOUIN = 0, 1, 2
+OPS = {"staggered": STAGGERED, "wilson": WILSON, "brillouin": BRILLOUIN}
+F64, F32, BF16, F16 = 0, 1, 2, 3
+PRECS = {"f64": F64, "f32": F32, "bf16": BF16, "f16": F16}
+CANONICAL, INTERNAL = 0, 1
+
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA = 0, 1, 2, 3, 4
+NOT_CONVERGED, BREAKDOWN, TIMEOUT = 5, 6, 7
+
+_lib = None
+
+
+class DiracError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    """Load libdirac_gb300.so (built by __graft_entry__.build() or build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
+                              "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB_PATH)
+        _declare(L)
+        _lib = L
+    return _lib
+
+
+P = ctypes.c_void_p
+I = ctypes.c_int
+D = ctypes.c_double
+
+# name -> (restype, argtypes); the C signatures of include/dirac.h
+SIGNATURES = {
+    "dirac_version": (ctypes.c_char_p, []),
+    "dirac_status_string": (ctypes.c_char_p, [I]),
+    "dirac_create": (I, [ctypes.POINTER(P), I, I, I, I, I, I, I, D, I, P]),
+    "dirac_destroy": (I, [P]),
+    "dirac_set_mass": (I, [P, D]),
+    "dirac_set_stream": (I, [P, P]),
+    "dirac_set_links": (I, [P, P, I, I]),
+    "dirac_field_bytes": (I, [P, I, ctypes.POINTER(ctypes.c_size_t)]),
+    "dirac_pack": (I, [P, P, P]),
+    "dirac_unpack": (I, [P, P, P]),
+    "dirac_apply": (I, [P, P, P, I]),
+    "dirac_apply_dagger": (I, [P, P, P, I]),
+    "dirac_set_kernel_config": (I, [P, I, I]),
+    "dirac_get_kernel_config": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+    "dirac_last_error": (ctypes.c_char_p, [P]),
+}
+
+
+def _declare(L):
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def _fwd(name):
+    def f(*args):
+        return getattr(lib(), name)(*args)
+    f.__name__ = name
+    f.__doc__ = f"ctypes call of the C entry point {name} (include/dirac.h)."
+    return f
+
+
+for _n in SIGNATURES:
+    globals()[_n] = _fwd(_n)
+
+
+def last_error(h) -> str:
+    s = lib().dirac_last_error(h)
+    return s.decode() if s else ""
+
+
+def check(status: int, h=None, what: str = "") -> None:
+    if status != OK:
+        raise DiracError(status, f"{what}: {last_error(h)}")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Dirac:
+    """One operator on one lattice, bound to a handle of the C library.
+
+    op: "staggered" | "wilson" | "brillouin"; L = (Nx, Ny, Nz, Nt);
+    mass: staggered m, Wilson kappa, Brillouin m0; prec: "f64" | "f32" | "bf16" | "f16".
+    Canonical spinor tensors have shape (Nt, Nz, Ny, Nx, Nv, 4, 3) (staggered:
+    (Nt, Nz, Ny, Nx, Nv, 3)) and dtype complex128 for f64, complex64 otherwise.
+    """
+
+    def __init__(self, op: str, L, Nv: int, mass: float, prec: str = "f32", Nc: int = 3,
+                 stream=None):
+        torch = _torch()
+        self.op, self.L, self.Nv, self.mass, self.prec = op, tuple(int(v) for v in L), int(Nv), float(mass), prec
+        self.Nc = Nc
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._stream = stream
+        h = P()
+        st = lib().dirac_create(ctypes.byref(h), OPS[op], Nc, *self.L, self.Nv, float(mass),
+                                PRECS[prec], _stream_ptr(stream))
+        check(st, None, "dirac_create")
+        self.h = h
+        self.canon_dtype = torch.complex128 if prec == "f64" else torch.complex64
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dirac_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- shapes ---------------------------------------------------------------
+    @property
+    def spin_shape(self):
+        return (self.Nv, 3) if self.op == "staggered" else (self.Nv, 4, 3)
+
+    @property
+    def canonical_shape(self):
+        Nx, Ny, Nz, Nt = self.L
+        return (Nt, Nz, Ny, Nx) + self.spin_shape
+
+    def field_bytes(self, layout=INTERNAL) -> int:
+        n = ctypes.c_size_t()
+        check(lib().dirac_field_bytes(self.h, layout, ctypes.byref(n)), self.h, "dirac_field_bytes")
+        return n.value
+
+    def new_internal(self):
+        torch = _torch()
+        return torch.empty(self.field_bytes(INTERNAL), dtype=torch.uint8, device=self.device)
+
+    def new_canonical(self):
+        torch = _torch()
+        return torch.empty(self.canonical_shape, dtype=self.canon_dtype, device=self.device)
+
+    def _sync_stream(self):
+        check(lib().dirac_set_stream(self.h, _stream_ptr(self._stream)), self.h, "dirac_set_stream")
+
+    # -- calls ------------------------------------------------------------------
+    def set_links(self, V):
+        """V: canonical links (Nt, Nz, Ny, Nx, 4, 3, 3), complex128/complex64, host or device."""
+        torch = _torch()
+        V = V.contiguous()
+        prec = F64 if V.dtype == torch.complex128 else F32
+        if V.dtype not in (torch.complex128, torch.complex64):
+            raise TypeError("links must be complex128 or complex64")
+        self._sync_stream()
+        check(lib().dirac_set_links(self.h, _ptr(V), prec, 1 if V.is_cuda else 0), self.h, "dirac_set_links")
+
+    def set_mass(self, mass: float):
+        check(lib().dirac_set_mass(self.h, float(mass)), self.h, "dirac_set_mass")
+        self.mass = float(mass)
+
+    def pack(self, canonical, out=None):
+        out = self.new_internal() if out is None else out
+        self._sync_stream()
+        check(lib().dirac_pack(self.h, _ptr(out), _ptr(canonical.contiguous())), self.h, "dirac_pack")
+        return out
+
+    def unpack(self, internal, out=None):
+        out = self.new_canonical() if out is None else out
+        self._sync_stream()
+        check(lib().dirac_unpack(self.h, _ptr(out), _ptr(internal)), self.h, "dirac_unpack")
+        return out
+
+    def apply(self, x, out=None, dagger: bool = False, layout=None):
+        """out = D x (or D^+ x).  x canonical (complex tensor) or internal (uint8 buffer)."""
+        if layout is None:
+            layout = INTERNAL if x.dtype == _torch().uint8 else CANONICAL
+        if out is None:
+            out = self.new_internal() if layout == INTERNAL else self.new_canonical()
+        self._sync_stream()
+        fn = lib().dirac_apply_dagger if dagger else lib().dirac_apply
+        check(fn(self.h, _ptr(out), _ptr(x.contiguous() if layout == CANONICAL else x), layout),
+              self.h, "dirac_apply_dagger" if dagger else "dirac_apply")
+        return out
+
+    def apply_dagger(self, x, out=None, layout=None):
+        return self.apply(x, out=out, dagger=True, layout=layout)
+
+    def set_kernel_config(self, R: int, block: int):
+        check(lib().dirac_set_kernel_config(self.h, R, block), self.h, "dirac_set_kernel_config")
+
+    def kernel_config(self):
+        R, B = I(), I()
+        check(lib().dirac_get_kernel_config(self.h, ctypes.byref(R), ctypes.byref(B)), self.h,
+              "dirac_get_kernel_config")
+        return R.value, B.value
+
+
+# per-site, per-right-hand-side model flop counts at Nc = 3 (complex mult-add = 8,
+# add = 2, real x complex = 2): staggered 64 Nc^2 - 2 Nc, Wilson 128 Nc^2 + 72 Nc,
+# Brillouin 80 * 4 (8 Nc^2 - 2 Nc) + 8 Nc sum_dir (1 + |dir|_1) + 984
+def flops_per_site_rhs(op: str, Nc: int = 3) -> int:
+    if op == "staggered":
+        return 64 * Nc * Nc - 2 * Nc
+    if op == "wilson":
+        return 128 * Nc * Nc + 72 * Nc
+    if op == "brillouin":
+        hops = sum(1 + k for k, n in ((1, 8), (2, 24), (3, 32), (4, 16)) for _ in range(n))
+        return 80 * 4 * (8 * Nc * Nc - 2 * Nc) + 8 * Nc * hops + 984
+    raise ValueError(op)
+
+
+def bytes_per_site(op: str, Nv: int, prec: str, Nc: int = 3) -> int:
+    """Algorithmic HBM bytes per site of one sweep: links once, in and out once."""
+    c = {"f64": 16, "f32": 8, "bf16": 4, "f16": 4}[prec]
+    nlink = {"staggered": 4, "wilson": 4, "brillouin": 40}[op]
+    ns = 1 if op == "staggered" else 4
+    return nlink * Nc * Nc * c + 2 * ns * Nc * Nv * c

@@ -1,0 +1,54 @@
+// Staggered D_S and D_S^+ sweeps (Sec. 3, plus a mass term) on the
+// internal site-fastest layout.  One thread owns one site and R right-hand
+// sides: every link is loaded once per thread and applied to its R spinors
+// from registers, and every output element is written once.  Consecutive
+// blocks cover the right-hand-side groups of the same sites, so the other
+// groups find the links in L2.
+#include "dirac_internal.h"
+
+namespace dirac {
+
+template <typename T, int R, bool DAG>
+__global__ void __launch_bounds__(256) k_staggered(ApplyArgs a, int ngroups)
+{
+    const long b = blockIdx.x;
+    const int group = (int)(b % ngroups);
+    const long s = (b / ngroups) * blockDim.x + threadIdx.x;
+    if (s >= a.g.vol) return;
+    staggered_site<T, R, DAG>(a, s, group);
+}
+
+template <typename T, int R>
+static cudaError_t go(bool dag, const ApplyArgs& a, int block, cudaStream_t st)
+{
+    const int ngroups = (a.Nv + R - 1) / R;
+    const long nblk = ((a.g.vol + block - 1) / block) * (long)ngroups;
+    if (dag) k_staggered<T, R, true><<<(unsigned)nblk, block, 0, st>>>(a, ngroups);
+    else k_staggered<T, R, false><<<(unsigned)nblk, block, 0, st>>>(a, ngroups);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t go_T(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
+{
+    switch (c.R) {
+    case 1: return go<T, 1>(dag, a, c.block, st);
+    case 2: return go<T, 2>(dag, a, c.block, st);
+    case 6: return go<T, 6>(dag, a, c.block, st);
+    case 4: return go<T, 4>(dag, a, c.block, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_apply_staggered(int prec, bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
+{
+    switch (prec) {
+    case P_F64: return go_T<double>(dag, a, c, st);
+    case P_F32: return go_T<float>(dag, a, c, st);
+    case P_BF16: return go_T<__nv_bfloat16>(dag, a, c, st);
+    case P_F16: return go_T<__half>(dag, a, c, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace dirac

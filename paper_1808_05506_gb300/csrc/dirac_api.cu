@@ -1,0 +1,451 @@
+// C ABI of the library (include/dirac.h): handle management, argument
+// validation and the dispatch onto the kernels.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/dirac.h"
+#include "dirac_handle.h"
+
+using namespace dirac;
+
+static thread_local std::string g_create_error;
+
+const char* dirac_version(void) { return "dirac_gb300 1.0 (sm_103a)"; }
+
+const char* dirac_status_string(dirac_status st)
+{
+    switch (st) {
+    case DIRAC_OK: return "ok";
+    case DIRAC_ERR_INVALID_ARG: return "invalid argument";
+    case DIRAC_ERR_UNSUPPORTED: return "unsupported";
+    case DIRAC_ERR_OOM: return "out of device memory";
+    case DIRAC_ERR_CUDA: return "CUDA error";
+    case DIRAC_NOT_CONVERGED: return "not converged";
+    case DIRAC_BREAKDOWN: return "breakdown";
+    case DIRAC_TIMEOUT: return "timeout";
+    }
+    return "unknown status";
+}
+
+dirac_status dirac_handle::fail(dirac_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    err = buf;
+    return st;
+}
+
+dirac_status dirac_handle::cuda(cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return DIRAC_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(DIRAC_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return fail(DIRAC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+dirac_status dirac_handle::alloc(void** p, size_t bytes, const char* what)
+{
+    *p = nullptr;
+    if (bytes == 0) return DIRAC_OK;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? DIRAC_ERR_OOM : DIRAC_ERR_CUDA,
+                    "allocating %zu bytes for %s: %s", bytes, what, cudaGetErrorString(e));
+    }
+    return DIRAC_OK;
+}
+
+void dirac_handle::release(void*& p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+size_t dirac_handle::field_bytes_internal(int nv) const
+{
+    return (size_t)g.vol * nv * nsc_of(op) * cbytes(prec);
+}
+
+size_t dirac_handle::field_bytes_canonical(int nv) const
+{
+    return (size_t)g.vol * nv * nsc_of(op) * (prec == P_F64 ? 16 : 8);
+}
+
+double dirac_handle::diag_of(double mass) const
+{
+    if (op == OP_WILSON) return 1.0 / (2.0 * mass);          // 4 + m0, m0 = 1/(2 kappa) - 4
+    if (op == OP_BRILLOUIN) return mass + 15.0 / 8.0;        // m0 - lambda_0 / 2
+    return mass;                                             // staggered m
+}
+
+dirac_status dirac_handle::ensure_workspace()
+{
+    const size_t need = field_bytes_internal(Nv);
+    if (ws_bytes >= need && ws_in && ws_out) return DIRAC_OK;
+    release(ws_in);
+    release(ws_out);
+    ws_bytes = 0;
+    dirac_status st = alloc(&ws_in, need, "apply workspace");
+    if (st) return st;
+    st = alloc(&ws_out, need, "apply workspace");
+    if (st) return st;
+    ws_bytes = need;
+    return DIRAC_OK;
+}
+
+ApplyArgs dirac_handle::args(void* out, const void* in, int nv, double diag_value) const
+{
+    ApplyArgs a;
+    a.g = g;
+    a.Nv = nv;
+    a.in = in;
+    a.out = out;
+    a.links = links;
+    a.diag = diag_value;
+    return a;
+}
+
+dirac_status dirac_handle::run_apply(bool dagger, void* out, const void* in, int nv,
+                                     double diag_value, const void* link_ptr, int p, LaunchCfg c)
+{
+    ApplyArgs a = args(out, in, nv, diag_value);
+    a.links = link_ptr;
+    return cuda(launch_apply(op, p, dagger, a, c, stream), "apply kernel launch");
+}
+
+static bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool dirac_check_device_ptr(const void* p) { return is_device_ptr(p); }
+
+// ------------------------------------------------------------------ lifecycle
+dirac_status dirac_create(dirac_handle** h, dirac_op op, int Nc, int Nx, int Ny, int Nz, int Nt,
+                          int Nv, double mass, dirac_prec prec, void* stream)
+{
+    if (!h) {
+        g_create_error = "dirac_create: NULL handle pointer";
+        return DIRAC_ERR_INVALID_ARG;
+    }
+    *h = nullptr;
+    if (op < DIRAC_STAGGERED || op > DIRAC_BRILLOUIN) {
+        g_create_error = "dirac_create: unknown operator";
+        return DIRAC_ERR_INVALID_ARG;
+    }
+    if (prec < DIRAC_F64 || prec > DIRAC_F16) {
+        g_create_error = "dirac_create: unknown precision";
+        return DIRAC_ERR_INVALID_ARG;
+    }
+    if (Nc != 3) {
+        g_create_error = "dirac_create: only Nc = 3 is built";
+        return DIRAC_ERR_UNSUPPORTED;
+    }
+    if (Nx < 2 || Ny < 2 || Nz < 2 || Nt < 2) {
+        g_create_error = "dirac_create: every lattice extent must be >= 2";
+        return DIRAC_ERR_INVALID_ARG;
+    }
+    if (Nv < 1) {
+        g_create_error = "dirac_create: Nv must be >= 1";
+        return DIRAC_ERR_INVALID_ARG;
+    }
+    if (op == DIRAC_WILSON && !(mass > 0.0)) {
+        g_create_error = "dirac_create: Wilson takes the hopping parameter kappa > 0";
+        return DIRAC_ERR_INVALID_ARG;
+    }
+    const long vol = (long)Nx * Ny * Nz * Nt;
+    if (vol > (1L << 31) / 2 || (double)vol * Nv * 12 * 16 > 2.0e11) {
+        g_create_error = "dirac_create: lattice x Nv too large for one GPU";
+        return DIRAC_ERR_INVALID_ARG;
+    }
+    dirac_handle* H = new (std::nothrow) dirac_handle();
+    if (!H) {
+        g_create_error = "dirac_create: host allocation failed";
+        return DIRAC_ERR_OOM;
+    }
+    H->op = (int)op;
+    H->Nc = Nc;
+    H->Nv = Nv;
+    H->prec = (int)prec;
+    H->g.L[0] = Nx;
+    H->g.L[1] = Ny;
+    H->g.L[2] = Nz;
+    H->g.L[3] = Nt;
+    H->g.stride[0] = 1;
+    H->g.stride[1] = Nx;
+    H->g.stride[2] = (long)Nx * Ny;
+    H->g.stride[3] = (long)Nx * Ny * Nz;
+    H->g.vol = vol;
+    H->mass = mass;
+    H->diag = H->diag_of(mass);
+    H->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&H->device) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = "dirac_create: no CUDA device";
+        delete H;
+        return DIRAC_ERR_CUDA;
+    }
+    H->cfg = default_config(H->op, H->prec, Nv);
+    if (H->op == OP_BRILLOUIN) {
+        cudaError_t e = upload_brillouin_table(H->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            g_create_error = std::string("dirac_create: direction table upload: ") + cudaGetErrorString(e);
+            delete H;
+            return DIRAC_ERR_CUDA;
+        }
+    }
+    *h = H;
+    return DIRAC_OK;
+}
+
+dirac_handle::~dirac_handle()
+{
+    release(links);
+    release(links64);
+    release(W64);
+    release(ws_in);
+    release(ws_out);
+    free_solver_workspace();
+}
+
+dirac_status dirac_destroy(dirac_handle* h)
+{
+    if (!h) return DIRAC_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    const int dev = h->device;
+    if (cur != dev) cudaSetDevice(dev);
+    delete h;
+    if (cur != dev) cudaSetDevice(cur);
+    return DIRAC_OK;
+}
+
+dirac_status dirac_set_mass(dirac_handle* h, double mass)
+{
+    if (!h) return DIRAC_ERR_INVALID_ARG;
+    if (h->op == OP_WILSON && !(mass > 0.0))
+        return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_set_mass: Wilson takes kappa > 0");
+    h->mass = mass;
+    h->diag = h->diag_of(mass);
+    return DIRAC_OK;
+}
+
+dirac_status dirac_set_stream(dirac_handle* h, void* stream)
+{
+    if (!h) return DIRAC_ERR_INVALID_ARG;
+    h->stream = (cudaStream_t)stream;
+    return DIRAC_OK;
+}
+
+// ------------------------------------------------------------------ links
+dirac_status dirac_set_links(dirac_handle* h, const void* V, dirac_prec V_prec, int on_device)
+{
+    if (!h) return DIRAC_ERR_INVALID_ARG;
+    if (!V) return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_set_links: NULL links");
+    if (V_prec != DIRAC_F64 && V_prec != DIRAC_F32)
+        return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_set_links: links must be complex double or float");
+    if (on_device && !is_device_ptr(V))
+        return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_set_links: on_device = 1 but V is not a device pointer");
+    const bool f64 = V_prec == DIRAC_F64;
+    const size_t canon_bytes = (size_t)h->g.vol * 4 * 9 * (f64 ? 16 : 8);
+    dirac_status st;
+    void* dV = nullptr;
+    const void* src = V;
+    if (!on_device) {
+        if ((st = h->alloc(&dV, canon_bytes, "staging links"))) return st;
+        if ((st = h->cuda(cudaMemcpyAsync(dV, V, canon_bytes, cudaMemcpyHostToDevice, h->stream),
+                          "copying links to the device"))) {
+            h->release(dV);
+            return st;
+        }
+        src = dV;
+    }
+    if (!h->links64 && (st = h->alloc(&h->links64, (size_t)h->g.vol * 4 * 9 * 16, "FP64 links"))) {
+        h->release(dV);
+        return st;
+    }
+    st = h->cuda(launch_links_to_f64(h->g, src, f64, h->links64, h->stream), "links conversion");
+    h->release_after_sync(dV);
+    if (st) return st;
+    h->release(h->W64);
+    const int nmat = (h->op == OP_BRILLOUIN) ? 40 : 4;
+    if (!h->links && (st = h->alloc(&h->links, (size_t)h->g.vol * 9 * nmat * cbytes(h->prec), "links")))
+        return st;
+    if (h->op == OP_BRILLOUIN) {
+        if ((st = h->build_W64())) return st;
+        st = h->cuda(launch_convert_links(h->prec, h->g, 40, h->W64, h->links, h->stream), "W conversion");
+        if (st) return st;
+        if (h->prec != P_F64) h->release_after_sync(h->W64);   // rebuilt on demand by the solver
+    } else {
+        st = h->cuda(launch_convert_links(h->prec, h->g, 4, h->links64, h->links, h->stream), "links conversion");
+        if (st) return st;
+    }
+    st = h->cuda(cudaStreamSynchronize(h->stream), "dirac_set_links");
+    if (st) return st;
+    h->have_links = true;
+    return DIRAC_OK;
+}
+
+dirac_status dirac_handle::build_W64()
+{
+    if (W64) return DIRAC_OK;
+    dirac_status st;
+    void* tmp = nullptr;
+    if ((st = alloc(&tmp, (size_t)g.vol * 81 * 9 * 16, "W build scratch"))) return st;
+    if ((st = alloc(&W64, (size_t)g.vol * 40 * 9 * 16, "FP64 W"))) {
+        release(tmp);
+        return st;
+    }
+    st = cuda(launch_build_W(g, links64, tmp, W64, stream), "W build");
+    release_after_sync(tmp);
+    return st;
+}
+
+void dirac_handle::release_after_sync(void*& p)
+{
+    if (!p) return;
+    cudaStreamSynchronize(stream);
+    release(p);
+}
+
+// ------------------------------------------------------------------ fields
+dirac_status dirac_field_bytes(const dirac_handle* h, dirac_layout layout, size_t* bytes)
+{
+    if (!h || !bytes) return DIRAC_ERR_INVALID_ARG;
+    *bytes = layout == DIRAC_INTERNAL ? h->field_bytes_internal(h->Nv) : h->field_bytes_canonical(h->Nv);
+    return DIRAC_OK;
+}
+
+dirac_status dirac_pack(dirac_handle* h, void* internal_out, const void* canonical_in)
+{
+    if (!h) return DIRAC_ERR_INVALID_ARG;
+    if (!internal_out || !canonical_in || internal_out == canonical_in)
+        return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_pack: NULL or aliased pointers");
+    return h->cuda(launch_pack_spinor(h->prec, nsc_of(h->op), h->g, h->Nv, canonical_in,
+                                      h->prec == P_F64, internal_out, h->stream), "pack");
+}
+
+dirac_status dirac_unpack(dirac_handle* h, void* canonical_out, const void* internal_in)
+{
+    if (!h) return DIRAC_ERR_INVALID_ARG;
+    if (!canonical_out || !internal_in || canonical_out == internal_in)
+        return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_unpack: NULL or aliased pointers");
+    return h->cuda(launch_unpack_spinor(h->prec, nsc_of(h->op), h->g, h->Nv, internal_in,
+                                        canonical_out, h->prec == P_F64, h->stream), "unpack");
+}
+
+// ------------------------------------------------------------------ apply
+static dirac_status apply_common(dirac_handle* h, bool dagger, void* out, const void* in,
+                                 dirac_layout layout, const char* name)
+{
+    if (!h) return DIRAC_ERR_INVALID_ARG;
+    if (!out || !in) return h->fail(DIRAC_ERR_INVALID_ARG, "%s: NULL pointer", name);
+    if (out == in) return h->fail(DIRAC_ERR_INVALID_ARG, "%s: out must not alias in", name);
+    if (layout != DIRAC_CANONICAL && layout != DIRAC_INTERNAL)
+        return h->fail(DIRAC_ERR_INVALID_ARG, "%s: unknown layout", name);
+    if (!h->have_links) return h->fail(DIRAC_ERR_INVALID_ARG, "%s: call dirac_set_links first", name);
+    if (!is_device_ptr(out) || !is_device_ptr(in))
+        return h->fail(DIRAC_ERR_INVALID_ARG, "%s: in and out must be device pointers", name);
+    dirac_status st;
+    if (layout == DIRAC_INTERNAL)
+        return h->run_apply(dagger, out, in, h->Nv, h->diag, h->links, h->prec, h->cfg);
+    if ((st = h->ensure_workspace())) return st;
+    if ((st = dirac_pack(h, h->ws_in, in))) return st;
+    if ((st = h->run_apply(dagger, h->ws_out, h->ws_in, h->Nv, h->diag, h->links, h->prec, h->cfg)))
+        return st;
+    return dirac_unpack(h, out, h->ws_out);
+}
+
+dirac_status dirac_apply(dirac_handle* h, void* out, const void* in, dirac_layout layout)
+{
+    return apply_common(h, false, out, in, layout, "dirac_apply");
+}
+
+dirac_status dirac_apply_dagger(dirac_handle* h, void* out, const void* in, dirac_layout layout)
+{
+    return apply_common(h, true, out, in, layout, "dirac_apply_dagger");
+}
+
+// ------------------------------------------------------------------ config
+dirac_status dirac_set_kernel_config(dirac_handle* h, int R, int block)
+{
+    if (!h) return DIRAC_ERR_INVALID_ARG;
+    if (!apply_config_supported(h->op, h->prec, R, block))
+        return h->fail(DIRAC_ERR_UNSUPPORTED, "dirac_set_kernel_config: R = %d, block = %d not built", R, block);
+    h->cfg = LaunchCfg{R, block};
+    return DIRAC_OK;
+}
+
+dirac_status dirac_get_kernel_config(const dirac_handle* h, int* R, int* block)
+{
+    if (!h || !R || !block) return DIRAC_ERR_INVALID_ARG;
+    *R = h->cfg.R;
+    *block = h->cfg.block;
+    return DIRAC_OK;
+}
+
+const char* dirac_last_error(const dirac_handle* h)
+{
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+// ------------------------------------------------------------------ dispatch
+namespace dirac {
+
+bool apply_config_supported(int op, int prec, int R, int block)
+{
+    (void)prec;
+    if (block < 32 || block > 256 || block % 32) return false;
+    if (op == OP_STAGGERED) return R == 1 || R == 2 || R == 4 || R == 6;
+    return R >= 1 && R <= 4;
+}
+
+LaunchCfg default_config(int op, int prec, int Nv)
+{
+    // the largest right-hand-side group that divides Nv and fits the
+    // registers without spilling (FP64 sweeps use at most 2 / 4)
+    if (op == OP_STAGGERED) {
+        int R = (Nv % 6 == 0) ? 6 : (Nv % 4 == 0 ? 4 : (Nv % 2 == 0 ? 2 : 1));
+        if (prec == P_F64 && R > 4) R = 4;
+        return LaunchCfg{R, 128};
+    }
+    if (prec == P_F64) return LaunchCfg{(Nv % 2 == 0) ? 2 : 1, 128};
+    int R = (Nv % 4 == 0) ? 4 : (Nv % 3 == 0 ? 3 : (Nv % 2 == 0 ? 2 : (Nv >= 4 ? 4 : Nv)));
+    return LaunchCfg{R, 128};
+}
+
+cudaError_t launch_apply(int op, int prec, bool dagger, const ApplyArgs& a, LaunchCfg cfg, cudaStream_t st)
+{
+    if (a.g.vol == 0 || a.Nv == 0) return cudaSuccess;
+    switch (op) {
+    case OP_STAGGERED: return launch_apply_staggered(prec, dagger, a, cfg, st);
+    case OP_WILSON: return launch_apply_wilson(prec, dagger, a, cfg, st);
+    case OP_BRILLOUIN: return launch_apply_brillouin(prec, dagger, a, cfg, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace dirac
+
+void dirac_handle::free_solver_workspace()
+{
+    release(sw);
+    sw_bytes = 0;
+    sw_nv = 0;
+}

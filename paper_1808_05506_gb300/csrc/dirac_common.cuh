@@ -1,0 +1,318 @@
+// Shared device-side building blocks of the Dirac kernels: storage types,
+// the internal site-fastest layouts, complex arithmetic, lattice geometry and
+// the chiral-basis spin projectors.
+//
+// Internal layouts (all site-fastest structure-of-arrays, one "element" is a
+// 4- to 16-byte vector so that a warp reading 32 consecutive sites issues one
+// coalesced load per element):
+//   spinor   [v][k][site]   k = 0..K-1 element of right-hand side v at a site;
+//                           Wilson/Brillouin: 12 complex (spin-major, colour-
+//                           minor) split into K = 12/CPV elements of CPV
+//                           complex each; staggered: 3 complex, K = 3, CPV = 1.
+//   links    [m][e][site]   m = mu (0..3) for V_mu, or one of the 40 stored
+//                           Brillouin directions; e = row*3 + col (9 complex).
+// Site index s = x + Nx (y + Ny (z + Nz t)).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#if defined(__CUDA_ARCH__)
+#define DEV_INLINE __device__ __forceinline__
+#else
+#define DEV_INLINE inline
+#endif
+#define HD __host__ __device__ __forceinline__
+
+namespace dirac {
+
+// ---------------------------------------------------------------- complex
+template <typename A> struct cx { A re, im; };
+
+template <typename A> HD cx<A> cmk(A r, A i) { return cx<A>{r, i}; }
+template <typename A> HD cx<A> operator+(cx<A> a, cx<A> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename A> HD cx<A> operator-(cx<A> a, cx<A> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename A> HD cx<A> operator-(cx<A> a) { return {-a.re, -a.im}; }
+template <typename A> HD cx<A> conj(cx<A> a) { return {a.re, -a.im}; }
+template <typename A> HD cx<A> times_i(cx<A> a) { return {-a.im, a.re}; }        // i a
+template <typename A> HD cx<A> times_mi(cx<A> a) { return {a.im, -a.re}; }       // -i a
+template <typename A> HD cx<A> scale(A s, cx<A> a) { return {s * a.re, s * a.im}; }
+// acc + a*b
+template <typename A> HD cx<A> cfma(cx<A> a, cx<A> b, cx<A> acc)
+{
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(-a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(a.im, b.re, acc.im);
+    return acc;
+}
+// acc + conj(a)*b
+template <typename A> HD cx<A> cfma_conj(cx<A> a, cx<A> b, cx<A> acc)
+{
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(-a.im, b.re, acc.im);
+    return acc;
+}
+template <typename A> HD cx<A> cmul(cx<A> a, cx<A> b) { return cfma(a, b, cx<A>{A(0), A(0)}); }
+
+// ---------------------------------------------------------------- storage
+enum Prec { P_F64 = 0, P_F32 = 1, P_BF16 = 2, P_F16 = 3 };
+
+template <typename T> struct Store;
+template <> struct Store<double> {
+    using A = double;              // arithmetic type
+    using Vec = double2;           // 16-byte element = 1 complex
+    static constexpr int CPV = 1;
+    using One = double2;           // element holding 1 complex
+};
+template <> struct Store<float> {
+    using A = float;
+    using Vec = float4;            // 16-byte element = 2 complex
+    static constexpr int CPV = 2;
+    using One = float2;
+};
+template <> struct Store<__nv_bfloat16> {
+    using A = float;
+    using Vec = uint4;             // 16-byte element = 4 complex
+    static constexpr int CPV = 4;
+    using One = uint32_t;
+};
+template <> struct Store<__half> {
+    using A = float;
+    using Vec = uint4;
+    static constexpr int CPV = 4;
+    using One = uint32_t;
+};
+
+// 16-bit pair <-> float complex
+HD cx<float> unpack2(uint32_t w, __nv_bfloat16*)
+{
+    __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&w);
+    float2 f = __bfloat1622float2(h);
+    return {f.x, f.y};
+}
+HD cx<float> unpack2(uint32_t w, __half*)
+{
+    __half2 h = *reinterpret_cast<__half2*>(&w);
+    float2 f = __half22float2(h);
+    return {f.x, f.y};
+}
+HD uint32_t pack2(cx<float> c, __nv_bfloat16*)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(c.re, c.im);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+HD uint32_t pack2(cx<float> c, __half*)
+{
+    __half2 h = __floats2half2_rn(c.re, c.im);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// read-only / streaming memory access (plain accesses when emulated on the host)
+template <typename V> DEV_INLINE V ld_ro(const V* p)
+{
+#if defined(__CUDA_ARCH__)
+    return __ldg(p);
+#else
+    return *p;
+#endif
+}
+template <typename V> DEV_INLINE void st_cs(V* p, V v)
+{
+#if defined(__CUDA_ARCH__)
+    __stcs(p, v);
+#else
+    *p = v;
+#endif
+}
+
+// one complex number of storage type T at element index i
+template <typename T> DEV_INLINE cx<typename Store<T>::A> ld_one(const void* base, size_t i);
+template <> DEV_INLINE cx<double> ld_one<double>(const void* base, size_t i)
+{
+    double2 v = ld_ro(reinterpret_cast<const double2*>(base) + i);
+    return {v.x, v.y};
+}
+template <> DEV_INLINE cx<float> ld_one<float>(const void* base, size_t i)
+{
+    float2 v = ld_ro(reinterpret_cast<const float2*>(base) + i);
+    return {v.x, v.y};
+}
+template <> DEV_INLINE cx<float> ld_one<__nv_bfloat16>(const void* base, size_t i)
+{
+    return unpack2(ld_ro(reinterpret_cast<const uint32_t*>(base) + i), (__nv_bfloat16*)nullptr);
+}
+template <> DEV_INLINE cx<float> ld_one<__half>(const void* base, size_t i)
+{
+    return unpack2(ld_ro(reinterpret_cast<const uint32_t*>(base) + i), (__half*)nullptr);
+}
+
+template <typename T> DEV_INLINE void st_one(void* base, size_t i, cx<typename Store<T>::A> c);
+template <> DEV_INLINE void st_one<double>(void* base, size_t i, cx<double> c)
+{
+    st_cs(reinterpret_cast<double2*>(base) + i, make_double2(c.re, c.im));
+}
+template <> DEV_INLINE void st_one<float>(void* base, size_t i, cx<float> c)
+{
+    st_cs(reinterpret_cast<float2*>(base) + i, make_float2(c.re, c.im));
+}
+template <> DEV_INLINE void st_one<__nv_bfloat16>(void* base, size_t i, cx<float> c)
+{
+    st_cs(reinterpret_cast<uint32_t*>(base) + i, pack2(c, (__nv_bfloat16*)nullptr));
+}
+template <> DEV_INLINE void st_one<__half>(void* base, size_t i, cx<float> c)
+{
+    st_cs(reinterpret_cast<uint32_t*>(base) + i, pack2(c, (__half*)nullptr));
+}
+
+// 16-byte element with CPV complex
+template <typename T> DEV_INLINE void ld_vec(const void* base, size_t i, cx<typename Store<T>::A>* out);
+template <> DEV_INLINE void ld_vec<double>(const void* base, size_t i, cx<double>* o)
+{
+    double2 v = ld_ro(reinterpret_cast<const double2*>(base) + i);
+    o[0] = {v.x, v.y};
+}
+template <> DEV_INLINE void ld_vec<float>(const void* base, size_t i, cx<float>* o)
+{
+    float4 v = ld_ro(reinterpret_cast<const float4*>(base) + i);
+    o[0] = {v.x, v.y};
+    o[1] = {v.z, v.w};
+}
+template <typename H> DEV_INLINE void ld_vec16(const void* base, size_t i, cx<float>* o)
+{
+    uint4 v = ld_ro(reinterpret_cast<const uint4*>(base) + i);
+    o[0] = unpack2(v.x, (H*)nullptr);
+    o[1] = unpack2(v.y, (H*)nullptr);
+    o[2] = unpack2(v.z, (H*)nullptr);
+    o[3] = unpack2(v.w, (H*)nullptr);
+}
+template <> DEV_INLINE void ld_vec<__nv_bfloat16>(const void* b, size_t i, cx<float>* o) { ld_vec16<__nv_bfloat16>(b, i, o); }
+template <> DEV_INLINE void ld_vec<__half>(const void* b, size_t i, cx<float>* o) { ld_vec16<__half>(b, i, o); }
+
+template <typename T> DEV_INLINE void st_vec(void* base, size_t i, const cx<typename Store<T>::A>* c);
+template <> DEV_INLINE void st_vec<double>(void* base, size_t i, const cx<double>* c)
+{
+    st_cs(reinterpret_cast<double2*>(base) + i, make_double2(c[0].re, c[0].im));
+}
+template <> DEV_INLINE void st_vec<float>(void* base, size_t i, const cx<float>* c)
+{
+    st_cs(reinterpret_cast<float4*>(base) + i, make_float4(c[0].re, c[0].im, c[1].re, c[1].im));
+}
+template <typename H> DEV_INLINE void st_vec16(void* base, size_t i, const cx<float>* c)
+{
+    uint4 v;
+    v.x = pack2(c[0], (H*)nullptr);
+    v.y = pack2(c[1], (H*)nullptr);
+    v.z = pack2(c[2], (H*)nullptr);
+    v.w = pack2(c[3], (H*)nullptr);
+    st_cs(reinterpret_cast<uint4*>(base) + i, v);
+}
+template <> DEV_INLINE void st_vec<__nv_bfloat16>(void* b, size_t i, const cx<float>* c) { st_vec16<__nv_bfloat16>(b, i, c); }
+template <> DEV_INLINE void st_vec<__half>(void* b, size_t i, const cx<float>* c) { st_vec16<__half>(b, i, c); }
+
+// spinor of NSC complex (12 Wilson/Brillouin, 3 staggered) for rhs v at site s
+template <typename T, int NSC> struct SpinorLayout {
+    static constexpr int CPV = (NSC == 12) ? Store<T>::CPV : 1;
+    static constexpr int K = NSC / CPV;
+};
+
+template <typename T, int NSC>
+DEV_INLINE void load_spinor(const void* base, size_t vol, int v, long s, cx<typename Store<T>::A>* out)
+{
+    using L = SpinorLayout<T, NSC>;
+#pragma unroll
+    for (int k = 0; k < L::K; ++k) {
+        size_t idx = ((size_t)v * L::K + k) * vol + (size_t)s;
+        if constexpr (L::CPV == 1) out[k] = ld_one<T>(base, idx);
+        else ld_vec<T>(base, idx, out + k * L::CPV);
+    }
+}
+
+template <typename T, int NSC>
+DEV_INLINE void store_spinor(void* base, size_t vol, int v, long s, const cx<typename Store<T>::A>* in)
+{
+    using L = SpinorLayout<T, NSC>;
+#pragma unroll
+    for (int k = 0; k < L::K; ++k) {
+        size_t idx = ((size_t)v * L::K + k) * vol + (size_t)s;
+        if constexpr (L::CPV == 1) st_one<T>(base, idx, in[k]);
+        else st_vec<T>(base, idx, in + k * L::CPV);
+    }
+}
+
+// 3x3 link m at site s
+template <typename T>
+DEV_INLINE void load_link(const void* base, size_t vol, int m, long s, cx<typename Store<T>::A>* U)
+{
+#pragma unroll
+    for (int e = 0; e < 9; ++e) U[e] = ld_one<T>(base, ((size_t)m * 9 + e) * vol + (size_t)s);
+}
+
+// w = U h  /  w = U^dagger h   (3-vectors)
+template <typename A> HD void mat_vec(const cx<A>* U, const cx<A>* h, cx<A>* w)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        cx<A> acc = cmul(U[3 * a], h[0]);
+        acc = cfma(U[3 * a + 1], h[1], acc);
+        acc = cfma(U[3 * a + 2], h[2], acc);
+        w[a] = acc;
+    }
+}
+template <typename A> HD void mat_dag_vec(const cx<A>* U, const cx<A>* h, cx<A>* w)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        cx<A> acc = cmul(conj(U[a]), h[0]);
+        acc = cfma_conj(U[3 + a], h[1], acc);
+        acc = cfma_conj(U[6 + a], h[2], acc);
+        w[a] = acc;
+    }
+}
+// acc += U h / acc += U^dagger h
+template <typename A> HD void mat_vec_acc(const cx<A>* U, const cx<A>* h, cx<A>* acc)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        acc[a] = cfma(U[3 * a], h[0], acc[a]);
+        acc[a] = cfma(U[3 * a + 1], h[1], acc[a]);
+        acc[a] = cfma(U[3 * a + 2], h[2], acc[a]);
+    }
+}
+template <typename A> HD void mat_dag_vec_acc(const cx<A>* U, const cx<A>* h, cx<A>* acc)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        acc[a] = cfma_conj(U[a], h[0], acc[a]);
+        acc[a] = cfma_conj(U[3 + a], h[1], acc[a]);
+        acc[a] = cfma_conj(U[6 + a], h[2], acc[a]);
+    }
+}
+
+// ---------------------------------------------------------------- geometry
+struct Geom {
+    int L[4];        // Nx, Ny, Nz, Nt
+    long stride[4];  // 1, Nx, Nx Ny, Nx Ny Nz
+    long vol;
+};
+
+// neighbour offsets of site s: fwd[mu] = (s + mu) - s, bwd[mu] = (s - mu) - s (periodic)
+HD void site_offsets(const Geom& g, long s, long* fwd, long* bwd, int* x)
+{
+    long r = s;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        int c = (int)(r % g.L[mu]);
+        r /= g.L[mu];
+        x[mu] = c;
+        fwd[mu] = (c == g.L[mu] - 1) ? -(long)(g.L[mu] - 1) * g.stride[mu] : g.stride[mu];
+        bwd[mu] = (c == 0) ? (long)(g.L[mu] - 1) * g.stride[mu] : -g.stride[mu];
+    }
+}
+
+}  // namespace dirac

@@ -1,0 +1,55 @@
+// The opaque handle behind dirac_handle* (include/dirac.h).
+#pragma once
+
+#include <string>
+
+#include "../../include/dirac.h"
+#include "dirac_internal.h"
+
+namespace dirac {
+LaunchCfg default_config(int op, int prec, int Nv);
+}
+
+struct dirac_handle {
+    int op = 0, Nc = 3, Nv = 1, prec = 1;
+    dirac::Geom g{};
+    double mass = 0.0;        // as given: staggered m, Wilson kappa, Brillouin m0
+    double diag = 0.0;        // the site-diagonal coefficient of the sweep
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    dirac::LaunchCfg cfg{1, 128};
+
+    void* links = nullptr;    // storage-precision links [m][9][site] (m = mu, or 40 stored W)
+    void* links64 = nullptr;  // FP64 V_mu [4][9][site]
+    void* W64 = nullptr;      // FP64 W [40][9][site] (Brillouin; kept for F64 handles, lazy otherwise)
+    bool have_links = false;
+
+    void* ws_in = nullptr;    // internal-layout workspaces of the canonical apply
+    void* ws_out = nullptr;
+    size_t ws_bytes = 0;
+
+    // solver workspace (dirac_solve.cu)
+    void* sw = nullptr;
+    size_t sw_bytes = 0;
+    int sw_nv = 0;
+
+    std::string err;
+
+    ~dirac_handle();
+    dirac_status fail(dirac_status st, const char* fmt, ...);
+    dirac_status cuda(cudaError_t e, const char* what);
+    dirac_status alloc(void** p, size_t bytes, const char* what);
+    void release(void*& p);
+    void release_after_sync(void*& p);
+    size_t field_bytes_internal(int nv) const;
+    size_t field_bytes_canonical(int nv) const;
+    double diag_of(double mass) const;
+    dirac_status ensure_workspace();
+    dirac_status build_W64();
+    dirac::ApplyArgs args(void* out, const void* in, int nv, double diag_value) const;
+    dirac_status run_apply(bool dagger, void* out, const void* in, int nv, double diag_value,
+                           const void* link_ptr, int p, dirac::LaunchCfg c);
+    void free_solver_workspace();
+};
+
+bool dirac_check_device_ptr(const void* p);

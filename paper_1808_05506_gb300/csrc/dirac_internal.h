@@ -1,0 +1,59 @@
+// Host-side launchers shared between the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "dirac_common.cuh"
+#include "dirac_kernels.cuh"
+
+namespace dirac {
+
+enum Op { OP_STAGGERED = 0, OP_WILSON = 1, OP_BRILLOUIN = 2 };
+
+// complex numbers per site and right-hand side
+inline int nsc_of(int op) { return op == OP_STAGGERED ? 3 : 12; }
+
+// bytes of one storage-precision complex number
+inline size_t cbytes(int prec)
+{
+    return prec == P_F64 ? 16 : (prec == P_F32 ? 8 : 4);
+}
+
+struct LaunchCfg {
+    int R;       // right-hand sides per thread
+    int block;   // threads per block
+};
+
+bool apply_config_supported(int op, int prec, int R, int block);
+
+// out = D in (or D^+ in) on internal-layout fields
+cudaError_t launch_apply(int op, int prec, bool dagger, const ApplyArgs& a, LaunchCfg cfg,
+                         cudaStream_t st);
+cudaError_t launch_apply_staggered(int prec, bool dagger, const ApplyArgs& a, LaunchCfg cfg,
+                                   cudaStream_t st);
+cudaError_t launch_apply_wilson(int prec, bool dagger, const ApplyArgs& a, LaunchCfg cfg,
+                                cudaStream_t st);
+cudaError_t launch_apply_brillouin(int prec, bool dagger, const ApplyArgs& a, LaunchCfg cfg,
+                                   cudaStream_t st);
+
+// the 80 Brillouin directions and the dir81 code of each of the 40 stored ones
+void brillouin_tables(BriDir dirs[80], int rep_dir81[40]);
+cudaError_t upload_brillouin_table(cudaStream_t st);
+
+// canonical (complex double if canon_f64 else complex float) <-> internal spinor
+cudaError_t launch_pack_spinor(int prec, int nsc, const Geom& g, int Nv, const void* canon,
+                               bool canon_f64, void* internal, cudaStream_t st);
+cudaError_t launch_unpack_spinor(int prec, int nsc, const Geom& g, int Nv, const void* internal,
+                                 void* canon, bool canon_f64, cudaStream_t st);
+
+// canonical links V[s][mu][a][b] -> FP64 internal [mu][9][s]
+cudaError_t launch_links_to_f64(const Geom& g, const void* canon, bool canon_f64, void* V64,
+                                cudaStream_t st);
+// FP64 internal [m][9][s] -> storage precision internal [m][9][s] (nmat matrices per site)
+cudaError_t launch_convert_links(int prec, const Geom& g, int nmat, const void* src64, void* dst,
+                                 cudaStream_t st);
+// Tab. tab:off-axis: FP64 links V64 [4][9][s] -> FP64 W64 [40][9][s]; tmp81 holds
+// 81 * 9 * vol complex doubles.
+cudaError_t launch_build_W(const Geom& g, const void* V64, void* tmp81, void* W64, cudaStream_t st);
+
+}  // namespace dirac

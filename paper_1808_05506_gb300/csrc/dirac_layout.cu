@@ -1,0 +1,258 @@
+// Layout conversion (canonical <-> internal site-fastest layout) and the
+// Brillouin off-axis link build of Tab. tab:off-axis.
+#include "dirac_internal.h"
+
+namespace dirac {
+
+// ---------------------------------------------------------------- spinors
+template <typename T, int NSC, typename CT>
+__global__ void k_pack(Geom g, int Nv, const CT* __restrict__ canon, void* internal)
+{
+    using A = typename Store<T>::A;
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;   // (site, v), v fastest
+    if (i >= g.vol * Nv) return;
+    const long s = i / Nv;
+    const int v = (int)(i % Nv);
+    const CT* src = canon + (size_t)i * NSC * 2;
+    cx<A> p[NSC];
+#pragma unroll
+    for (int c = 0; c < NSC; ++c) p[c] = cx<A>{(A)src[2 * c], (A)src[2 * c + 1]};
+    store_spinor<T, NSC>(internal, g.vol, v, s, p);
+}
+
+template <typename T, int NSC, typename CT>
+__global__ void k_unpack(Geom g, int Nv, const void* internal, CT* __restrict__ canon)
+{
+    using A = typename Store<T>::A;
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.vol * Nv) return;
+    const long s = i / Nv;
+    const int v = (int)(i % Nv);
+    cx<A> p[NSC];
+    load_spinor<T, NSC>(internal, g.vol, v, s, p);
+    CT* dst = canon + (size_t)i * NSC * 2;
+#pragma unroll
+    for (int c = 0; c < NSC; ++c) {
+        dst[2 * c] = (CT)p[c].re;
+        dst[2 * c + 1] = (CT)p[c].im;
+    }
+}
+
+template <typename T, int NSC>
+static cudaError_t pack_T(const Geom& g, int Nv, const void* canon, bool f64, void* internal,
+                          cudaStream_t st)
+{
+    const long n = g.vol * Nv;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    if (f64) k_pack<T, NSC, double><<<nb, 256, 0, st>>>(g, Nv, (const double*)canon, internal);
+    else k_pack<T, NSC, float><<<nb, 256, 0, st>>>(g, Nv, (const float*)canon, internal);
+    return cudaGetLastError();
+}
+
+template <typename T, int NSC>
+static cudaError_t unpack_T(const Geom& g, int Nv, const void* internal, void* canon, bool f64,
+                            cudaStream_t st)
+{
+    const long n = g.vol * Nv;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    if (f64) k_unpack<T, NSC, double><<<nb, 256, 0, st>>>(g, Nv, internal, (double*)canon);
+    else k_unpack<T, NSC, float><<<nb, 256, 0, st>>>(g, Nv, internal, (float*)canon);
+    return cudaGetLastError();
+}
+
+#define DISPATCH_PREC_NSC(FN, ...)                                                        \
+    switch (prec) {                                                                       \
+    case P_F64: return nsc == 12 ? FN<double, 12>(__VA_ARGS__) : FN<double, 3>(__VA_ARGS__); \
+    case P_F32: return nsc == 12 ? FN<float, 12>(__VA_ARGS__) : FN<float, 3>(__VA_ARGS__);   \
+    case P_BF16:                                                                          \
+        return nsc == 12 ? FN<__nv_bfloat16, 12>(__VA_ARGS__) : FN<__nv_bfloat16, 3>(__VA_ARGS__); \
+    case P_F16: return nsc == 12 ? FN<__half, 12>(__VA_ARGS__) : FN<__half, 3>(__VA_ARGS__); \
+    default: return cudaErrorInvalidValue;                                                \
+    }
+
+cudaError_t launch_pack_spinor(int prec, int nsc, const Geom& g, int Nv, const void* canon,
+                               bool canon_f64, void* internal, cudaStream_t st)
+{
+    if (g.vol * Nv == 0) return cudaSuccess;
+    DISPATCH_PREC_NSC(pack_T, g, Nv, canon, canon_f64, internal, st)
+}
+
+cudaError_t launch_unpack_spinor(int prec, int nsc, const Geom& g, int Nv, const void* internal,
+                                 void* canon, bool canon_f64, cudaStream_t st)
+{
+    if (g.vol * Nv == 0) return cudaSuccess;
+    DISPATCH_PREC_NSC(unpack_T, g, Nv, internal, canon, canon_f64, st)
+}
+
+// ---------------------------------------------------------------- links
+template <typename CT>
+__global__ void k_links_to_f64(Geom g, const CT* __restrict__ canon, double2* V64)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;   // (site, mu)
+    if (i >= g.vol * 4) return;
+    const long s = i / 4;
+    const int mu = (int)(i % 4);
+    const CT* src = canon + (size_t)i * 18;
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+        V64[((size_t)mu * 9 + e) * g.vol + s] = make_double2((double)src[2 * e], (double)src[2 * e + 1]);
+}
+
+cudaError_t launch_links_to_f64(const Geom& g, const void* canon, bool canon_f64, void* V64,
+                                cudaStream_t st)
+{
+    const unsigned nb = (unsigned)((g.vol * 4 + 255) / 256);
+    if (canon_f64) k_links_to_f64<double><<<nb, 256, 0, st>>>(g, (const double*)canon, (double2*)V64);
+    else k_links_to_f64<float><<<nb, 256, 0, st>>>(g, (const float*)canon, (double2*)V64);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_convert_links(long n, const double2* __restrict__ src, void* dst)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 v = src[i];
+    using A = typename Store<T>::A;
+    st_one<T>(dst, (size_t)i, cx<A>{(A)v.x, (A)v.y});
+}
+
+cudaError_t launch_convert_links(int prec, const Geom& g, int nmat, const void* src64, void* dst,
+                                 cudaStream_t st)
+{
+    const long n = g.vol * 9L * nmat;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    const double2* s = (const double2*)src64;
+    switch (prec) {
+    case P_F64: k_convert_links<double><<<nb, 256, 0, st>>>(n, s, dst); break;
+    case P_F32: k_convert_links<float><<<nb, 256, 0, st>>>(n, s, dst); break;
+    case P_BF16: k_convert_links<__nv_bfloat16><<<nb, 256, 0, st>>>(n, s, dst); break;
+    case P_F16: k_convert_links<__half><<<nb, 256, 0, st>>>(n, s, dst); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- W build
+// Tab. tab:off-axis defines W_dir(x) as the average of the path products over
+// the k! orderings of the k unit hops of dir.  Splitting off the first hop a
+// gives the recursion W_dir(x) = (1/k) sum_{hops a of dir} V_a(x) W_{dir-a}(x+a)
+// with V_{-mu}(x) = V_mu(x-mu)^+; it is evaluated level by level (k = 1..4)
+// in FP64 over all 80 directions, with tmp81 laid out [dir81][9][site].
+__device__ __forceinline__ int dir81_of(const int d[4])
+{
+    return (d[0] + 1) + 3 * (d[1] + 1) + 9 * (d[2] + 1) + 27 * (d[3] + 1);
+}
+
+__global__ void k_wbuild_level1(Geom g, const double2* __restrict__ V64, double2* tmp)
+{
+    const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.vol) return;
+    long fwd[4], bwd[4];
+    int x[4];
+    site_offsets(g, s, fwd, bwd, x);
+    for (int mu = 0; mu < 4; ++mu) {
+        int dp[4] = {0, 0, 0, 0}, dm[4] = {0, 0, 0, 0};
+        dp[mu] = 1;
+        dm[mu] = -1;
+        const int cp = dir81_of(dp), cm = dir81_of(dm);
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                tmp[((size_t)cp * 9 + a * 3 + b) * g.vol + s] = V64[((size_t)mu * 9 + a * 3 + b) * g.vol + s];
+                double2 u = V64[((size_t)mu * 9 + b * 3 + a) * g.vol + s + bwd[mu]];
+                tmp[((size_t)cm * 9 + a * 3 + b) * g.vol + s] = make_double2(u.x, -u.y);
+            }
+    }
+}
+
+struct DirList {
+    int n;
+    int k;
+    short code[32];
+};
+
+__global__ void k_wbuild_level(Geom g, DirList L, double2* tmp)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;   // (site, j), site fastest
+    if (i >= g.vol * L.n) return;
+    const long s = i % g.vol;
+    const int j = (int)(i / g.vol);
+    const int c = L.code[j];
+    int d[4] = {c % 3 - 1, (c / 3) % 3 - 1, (c / 9) % 3 - 1, (c / 27) % 3 - 1};
+    long fwd[4], bwd[4];
+    int x[4];
+    site_offsets(g, s, fwd, bwd, x);
+    cx<double> acc[9];
+    for (int e = 0; e < 9; ++e) acc[e] = cx<double>{0.0, 0.0};
+    for (int mu = 0; mu < 4; ++mu) {
+        if (d[mu] == 0) continue;
+        int a[4] = {0, 0, 0, 0};
+        a[mu] = d[mu];
+        int rest[4] = {d[0], d[1], d[2], d[3]};
+        rest[mu] = 0;
+        const int ca = dir81_of(a), cr = dir81_of(rest);
+        const long sa = s + (d[mu] > 0 ? fwd[mu] : bwd[mu]);
+        cx<double> Va[9], Wr[9];
+        for (int e = 0; e < 9; ++e) {
+            double2 u = tmp[((size_t)ca * 9 + e) * g.vol + s];
+            double2 w = tmp[((size_t)cr * 9 + e) * g.vol + sa];
+            Va[e] = {u.x, u.y};
+            Wr[e] = {w.x, w.y};
+        }
+        for (int r = 0; r < 3; ++r)
+            for (int q = 0; q < 3; ++q) {
+                cx<double> t = acc[r * 3 + q];
+                for (int m = 0; m < 3; ++m) t = cfma(Va[r * 3 + m], Wr[m * 3 + q], t);
+                acc[r * 3 + q] = t;
+            }
+    }
+    const double inv = 1.0 / L.k;
+    for (int e = 0; e < 9; ++e)
+        tmp[((size_t)c * 9 + e) * g.vol + s] = make_double2(acc[e].re * inv, acc[e].im * inv);
+}
+
+struct RepList {
+    short code[40];
+};
+
+__global__ void k_wbuild_store(Geom g, RepList R, const double2* __restrict__ tmp, double2* W64)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;   // (site, rep), site fastest
+    if (i >= g.vol * 40) return;
+    const long s = i % g.vol;
+    const int r = (int)(i / g.vol);
+    for (int e = 0; e < 9; ++e) W64[((size_t)r * 9 + e) * g.vol + s] = tmp[((size_t)R.code[r] * 9 + e) * g.vol + s];
+}
+
+cudaError_t launch_build_W(const Geom& g, const void* V64, void* tmp81, void* W64, cudaStream_t st)
+{
+    double2* tmp = (double2*)tmp81;
+    unsigned nb = (unsigned)((g.vol + 255) / 256);
+    k_wbuild_level1<<<nb, 256, 0, st>>>(g, (const double2*)V64, tmp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    for (int k = 2; k <= 4; ++k) {
+        DirList L;
+        L.n = 0;
+        L.k = k;
+        for (int c = 0; c < 81; ++c) {
+            int d[4] = {c % 3 - 1, (c / 3) % 3 - 1, (c / 9) % 3 - 1, (c / 27) % 3 - 1};
+            int kk = (d[0] != 0) + (d[1] != 0) + (d[2] != 0) + (d[3] != 0);
+            if (kk == k) L.code[L.n++] = (short)c;
+        }
+        const long n = g.vol * L.n;
+        k_wbuild_level<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(g, L, tmp);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    BriDir dirs[80];
+    int reps[40];
+    brillouin_tables(dirs, reps);
+    RepList R;
+    for (int r = 0; r < 40; ++r) R.code[r] = (short)reps[r];
+    const long n = g.vol * 40;
+    k_wbuild_store<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, R, tmp, (double2*)W64);
+    return cudaGetLastError();
+}
+
+}  // namespace dirac

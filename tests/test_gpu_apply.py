@@ -1,0 +1,185 @@
+"""GPU parity of the Dirac sweeps against the FP64 oracle, through the C ABI.
+
+Bar (stated in the benchmark spec for this path): relative L2 error per call
+<= 1e-6 in FP32 and <= 1e-13 in FP64, the oracle run on the same rounded
+inputs the GPU saw.  BF16/FP16 storage has no apply parity target; the sweep
+is checked against its own rounding bound (a few units of the storage
+precision's epsilon).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-13, "f32": 1e-6, "bf16": 3e-2, "f16": 4e-3}
+NS = {"staggered": 1, "wilson": 4, "brillouin": 4}
+
+
+@pytest.fixture(scope="module")
+def dg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1808_05506_gb300 as dg
+    torch.cuda.set_device(0)
+    return dg
+
+
+def m0_of(op, mass):
+    return oracle.kappa_to_m0(mass) if op == "wilson" else mass
+
+
+def inputs(op, L, Nv, prec, seed, kind="haar"):
+    V = synth.gauge_links(L, 3, kind, seed)
+    psi = synth.spinor(L, Nv, NS[op], 3, seed + 1)
+    rin = "f64" if prec == "f64" else "f32"
+    V = synth.round_to(V, rin)
+    psi = synth.round_to(psi, rin)
+    return V, psi
+
+
+def rel_l2(got, want):
+    return np.linalg.norm((got - want).ravel()) / np.linalg.norm(want.ravel())
+
+
+def run(dg, op, L, Nv, mass, prec, V, psi, dagger=False, cfg=None, internal=False):
+    D = dg.Dirac(op, L, Nv, mass, prec)
+    cdt = torch.complex128 if prec == "f64" else torch.complex64
+    D.set_links(torch.from_numpy(V.astype(np.complex128 if prec == "f64" else np.complex64)).cuda())
+    if cfg:
+        D.set_kernel_config(*cfg)
+    x = torch.from_numpy(psi).to(cdt).cuda()
+    if internal:
+        xi = D.pack(x)
+        yi = D.new_internal()
+        yi.fill_(0xFF)                      # NaN pattern: every element must be overwritten
+        D.apply(xi, out=yi, dagger=dagger)
+        y = D.unpack(yi)
+    else:
+        y = D.apply(x, dagger=dagger)
+    torch.cuda.synchronize()
+    D.close()
+    return y.cpu().numpy().astype(np.complex128)
+
+
+def rounded_for_oracle(V, psi, prec):
+    if prec in ("bf16", "f16"):
+        return synth.round_to(V, prec), synth.round_to(psi, prec)
+    return V, psi
+
+
+@pytest.mark.parametrize("op,mass", [("wilson", 0.1237), ("staggered", 0.031), ("brillouin", 0.05)])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_parity_ragged(dg, op, mass, prec, dagger):
+    """Several blocks plus a ragged tail (vol = 720 is not a multiple of any
+    block size) and an Nv that leaves a partial right-hand-side group."""
+    L, Nv = (6, 4, 6, 5), 5
+    V, psi = inputs(op, L, Nv, prec, 200)
+    got = run(dg, op, L, Nv, mass, prec, V, psi, dagger=dagger)
+    want = oracle.apply(op, V, psi, m0_of(op, mass), dagger=dagger)
+    assert rel_l2(got, want) <= TOL[prec]
+
+
+@pytest.mark.parametrize("op,mass", [("wilson", 0.125), ("staggered", 0.0), ("brillouin", 0.3)])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_parity_every_config(dg, op, mass, prec):
+    L, Nv = (4, 6, 2, 4), 7
+    V, psi = inputs(op, L, Nv, prec, 210)
+    want = oracle.apply(op, V, psi, m0_of(op, mass))
+    Rs = (1, 2, 4, 6) if op == "staggered" else (1, 2, 3, 4)
+    for R in Rs:
+        for block in (32, 128, 256):
+            got = run(dg, op, L, Nv, mass, prec, V, psi, cfg=(R, block), internal=True)
+            assert rel_l2(got, want) <= TOL[prec], (R, block)
+
+
+@pytest.mark.parametrize("op,mass", [("wilson", 0.11), ("staggered", 0.2), ("brillouin", -0.1)])
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+def test_low_precision_storage(dg, op, mass, prec):
+    L, Nv = (4, 4, 4, 4), 4
+    V, psi = inputs(op, L, Nv, prec, 220, kind="near_identity")
+    got = run(dg, op, L, Nv, mass, prec, V, psi)
+    Vr, pr = rounded_for_oracle(V, psi, prec)
+    if op == "brillouin":
+        # W is built in FP64 from the FP32 links and rounded once to the storage type
+        pr = synth.round_to(psi, prec)
+        want = oracle.apply(op, V, pr, m0_of(op, mass))
+    else:
+        want = oracle.apply(op, Vr, pr, m0_of(op, mass))
+    assert rel_l2(got, want) <= TOL[prec]
+
+
+@pytest.mark.parametrize("op,mass", [("wilson", 0.13), ("staggered", 0.1), ("brillouin", 0.05)])
+def test_tiny_and_odd_lattices(dg, op, mass):
+    """Extent 2 (x+mu = x-mu, both hops land on the same site), odd extents,
+    a single right-hand side."""
+    for L, Nv in (((2, 2, 2, 2), 1), ((3, 5, 2, 3), 2), ((2, 3, 7, 2), 3)):
+        V, psi = inputs(op, L, Nv, "f64", 230)
+        got = run(dg, op, L, Nv, mass, "f64", V, psi, internal=True)
+        want = oracle.apply(op, V, psi, m0_of(op, mass))
+        assert rel_l2(got, want) <= TOL["f64"], L
+
+
+def test_staggered_config_c1_full(dg):
+    """Staggered, 8^4 periodic, Nv = 4, FP32, Haar links, m = 0: the whole lattice."""
+    L, Nv = (8, 8, 8, 8), 4
+    V, psi = inputs("staggered", L, Nv, "f32", 1001)
+    got = run(dg, "staggered", L, Nv, 0.0, "f32", V, psi)
+    assert rel_l2(got, oracle.apply("staggered", V, psi, 0.0)) <= TOL["f32"]
+
+
+def _sampled(L, n, seed):
+    vol = int(np.prod(L))
+    rng = synth.rng(seed, synth.STREAM_MISC)
+    Nx, Ny, Nz, Nt = L
+    corners = [0, vol - 1, Nx - 1, Nx * Ny * Nz * (Nt - 1)]
+    return np.unique(np.concatenate([corners, rng.integers(0, vol, n)]))
+
+
+@pytest.mark.parametrize("dagger", [False, True])
+def test_wilson_full_size_sampled(dg, dagger):
+    """Wilson 32^4, Nv = 12, FP32, kappa = 0.125, U = exp(0.3 i H): the
+    workload the benchmark times, in the same launch configuration, checked
+    on sampled sites (including the lattice corners)."""
+    L, Nv = (32, 32, 32, 32), 12
+    V = synth.round_to(synth.gauge_links(L, 3, "near_identity", 1002), "f32")
+    psi = synth.round_to(synth.spinor(L, Nv, 4, 3, 2002), "f32")
+    got = run(dg, "wilson", L, Nv, 0.125, "f32", V, psi, dagger=dagger).reshape(-1, Nv, 4, 3)
+    sites = _sampled(L, 256, 7)
+    want = oracle.apply("wilson", V, psi, 0.0, sites=sites, dagger=dagger)
+    assert rel_l2(got[sites], want) <= TOL["f32"]
+    assert np.isfinite(got).all()
+
+
+def test_brillouin_full_size_sampled(dg):
+    """Brillouin 24^3 x 48, Nv = 12, FP32 storage, m0 = 0.05, near-identity links."""
+    L, Nv = (24, 24, 24, 48), 12
+    V = synth.round_to(synth.gauge_links(L, 3, "near_identity", 1003), "f32")
+    psi = synth.round_to(synth.spinor(L, Nv, 4, 3, 2003), "f32")
+    got = run(dg, "brillouin", L, Nv, 0.05, "f32", V, psi).reshape(-1, Nv, 4, 3)
+    sites = _sampled(L, 48, 8)
+    want = oracle.apply("brillouin", V, psi, 0.05, sites=sites)
+    assert rel_l2(got[sites], want) <= TOL["f32"]
+
+
+def test_error_paths(dg):
+    D = dg.Dirac("wilson", (4, 4, 4, 4), 2, 0.12, "f32")
+    x = D.new_canonical()
+    with pytest.raises(dg.DiracError) as e:          # links not loaded yet
+        D.apply(x)
+    assert e.value.status == dg.ERR_INVALID_ARG
+    V = synth.gauge_links((4, 4, 4, 4), 3, "haar", 240)
+    D.set_links(torch.from_numpy(V))                 # host links are copied
+    with pytest.raises(dg.DiracError):               # aliasing
+        D.apply(x, out=x)
+    xh = torch.zeros_like(x, device="cpu")
+    with pytest.raises(dg.DiracError):               # host pointer
+        D.apply(xh, out=torch.zeros_like(xh))
+    with pytest.raises(dg.DiracError) as e:
+        D.set_kernel_config(5, 128)
+    assert e.value.status == dg.ERR_UNSUPPORTED
+    D.close()
