@@ -258,7 +258,14 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--lattice", default=None, help="Nx,Ny,Nz,Nt (a smaller case for profiling)")
+    ap.add_argument("--prec", default=None, choices=["f32", "bf16", "f16", "f64"])
     args = ap.parse_args()
+    global WORKLOAD
+    if args.lattice:
+        WORKLOAD = dict(WORKLOAD, L=tuple(int(v) for v in args.lattice.split(",")))
+    if args.prec:
+        WORKLOAD = dict(WORKLOAD, prec=args.prec)
     if args.impl == "reference":
         return run_reference(args)
     args.warmup = max(3, args.warmup)
@@ -277,8 +284,11 @@ def main():
     x = D.pack(xin)
     y = D.new_internal()
     vol = int(np.prod(w["L"]))
+    workload = "wilson_apply_{}_nv{}_{}".format("x".join(map(str, w["L"])), w["Nv"], w["prec"])
     flops_step = dg.flops_per_site_rhs("wilson") * vol * w["Nv"]
     bytes_step = dg.bytes_per_site("wilson", w["Nv"], w["prec"]) * vol
+    if bytes_step < 4 * 129e6:
+        raise SystemExit("the timed step must stream more than the L2 (use a larger --lattice)")
 
     step = lambda: D.apply(x, out=y)   # noqa: E731  one launch of the sweep kernel
     for _ in range(args.warmup):
@@ -322,17 +332,17 @@ def main():
     traffic = None
     if os.path.exists(TRAFFIC_FILE):
         tf = json.load(open(TRAFFIC_FILE))
-        if tf.get("kernel_hash") == kernel_hash() and tf.get("workload") == "wilson_apply_32x32x32x32_nv12_f32":
+        if tf.get("kernel_hash") == kernel_hash() and tf.get("workload") == workload:
             traffic = tf.get("dram_bytes_per_launch")
     cfg = D.kernel_config()
     line = {
         "metric": METRIC, "value": value, "unit": "Gflop/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "wilson_apply_32x32x32x32_nv12_f32", "op": "wilson", "lattice": list(w["L"]),
+        "vs_baseline": None, "dtype": "f32" if w["prec"] != "f64" else "f64", "data": "synthetic",
+        "config": {"workload": workload, "op": "wilson", "storage": w["prec"], "lattice": list(w["L"]),
                    "Nc": 3, "Nv": w["Nv"], "kappa": w["mass"], "links": "exp(0.3 i H), H traceless Gaussian",
                    "source": "complex Gaussian N(0,1)", "layout": "internal site-fastest SoA",
-                   "l2": "no flush: each step streams 2.7 GB > 129 MB L2",
+                   "l2": "no flush: each step streams {:.2f} GB > 129 MB L2".format(bytes_step / 1e9),
                    "kernel": {"rhs_per_thread": cfg[0], "block": cfg[1]},
                    "parallelism": f"replicas x{ws}"},
         "hbm_gbs": achieved,

@@ -145,6 +145,39 @@ DIRAC_API dirac_status dirac_apply(dirac_handle* h, void* out, const void* in, d
  * Same contract as dirac_apply. */
 DIRAC_API dirac_status dirac_apply_dagger(dirac_handle* h, void* out, const void* in, dirac_layout layout);
 
+/* Statistics of one dirac_solve call. */
+typedef struct {
+    int outer_iterations;   /* refinement steps (inner solves) taken */
+    int inner_iterations;   /* inner CGLS iterations summed over the refinement steps */
+    int sweeps;             /* storage-precision applications of D or D^+ */
+    int fp64_sweeps;        /* FP64 applications of D (outer residuals) */
+    double residual_max;    /* max over right-hand sides of |b - D x| / |b|, FP64 */
+    double seconds;         /* host wall time of the call */
+} dirac_solve_stats;
+
+/* Solve D x = b for all Nv right-hand sides (each with its own scalars and
+ * convergence test) by defect correction: the outer loop forms the true
+ * residual r = b - D x with FP64 links, an FP64 sweep and FP64 norms, and
+ * stops when |r_v| / |b_v| <= tol for every v; each refinement step solves
+ * D e = r / |r| approximately by CGLS (conjugate gradients on D^+ D, carrying
+ * the residual of D e = r_hat) with fields in the handle's storage precision
+ * and FP32 arithmetic (FP64 for DIRAC_F64 handles), to |r_hat - D e| <=
+ * inner_tol |r_hat| or max_inner iterations, then updates x += |r| e in FP64.
+ *   x            canonical FP64 device field; on entry the starting guess
+ *                (resume = call again with the previous result)
+ *   b            canonical FP64 device field, not aliasing x
+ *   tol          target relative residual, > 0 (e.g. 1e-10)
+ *   max_outer    maximum refinement steps, >= 1
+ *   max_inner    maximum CGLS iterations per step, >= 1
+ *   inner_tol    relative residual reduction per step, in (0, 1)
+ *   rel_residual host array of Nv doubles for the final |b - D x| / |b| (or NULL)
+ *   stats        host struct (or NULL)
+ * Blocks until done.  Returns DIRAC_OK, DIRAC_NOT_CONVERGED (x holds the
+ * last iterate), DIRAC_BREAKDOWN (non-finite residual) or an error. */
+DIRAC_API dirac_status dirac_solve(dirac_handle* h, void* x, const void* b, double tol, int max_outer,
+                                   int max_inner, double inner_tol, double* rel_residual,
+                                   dirac_solve_stats* stats);
+
 /* Kernel configuration: R = right-hand sides per thread (1..4 for Wilson and
  * Brillouin, 1, 2, 4 or 6 for staggered), block = threads per block (a
  * multiple of 32, 32..256).  UNSUPPORTED for other values. */

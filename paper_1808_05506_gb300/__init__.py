@@ -67,7 +67,18 @@ SIGNATURES = {
     "dirac_set_kernel_config": (I, [P, I, I]),
     "dirac_get_kernel_config": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
     "dirac_last_error": (ctypes.c_char_p, [P]),
+    "dirac_solve": (I, [P, P, P, D, I, I, D, P, P]),
 }
+
+
+class SolveStats(ctypes.Structure):
+    """dirac_solve_stats of include/dirac.h."""
+    _fields_ = [("outer_iterations", ctypes.c_int), ("inner_iterations", ctypes.c_int),
+                ("sweeps", ctypes.c_int), ("fp64_sweeps", ctypes.c_int),
+                ("residual_max", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 def _declare(L):
@@ -215,6 +226,25 @@ class Dirac:
 
     def apply_dagger(self, x, out=None, layout=None):
         return self.apply(x, out=out, dagger=True, layout=layout)
+
+    def solve(self, b, x0=None, tol: float = 1e-10, max_outer: int = 30, max_inner: int = 2000,
+              inner_tol: float | None = None):
+        """Solve D x = b (defect correction, FP64 outer residual).  b, x0: canonical
+        complex128 device tensors.  Returns (x, per-rhs relative residuals, stats dict, status)."""
+        import numpy as np
+        torch = _torch()
+        if inner_tol is None:
+            inner_tol = {"f64": 1e-10, "f32": 1e-5, "f16": 2e-3, "bf16": 1e-2}[self.prec]
+        b = b.to(torch.complex128).contiguous()
+        x = torch.zeros_like(b) if x0 is None else x0.to(torch.complex128).contiguous().clone()
+        res = np.zeros(self.Nv, dtype=np.float64)
+        st = SolveStats()
+        self._sync_stream()
+        status = lib().dirac_solve(self.h, _ptr(x), _ptr(b), float(tol), int(max_outer), int(max_inner),
+                                   float(inner_tol), res.ctypes.data_as(P), ctypes.byref(st))
+        if status not in (OK, NOT_CONVERGED):
+            check(status, self.h, "dirac_solve")
+        return x, res, st.as_dict(), status
 
     def set_kernel_config(self, R: int, block: int):
         check(lib().dirac_set_kernel_config(self.h, R, block), self.h, "dirac_set_kernel_config")

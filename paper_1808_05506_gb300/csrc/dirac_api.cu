@@ -442,10 +442,3 @@ cudaError_t launch_apply(int op, int prec, bool dagger, const ApplyArgs& a, Laun
 }
 
 }  // namespace dirac
-
-void dirac_handle::free_solver_workspace()
-{
-    release(sw);
-    sw_bytes = 0;
-    sw_nv = 0;
-}

@@ -1,0 +1,302 @@
+// Vector kernels of the solvers on internal-layout fields.
+//
+// Every field is seen as Nv contiguous segments (one per right-hand side) of
+// n = NSC * vol complex numbers of its storage type, which holds for all
+// internal layouts because the right-hand-side index is the slowest one.
+// Arithmetic is FP32 for FP32/BF16/FP16 storage and FP64 for FP64 storage;
+// every norm and dot product is accumulated in FP64: per-thread sums, warp
+// shuffles, one partial per block, then a second kernel that adds the
+// partials of each right-hand side in a fixed order (deterministic).
+#include "dirac_blas.h"
+
+namespace dirac {
+
+constexpr int BT = 256;   // threads per block of the vector kernels
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block sum of v written to part[v_index * nblk + blockIdx.x]
+__device__ __forceinline__ void block_partial(double v, double* part, size_t slot)
+{
+    __shared__ double sh[BT / 32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < (BT / 32) ? sh[lane] : 0.0;
+        v = warp_sum(v);
+        if (lane == 0) part[slot] = v;
+    }
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ part, int nblk, double* out, int accumulate)
+{
+    const int v = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += BT) s += part[(size_t)v * nblk + i];
+    __shared__ double sh[BT / 32];
+    s = warp_sum(s);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = s;
+    __syncthreads();
+    if (w == 0) {
+        s = lane < (BT / 32) ? sh[lane] : 0.0;
+        s = warp_sum(s);
+        if (lane == 0) out[v] = accumulate ? out[v] + s : s;
+    }
+}
+
+int blas_blocks(size_t n)
+{
+    size_t b = (n + (size_t)BT * 4 - 1) / ((size_t)BT * 4);
+    if (b > 1024) b = 1024;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+size_t blas_partials(size_t n, int Nv) { return (size_t)blas_blocks(n) * Nv; }
+
+template <typename A> __device__ __forceinline__ double norm2c(cx<A> c)
+{
+    return (double)c.re * (double)c.re + (double)c.im * (double)c.im;
+}
+
+// ---------------------------------------------------------------- norms
+template <typename T>
+__global__ void k_norm2(size_t n, const void* __restrict__ x, double* part)
+{
+    const int v = blockIdx.y;
+    const size_t base = (size_t)v * n;
+    double s = 0.0;
+    for (size_t i = (size_t)blockIdx.x * BT + threadIdx.x; i < n; i += (size_t)gridDim.x * BT)
+        s += norm2c(ld_one<T>(x, base + i));
+    block_partial(s, part, (size_t)v * gridDim.x + blockIdx.x);
+}
+
+// re <x, y> and im <x, y> = sum conj(x) y
+template <typename T>
+__global__ void k_dot(size_t n, const void* __restrict__ x, const void* __restrict__ y, double* part_re,
+                      double* part_im)
+{
+    const int v = blockIdx.y;
+    const size_t base = (size_t)v * n;
+    double sr = 0.0, si = 0.0;
+    for (size_t i = (size_t)blockIdx.x * BT + threadIdx.x; i < n; i += (size_t)gridDim.x * BT) {
+        auto a = ld_one<T>(x, base + i);
+        auto b = ld_one<T>(y, base + i);
+        sr += (double)a.re * b.re + (double)a.im * b.im;
+        si += (double)a.re * b.im - (double)a.im * b.re;
+    }
+    block_partial(sr, part_re, (size_t)v * gridDim.x + blockIdx.x);
+    __syncthreads();
+    block_partial(si, part_im, (size_t)v * gridDim.x + blockIdx.x);
+}
+
+// ---------------------------------------------------------------- CGLS steps
+// e += alpha_v p ;  r -= alpha_v t ;  partial |r|^2
+template <typename T>
+__global__ void k_cgls_step(size_t n, const double* __restrict__ alpha, void* e, const void* __restrict__ p,
+                            void* r, const void* __restrict__ t, double* part)
+{
+    using A = typename Store<T>::A;
+    const int v = blockIdx.y;
+    const size_t base = (size_t)v * n;
+    const A a = (A)alpha[v];
+    double s = 0.0;
+    for (size_t i = (size_t)blockIdx.x * BT + threadIdx.x; i < n; i += (size_t)gridDim.x * BT) {
+        cx<A> ev = ld_one<T>(e, base + i), pv = ld_one<T>(p, base + i);
+        cx<A> rv = ld_one<T>(r, base + i), tv = ld_one<T>(t, base + i);
+        ev.re = fma(a, pv.re, ev.re);
+        ev.im = fma(a, pv.im, ev.im);
+        rv.re = fma(-a, tv.re, rv.re);
+        rv.im = fma(-a, tv.im, rv.im);
+        st_one<T>(e, base + i, ev);
+        st_one<T>(r, base + i, rv);
+        s += norm2c(rv);
+    }
+    block_partial(s, part, (size_t)v * gridDim.x + blockIdx.x);
+}
+
+// p = s + beta_v p
+template <typename T>
+__global__ void k_xpay(size_t n, const void* __restrict__ s, const double* __restrict__ beta, void* p)
+{
+    using A = typename Store<T>::A;
+    const int v = blockIdx.y;
+    const size_t base = (size_t)v * n;
+    const A b = (A)beta[v];
+    for (size_t i = (size_t)blockIdx.x * BT + threadIdx.x; i < n; i += (size_t)gridDim.x * BT) {
+        cx<A> sv = ld_one<T>(s, base + i), pv = ld_one<T>(p, base + i);
+        pv.re = fma(b, pv.re, sv.re);
+        pv.im = fma(b, pv.im, sv.im);
+        st_one<T>(p, base + i, pv);
+    }
+}
+
+// dst = scale_v * src (any storage types), optional partial |dst|^2
+template <typename TS, typename TD>
+__global__ void k_scale_copy(size_t n, const void* __restrict__ src, const double* __restrict__ scale, void* dst,
+                             double* part)
+{
+    using AD = typename Store<TD>::A;
+    const int v = blockIdx.y;
+    const size_t base = (size_t)v * n;
+    const double c = scale ? scale[v] : 1.0;
+    double s = 0.0;
+    for (size_t i = (size_t)blockIdx.x * BT + threadIdx.x; i < n; i += (size_t)gridDim.x * BT) {
+        auto x = ld_one<TS>(src, base + i);
+        cx<AD> y{(AD)(c * (double)x.re), (AD)(c * (double)x.im)};
+        st_one<TD>(dst, base + i, y);
+        s += norm2c(y);
+    }
+    if (part) block_partial(s, part, (size_t)v * gridDim.x + blockIdx.x);
+}
+
+// x64 += coef_v * e  (e in storage type T, x in FP64)
+template <typename T>
+__global__ void k_axpy_to64(size_t n, const double* __restrict__ coef, const void* __restrict__ e, void* x64)
+{
+    const int v = blockIdx.y;
+    const size_t base = (size_t)v * n;
+    const double c = coef[v];
+    if (c == 0.0) return;
+    for (size_t i = (size_t)blockIdx.x * BT + threadIdx.x; i < n; i += (size_t)gridDim.x * BT) {
+        auto ev = ld_one<T>(e, base + i);
+        cx<double> xv = ld_one<double>(x64, base + i);
+        xv.re = fma(c, (double)ev.re, xv.re);
+        xv.im = fma(c, (double)ev.im, xv.im);
+        st_one<double>(x64, base + i, xv);
+    }
+}
+
+// r64 = b64 - a64, partial |r|^2 (FP64 fields)
+__global__ void k_residual64(size_t n, const void* __restrict__ b, const void* __restrict__ a, void* r,
+                             double* part)
+{
+    const int v = blockIdx.y;
+    const size_t base = (size_t)v * n;
+    double s = 0.0;
+    for (size_t i = (size_t)blockIdx.x * BT + threadIdx.x; i < n; i += (size_t)gridDim.x * BT) {
+        cx<double> bv = ld_one<double>(b, base + i), av = ld_one<double>(a, base + i);
+        cx<double> rv{bv.re - av.re, bv.im - av.im};
+        st_one<double>(r, base + i, rv);
+        s += rv.re * rv.re + rv.im * rv.im;
+    }
+    block_partial(s, part, (size_t)v * gridDim.x + blockIdx.x);
+}
+
+// ---------------------------------------------------------------- launchers
+#define PREC_SWITCH(prec, FN)                                  \
+    switch (prec) {                                            \
+    case P_F64: FN(double); break;                             \
+    case P_F32: FN(float); break;                              \
+    case P_BF16: FN(__nv_bfloat16); break;                     \
+    case P_F16: FN(__half); break;                             \
+    default: return cudaErrorInvalidValue;                     \
+    }
+
+static dim3 grid_of(size_t n, int Nv) { return dim3((unsigned)blas_blocks(n), (unsigned)Nv); }
+
+cudaError_t blas_norm2(int prec, size_t n, int Nv, const void* x, double* part, double* out,
+                       cudaStream_t st)
+{
+    dim3 g = grid_of(n, Nv);
+#define GO(T) k_norm2<T><<<g, BT, 0, st>>>(n, x, part)
+    PREC_SWITCH(prec, GO)
+#undef GO
+    k_reduce_partials<<<Nv, BT, 0, st>>>(part, g.x, out, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t blas_dot(int prec, size_t n, int Nv, const void* x, const void* y, double* part,
+                     double* out_re, double* out_im, cudaStream_t st)
+{
+    dim3 g = grid_of(n, Nv);
+    double* part_im = part + (size_t)g.x * Nv;
+#define GO(T) k_dot<T><<<g, BT, 0, st>>>(n, x, y, part, part_im)
+    PREC_SWITCH(prec, GO)
+#undef GO
+    k_reduce_partials<<<Nv, BT, 0, st>>>(part, g.x, out_re, 0);
+    k_reduce_partials<<<Nv, BT, 0, st>>>(part_im, g.x, out_im, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t blas_cgls_step(int prec, size_t n, int Nv, const double* alpha, void* e, const void* p, void* r,
+                           const void* t, double* part, double* rr, cudaStream_t st)
+{
+    dim3 g = grid_of(n, Nv);
+#define GO(T) k_cgls_step<T><<<g, BT, 0, st>>>(n, alpha, e, p, r, t, part)
+    PREC_SWITCH(prec, GO)
+#undef GO
+    k_reduce_partials<<<Nv, BT, 0, st>>>(part, g.x, rr, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t blas_xpay(int prec, size_t n, int Nv, const void* s, const double* beta, void* p, cudaStream_t st)
+{
+    dim3 g = grid_of(n, Nv);
+#define GO(T) k_xpay<T><<<g, BT, 0, st>>>(n, s, beta, p)
+    PREC_SWITCH(prec, GO)
+#undef GO
+    return cudaGetLastError();
+}
+
+template <typename TS>
+static cudaError_t scale_copy_from(int dprec, dim3 g, size_t n, const void* src, const double* scale, void* dst,
+                                   double* part, cudaStream_t st)
+{
+#define GO(T) k_scale_copy<TS, T><<<g, BT, 0, st>>>(n, src, scale, dst, part)
+    switch (dprec) {
+    case P_F64: GO(double); break;
+    case P_F32: GO(float); break;
+    case P_BF16: GO(__nv_bfloat16); break;
+    case P_F16: GO(__half); break;
+    default: return cudaErrorInvalidValue;
+    }
+#undef GO
+    return cudaGetLastError();
+}
+
+cudaError_t blas_scale_copy(int sprec, int dprec, size_t n, int Nv, const void* src, const double* scale,
+                            void* dst, double* part, double* nrm2, cudaStream_t st)
+{
+    dim3 g = grid_of(n, Nv);
+    cudaError_t e;
+    switch (sprec) {
+    case P_F64: e = scale_copy_from<double>(dprec, g, n, src, scale, dst, part, st); break;
+    case P_F32: e = scale_copy_from<float>(dprec, g, n, src, scale, dst, part, st); break;
+    case P_BF16: e = scale_copy_from<__nv_bfloat16>(dprec, g, n, src, scale, dst, part, st); break;
+    case P_F16: e = scale_copy_from<__half>(dprec, g, n, src, scale, dst, part, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    if (part && nrm2) k_reduce_partials<<<Nv, BT, 0, st>>>(part, g.x, nrm2, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t blas_axpy_to64(int prec, size_t n, int Nv, const double* coef, const void* e, void* x64,
+                           cudaStream_t st)
+{
+    dim3 g = grid_of(n, Nv);
+#define GO(T) k_axpy_to64<T><<<g, BT, 0, st>>>(n, coef, e, x64)
+    PREC_SWITCH(prec, GO)
+#undef GO
+    return cudaGetLastError();
+}
+
+cudaError_t blas_residual64(size_t n, int Nv, const void* b, const void* a, void* r, double* part, double* rr,
+                            cudaStream_t st)
+{
+    dim3 g = grid_of(n, Nv);
+    k_residual64<<<g, BT, 0, st>>>(n, b, a, r, part);
+    k_reduce_partials<<<Nv, BT, 0, st>>>(part, g.x, rr, 0);
+    return cudaGetLastError();
+}
+
+}  // namespace dirac
