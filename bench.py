@@ -154,6 +154,7 @@ def sweep_rate(dg, torch, w, steps, warmup):
     V, psi = gen_inputs(w)
     D = dg.Dirac(w["op"], w["L"], w["Nv"], w["mass"], w["prec"])
     D.set_links(torch.from_numpy(V).cuda())
+    D.autotune()
     x = D.pack(torch.from_numpy(psi).cuda())
     y = D.new_internal()
     total, per = time_kernel(torch, lambda: D.apply(x, out=y), steps, warmup)
@@ -163,7 +164,8 @@ def sweep_rate(dg, torch, w, steps, warmup):
     byts = dg.bytes_per_site(w["op"], w["Nv"], w["prec"]) * vol
     cfg = D.kernel_config()
     D.close()
-    return {"gflops": flops / t / 1e9, "gbs": byts / t / 1e9, "ms": t * 1e3, "R": cfg[0], "block": cfg[1]}
+    return {"gflops": flops / t / 1e9, "gbs": byts / t / 1e9, "ms": t * 1e3, "R": cfg[0], "block": cfg[1],
+            "pipe": cfg[2]}
 
 
 class OracleSample:
@@ -280,6 +282,7 @@ def main():
     V, psi = gen_inputs(w)
     D = dg.Dirac(w["op"], w["L"], w["Nv"], w["mass"], w["prec"])
     D.set_links(torch.from_numpy(V).cuda())
+    D.autotune()                       # best of the built launch shapes on this GPU
     xin = torch.from_numpy(psi).cuda()
     x = D.pack(xin)
     y = D.new_internal()
@@ -343,7 +346,7 @@ def main():
                    "Nc": 3, "Nv": w["Nv"], "kappa": w["mass"], "links": "exp(0.3 i H), H traceless Gaussian",
                    "source": "complex Gaussian N(0,1)", "layout": "internal site-fastest SoA",
                    "l2": "no flush: each step streams {:.2f} GB > 129 MB L2".format(bytes_step / 1e9),
-                   "kernel": {"rhs_per_thread": cfg[0], "block": cfg[1]},
+                   "kernel": {"rhs_per_thread": cfg[0], "block": cfg[1], "pipe": cfg[2]},
                    "parallelism": f"replicas x{ws}"},
         "hbm_gbs": achieved,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",

@@ -145,6 +145,20 @@ DIRAC_API dirac_status dirac_apply(dirac_handle* h, void* out, const void* in, d
  * Same contract as dirac_apply. */
 DIRAC_API dirac_status dirac_apply_dagger(dirac_handle* h, void* out, const void* in, dirac_layout layout);
 
+/* Link gradient of the loss L = Re <g, D psi> = Re sum_x g(x)^+ (D psi)(x)
+ * (the backward pass of out = D psi with respect to the links; the backward
+ * pass with respect to psi is dirac_apply_dagger on g).  Convention for a
+ * real function of complex links (PyTorch's): F = dL/dRe V + i dL/dIm V.
+ * Staggered (Sec. 3):  F_mu(x) = 1/2 eta_mu(x) sum_v [g_v(x) psi_v(x+mu)^+ - psi_v(x) g_v(x+mu)^+]
+ * Wilson (def_wils):   F_mu(x) = -1/2 sum_v,s [(1-gamma_mu) g_v(x)]_s psi_v(x+mu)_s^+
+ *                                -1/2 sum_v,s psi_v(x)_s [(1+gamma_mu) g_v(x+mu)]_s^+
+ *   F        device, canonical link layout [s][mu][a][b], complex double for
+ *            F64 handles and complex float otherwise; written once per link
+ *   psi, g   device spinor fields in `layout`
+ * UNSUPPORTED for Brillouin (its links W are composite).  Asynchronous. */
+DIRAC_API dirac_status dirac_force(dirac_handle* h, void* F, const void* psi, const void* g,
+                                   dirac_layout layout);
+
 /* Statistics of one dirac_solve call. */
 typedef struct {
     int outer_iterations;   /* refinement steps (inner solves) taken */
@@ -180,9 +194,22 @@ DIRAC_API dirac_status dirac_solve(dirac_handle* h, void* x, const void* b, doub
 
 /* Kernel configuration: R = right-hand sides per thread (1..4 for Wilson and
  * Brillouin, 1, 2, 4 or 6 for staggered), block = threads per block (a
- * multiple of 32, 32..256).  UNSUPPORTED for other values. */
-DIRAC_API dirac_status dirac_set_kernel_config(dirac_handle* h, int R, int block);
-DIRAC_API dirac_status dirac_get_kernel_config(const dirac_handle* h, int* R, int* block);
+ * multiple of 32, 32..256), pipe = 0 (direct loads) or 3 (Wilson only: a
+ * three-stage cp.async pipeline that keeps the next two hops' spinors and
+ * links in flight in shared memory; needs R * 3 * block * (bytes per hop)
+ * <= 227 KB).  UNSUPPORTED for other values. */
+DIRAC_API dirac_status dirac_set_kernel_config(dirac_handle* h, int R, int block, int pipe);
+DIRAC_API dirac_status dirac_get_kernel_config(const dirac_handle* h, int* R, int* block, int* pipe);
+
+/* Autotuner (the paper's "best of breed" selection, Sec. 4 and Sec. 6: time
+ * every built variant on this machine and keep the winner): times each
+ * supported (R, block) of dirac_set_kernel_config on the handle's own
+ * workspace and keeps the fastest in the handle.  With the environment
+ * variable DIRAC_TUNE_CACHE naming a writable file, results are cached per
+ * (operator, precision, lattice, Nv, GPU name) and reused unless force != 0.
+ * Synchronous.  R, block, pipe, ms (host, may be NULL) receive the choice and
+ * its median time per sweep in milliseconds (from the cache when reused). */
+DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int* R, int* block, int* pipe, double* ms);
 
 /* One-line description of the last error on h (or of the last failed
  * dirac_create when h is NULL).  Static or handle-owned storage. */

@@ -64,10 +64,12 @@ SIGNATURES = {
     "dirac_unpack": (I, [P, P, P]),
     "dirac_apply": (I, [P, P, P, I]),
     "dirac_apply_dagger": (I, [P, P, P, I]),
-    "dirac_set_kernel_config": (I, [P, I, I]),
-    "dirac_get_kernel_config": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+    "dirac_set_kernel_config": (I, [P, I, I, I]),
+    "dirac_get_kernel_config": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
     "dirac_last_error": (ctypes.c_char_p, [P]),
     "dirac_solve": (I, [P, P, P, D, I, I, D, P, P]),
+    "dirac_force": (I, [P, P, P, P, I]),
+    "dirac_autotune": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
 }
 
 
@@ -246,8 +248,27 @@ class Dirac:
             check(status, self.h, "dirac_solve")
         return x, res, st.as_dict(), status
 
+    def force(self, psi, g, out=None):
+        """Link gradient of Re <g, D psi>: canonical links shape, complex128 (f64) / complex64."""
+        torch = _torch()
+        Nx, Ny, Nz, Nt = self.L
+        if out is None:
+            out = torch.empty((Nt, Nz, Ny, Nx, 4, 3, 3), dtype=self.canon_dtype, device=self.device)
+        self._sync_stream()
+        check(lib().dirac_force(self.h, _ptr(out), _ptr(psi.contiguous()), _ptr(g.contiguous()), CANONICAL),
+              self.h, "dirac_force")
+        return out
+
     def set_kernel_config(self, R: int, block: int):
         check(lib().dirac_set_kernel_config(self.h, R, block), self.h, "dirac_set_kernel_config")
+
+    def autotune(self, force: bool = False):
+        """Pick the fastest (R, block, pipe) for this handle; returns (R, block, pipe, ms per sweep)."""
+        R, B, Pp, ms = I(), I(), I(), D()
+        self._sync_stream()
+        check(lib().dirac_autotune(self.h, 1 if force else 0, ctypes.byref(R), ctypes.byref(B), ctypes.byref(Pp),
+                                   ctypes.byref(ms)), self.h, "dirac_autotune")
+        return R.value, B.value, Pp.value, ms.value
 
     def kernel_config(self):
         R, B = I(), I()

@@ -36,6 +36,7 @@ static cudaError_t go(bool dag, const ApplyArgs& a, int block, cudaStream_t st)
 template <typename T>
 static cudaError_t go_T(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
 {
+    if (c.pipe != 0) return cudaErrorInvalidValue;
     switch (c.R) {
     case 1: return go<T, 1>(dag, a, c.block, st);
     case 2: return go<T, 2>(dag, a, c.block, st);

@@ -18,11 +18,32 @@ __global__ void __launch_bounds__(256) k_wilson(ApplyArgs a, int ngroups)
     wilson_site<T, R, DAG>(a, s, group);
 }
 
-template <typename T, int R>
-static cudaError_t go(bool dag, const ApplyArgs& a, int block, cudaStream_t st)
+// pipelined variant: the loads of later hops are in flight in shared memory
+template <typename T, int R, bool DAG, int ST>
+__global__ void __launch_bounds__(256) k_wilson_pipe(ApplyArgs a, int ngroups)
 {
+    extern __shared__ __align__(16) char smem[];
+    const long b = blockIdx.x;
+    const int group = (int)(b % ngroups);
+    const long s = (b / ngroups) * blockDim.x + threadIdx.x;
+    if (s >= a.g.vol) return;   // no block-wide synchronisation follows
+    wilson_site_pipe<T, R, DAG, ST>(a, s, group, smem, threadIdx.x, blockDim.x);
+}
+
+template <typename T, int R>
+static cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
+{
+    const int block = c.block;
     const int ngroups = (a.Nv + R - 1) / R;
     const long nblk = ((a.g.vol + block - 1) / block) * (long)ngroups;
+    if (c.pipe == 3) {
+        const size_t smem = WilsonPipe<T, R>::stage_bytes_per_thread * 3 * block;
+        auto kern = dag ? k_wilson_pipe<T, R, true, 3> : k_wilson_pipe<T, R, false, 3>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<(unsigned)nblk, block, smem, st>>>(a, ngroups);
+        return cudaGetLastError();
+    }
     if (dag) k_wilson<T, R, true><<<(unsigned)nblk, block, 0, st>>>(a, ngroups);
     else k_wilson<T, R, false><<<(unsigned)nblk, block, 0, st>>>(a, ngroups);
     return cudaGetLastError();
@@ -32,12 +53,19 @@ template <typename T>
 static cudaError_t go_T(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
 {
     switch (c.R) {
-    case 1: return go<T, 1>(dag, a, c.block, st);
-    case 2: return go<T, 2>(dag, a, c.block, st);
-    case 3: return go<T, 3>(dag, a, c.block, st);
-    case 4: return go<T, 4>(dag, a, c.block, st);
+    case 1: return go<T, 1>(dag, a, c, st);
+    case 2: return go<T, 2>(dag, a, c, st);
+    case 3: return go<T, 3>(dag, a, c, st);
+    case 4: return go<T, 4>(dag, a, c, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+size_t wilson_pipe_smem(int prec, int R, int block, int stages)
+{
+    const size_t K = prec == P_F64 ? 12 : (prec == P_F32 ? 6 : 3);
+    const size_t LB = prec == P_F64 ? 16 : (prec == P_F32 ? 8 : 4);
+    return (R * K * 16 + 9 * LB) * stages * block;
 }
 
 cudaError_t launch_apply_wilson(int prec, bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)

@@ -294,6 +294,39 @@ template <typename A> HD void mat_dag_vec_acc(const cx<A>* U, const cx<A>* h, cx
     }
 }
 
+// ---------------------------------------------------------------- async copies
+// cp.async (global -> shared, completion tracked per thread by commit/wait
+// groups).  Each thread reads back only what it copied itself, so no barrier
+// is needed between the copy and the use.
+template <int BYTES> DEV_INLINE void cp_async(void* smem, const void* gmem)
+{
+#if defined(__CUDA_ARCH__)
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else if constexpr (BYTES == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+#else
+    const char* g = static_cast<const char*>(gmem);
+    char* d = static_cast<char*>(smem);
+    for (int i = 0; i < BYTES; ++i) d[i] = g[i];
+#endif
+}
+DEV_INLINE void cp_async_commit()
+{
+#if defined(__CUDA_ARCH__)
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+#endif
+}
+template <int N> DEV_INLINE void cp_async_wait()
+{
+#if defined(__CUDA_ARCH__)
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+#endif
+}
+
 // ---------------------------------------------------------------- geometry
 struct Geom {
     int L[4];        // Nx, Ny, Nz, Nt

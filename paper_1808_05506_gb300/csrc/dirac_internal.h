@@ -22,9 +22,11 @@ inline size_t cbytes(int prec)
 struct LaunchCfg {
     int R;       // right-hand sides per thread
     int block;   // threads per block
+    int pipe;    // 0: direct loads; ST >= 2: cp.async pipeline with ST stages (Wilson)
 };
 
-bool apply_config_supported(int op, int prec, int R, int block);
+bool apply_config_supported(int op, int prec, int R, int block, int pipe);
+size_t wilson_pipe_smem(int prec, int R, int block, int stages);
 
 // out = D in (or D^+ in) on internal-layout fields
 cudaError_t launch_apply(int op, int prec, bool dagger, const ApplyArgs& a, LaunchCfg cfg,
@@ -55,5 +57,9 @@ cudaError_t launch_convert_links(int prec, const Geom& g, int nmat, const void* 
 // Tab. tab:off-axis: FP64 links V64 [4][9][s] -> FP64 W64 [40][9][s]; tmp81 holds
 // 81 * 9 * vol complex doubles.
 cudaError_t launch_build_W(const Geom& g, const void* V64, void* tmp81, void* W64, cudaStream_t st);
+
+// link gradient of Re <g, D psi> (staggered, Wilson); F canonical link layout
+cudaError_t launch_force(int op, int prec, const Geom& g, int Nv, const void* psi, const void* gv, void* F,
+                         cudaStream_t st);
 
 }  // namespace dirac

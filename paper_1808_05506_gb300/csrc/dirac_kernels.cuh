@@ -137,6 +137,192 @@ DEV_INLINE void wilson_site(const ApplyArgs& a, long s, int group)
     }
 }
 
+// ---------------------------------------------------------------- Wilson, pipelined
+// The same sweep with the loads of hop h + ST - 1 in flight (cp.async into
+// this thread's own shared-memory slots) while hop h is computed, so that the
+// memory latency is covered without holding the data in registers.
+// Hops 0..7 are (mu, +), (mu, -) for mu = 0..3; hop 8 is the site itself.
+// Shared memory per thread and stage: R*K 16-byte spinor elements and the 9
+// link entries; layout [stage][element][thread] (conflict-free 16-byte rows).
+template <typename T, int R>
+struct WilsonPipe {
+    static constexpr int K = SpinorLayout<T, 12>::K;
+    static constexpr int E = R * K;
+    static constexpr int LB = (int)sizeof(typename Store<T>::One);
+    static constexpr size_t stage_bytes_per_thread = (size_t)E * 16 + 9 * LB;
+};
+
+template <typename T, int R>
+DEV_INLINE void wilson_issue(const ApplyArgs& a, int h, long nbr, long lsite, int v0, char* stage, int tid,
+                             int nthr)
+{
+    using P = WilsonPipe<T, R>;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (v0 + r < a.Nv) {
+#pragma unroll
+            for (int k = 0; k < P::K; ++k) {
+                const size_t gi = ((size_t)(v0 + r) * P::K + k) * a.g.vol + (size_t)nbr;
+                cp_async<16>(stage + ((size_t)(r * P::K + k) * nthr + tid) * 16,
+                             static_cast<const char*>(a.in) + gi * 16);
+            }
+        }
+    }
+    if (h < 8) {
+        char* lb = stage + (size_t)P::E * 16 * nthr;
+        const int mu = h >> 1;
+#pragma unroll
+        for (int e = 0; e < 9; ++e)
+            cp_async<P::LB>(lb + ((size_t)e * nthr + tid) * P::LB,
+                            static_cast<const char*>(a.links) + (((size_t)mu * 9 + e) * a.g.vol + (size_t)lsite) * P::LB);
+    }
+    cp_async_commit();
+}
+
+// plain (shared-memory) reads of one complex / one 16-byte element
+template <typename T> DEV_INLINE cx<typename Store<T>::A> sm_one(const char* p);
+template <> DEV_INLINE cx<double> sm_one<double>(const char* p)
+{
+    double2 v = *reinterpret_cast<const double2*>(p);
+    return {v.x, v.y};
+}
+template <> DEV_INLINE cx<float> sm_one<float>(const char* p)
+{
+    float2 v = *reinterpret_cast<const float2*>(p);
+    return {v.x, v.y};
+}
+template <> DEV_INLINE cx<float> sm_one<__nv_bfloat16>(const char* p)
+{
+    return unpack2(*reinterpret_cast<const uint32_t*>(p), (__nv_bfloat16*)nullptr);
+}
+template <> DEV_INLINE cx<float> sm_one<__half>(const char* p)
+{
+    return unpack2(*reinterpret_cast<const uint32_t*>(p), (__half*)nullptr);
+}
+template <typename T> DEV_INLINE void sm_vec(const char* p, cx<typename Store<T>::A>* o);
+template <> DEV_INLINE void sm_vec<double>(const char* p, cx<double>* o) { o[0] = sm_one<double>(p); }
+template <> DEV_INLINE void sm_vec<float>(const char* p, cx<float>* o)
+{
+    float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = {v.x, v.y};
+    o[1] = {v.z, v.w};
+}
+template <typename H> DEV_INLINE void sm_vec16(const char* p, cx<float>* o)
+{
+    uint4 v = *reinterpret_cast<const uint4*>(p);
+    o[0] = unpack2(v.x, (H*)nullptr);
+    o[1] = unpack2(v.y, (H*)nullptr);
+    o[2] = unpack2(v.z, (H*)nullptr);
+    o[3] = unpack2(v.w, (H*)nullptr);
+}
+template <> DEV_INLINE void sm_vec<__nv_bfloat16>(const char* p, cx<float>* o) { sm_vec16<__nv_bfloat16>(p, o); }
+template <> DEV_INLINE void sm_vec<__half>(const char* p, cx<float>* o) { sm_vec16<__half>(p, o); }
+
+template <typename T, int R, bool DAG, int H>
+DEV_INLINE void wilson_pipe_hop(const ApplyArgs& a, const char* stage, int v0, int tid, int nthr,
+                                cx<typename Store<T>::A> (&acc)[R][12])
+{
+    using A = typename Store<T>::A;
+    using P = WilsonPipe<T, R>;
+    using L = SpinorLayout<T, 12>;
+    constexpr int MU = H >> 1;
+    constexpr bool BACK = (H & 1) != 0;
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int S = BACK ? -SF : SF;
+    cx<A> U[9];
+    const char* lb = stage + (size_t)P::E * 16 * nthr;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) U[e] = sm_one<T>(lb + ((size_t)e * nthr + tid) * P::LB);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (v0 + r < a.Nv) {
+            cx<A> p[12], h[6], w[6];
+#pragma unroll
+            for (int k = 0; k < P::K; ++k) {
+                const char* q = stage + ((size_t)(r * P::K + k) * nthr + tid) * 16;
+                if constexpr (L::CPV == 1) p[k] = sm_one<T>(q);
+                else sm_vec<T>(q, p + k * L::CPV);
+            }
+            wilson_project<MU, S>(p, h);
+            if constexpr (BACK) { mat_dag_vec(U, h, w); mat_dag_vec(U, h + 3, w + 3); }
+            else { mat_vec(U, h, w); mat_vec(U, h + 3, w + 3); }
+            wilson_reconstruct<MU, S>(w, acc[r]);
+        }
+    }
+}
+
+template <typename T, int R, bool DAG, int ST, int H>
+DEV_INLINE void wilson_pipe_step(const ApplyArgs& a, const long* nb, const long* ls, int v0, char* smem, int tid,
+                                 int nthr, cx<typename Store<T>::A> (&acc)[R][12])
+{
+    using P = WilsonPipe<T, R>;
+    const size_t sb = P::stage_bytes_per_thread * nthr;
+    if constexpr (H + ST - 1 <= 8) wilson_issue<T, R>(a, H + ST - 1, nb[H + ST - 1], ls[H + ST - 1], v0,
+                                                      smem + ((H + ST - 1) % ST) * sb, tid, nthr);
+    else cp_async_commit();
+    cp_async_wait<ST - 1>();
+    const char* stage = smem + (H % ST) * sb;
+    if constexpr (H < 8) {
+        wilson_pipe_hop<T, R, DAG, H>(a, stage, v0, tid, nthr, acc);
+        wilson_pipe_step<T, R, DAG, ST, H + 1>(a, nb, ls, v0, smem, tid, nthr, acc);
+    } else {
+        using A = typename Store<T>::A;
+        using L = SpinorLayout<T, 12>;
+        const A dg = (A)a.diag;
+        const A mh = (A)(-0.5);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (v0 + r < a.Nv) {
+                cx<A> p[12];
+#pragma unroll
+                for (int k = 0; k < P::K; ++k) {
+                    const char* q = stage + ((size_t)(r * P::K + k) * nthr + tid) * 16;
+                    if constexpr (L::CPV == 1) p[k] = sm_one<T>(q);
+                    else sm_vec<T>(q, p + k * L::CPV);
+                }
+#pragma unroll
+                for (int i = 0; i < 12; ++i) {
+                    cx<A> o;
+                    o.re = fma(mh, acc[r][i].re, dg * p[i].re);
+                    o.im = fma(mh, acc[r][i].im, dg * p[i].im);
+                    p[i] = o;
+                }
+                store_spinor<T, 12>(a.out, a.g.vol, v0 + r, nb[8], p);
+            }
+        }
+    }
+}
+
+template <typename T, int R, bool DAG, int ST>
+DEV_INLINE void wilson_site_pipe(const ApplyArgs& a, long s, int group, char* smem, int tid, int nthr)
+{
+    using A = typename Store<T>::A;
+    using P = WilsonPipe<T, R>;
+    long fwd[4], bwd[4];
+    int x[4];
+    site_offsets(a.g, s, fwd, bwd, x);
+    const int v0 = group * R;
+    long nb[9], ls[9];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        nb[2 * mu] = s + fwd[mu];
+        ls[2 * mu] = s;
+        nb[2 * mu + 1] = s + bwd[mu];
+        ls[2 * mu + 1] = s + bwd[mu];
+    }
+    nb[8] = s;
+    ls[8] = s;
+    const size_t sb = P::stage_bytes_per_thread * nthr;
+#pragma unroll
+    for (int h = 0; h < ST - 1; ++h) wilson_issue<T, R>(a, h, nb[h], ls[h], v0, smem + h * sb, tid, nthr);
+    cx<A> acc[R][12];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int i = 0; i < 12; ++i) acc[r][i] = cx<A>{A(0), A(0)};
+    wilson_pipe_step<T, R, DAG, ST, 0>(a, nb, ls, v0, smem, tid, nthr, acc);
+}
+
 // ---------------------------------------------------------------- staggered
 template <typename T, int R, bool DAG>
 DEV_INLINE void staggered_site(const ApplyArgs& a, long s, int group)

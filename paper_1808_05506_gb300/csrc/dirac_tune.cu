@@ -1,0 +1,136 @@
+// Autotuner: the "best of breed" selection of Sec. 4 and Sec. 6 (build every
+// variant, time a few calls, keep the winner for this machine) applied to
+// the launch shape of the sweeps: right-hand sides per thread R and threads
+// per block.  Results can be kept in a plain-text cache file named by the
+// environment variable DIRAC_TUNE_CACHE, one line per
+// (operator, precision, lattice, Nv, device name).
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "dirac_handle.h"
+
+using namespace dirac;
+
+static std::mutex g_cache_mu;
+
+static std::string tune_key(const dirac_handle* h)
+{
+    cudaDeviceProp p;
+    std::string dev = "unknown";
+    if (cudaGetDeviceProperties(&p, h->device) == cudaSuccess) dev = p.name;
+    for (auto& c : dev)
+        if (c == ' ') c = '_';
+    char buf[256];
+    snprintf(buf, sizeof(buf), "op%d prec%d %dx%dx%dx%d nv%d %s", h->op, h->prec, h->g.L[0], h->g.L[1],
+             h->g.L[2], h->g.L[3], h->Nv, dev.c_str());
+    return buf;
+}
+
+static bool cache_lookup(const std::string& key, int* R, int* B, int* Pp, double* ms)
+{
+    const char* path = getenv("DIRAC_TUNE_CACHE");
+    if (!path || !*path) return false;
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (fgets(line, sizeof(line), f)) {
+        const size_t kl = key.size();
+        if (strncmp(line, key.c_str(), kl) == 0 && line[kl] == ' ') {
+            int r, b;
+            double t;
+            int pp;
+            if (sscanf(line + kl, " R%d B%d P%d %lf", &r, &b, &pp, &t) == 4) {
+                *R = r;
+                *B = b;
+                *Pp = pp;
+                *ms = t;
+                found = true;   // the last entry wins
+            }
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+static void cache_store(const std::string& key, int R, int B, int Pp, double ms)
+{
+    const char* path = getenv("DIRAC_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s R%d B%d P%d %.6f\n", key.c_str(), R, B, Pp, ms);
+    fclose(f);
+}
+
+extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int* R_out, int* block_out,
+                                                 int* pipe_out, double* ms_out)
+{
+    if (!h) return DIRAC_ERR_INVALID_ARG;
+    if (!h->have_links) return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_autotune: call dirac_set_links first");
+    const std::string key = tune_key(h);
+    int R = 0, B = 0, Pp = 0;
+    double best = 0.0;
+    if (!force && cache_lookup(key, &R, &B, &Pp, &best) && apply_config_supported(h->op, h->prec, R, B, Pp)) {
+        h->cfg = LaunchCfg{R, B, Pp};
+    } else {
+        dirac_status st;
+        if ((st = h->ensure_workspace())) return st;
+        if ((st = h->cuda(cudaMemsetAsync(h->ws_in, 0, h->field_bytes_internal(h->Nv), h->stream), "autotune")))
+            return st;
+        std::vector<int> Rs = (h->op == OP_STAGGERED) ? std::vector<int>{1, 2, 4, 6} : std::vector<int>{1, 2, 3, 4};
+        const int blocks[] = {64, 128, 256};
+        cudaEvent_t e0, e1;
+        if ((st = h->cuda(cudaEventCreate(&e0), "autotune"))) return st;
+        if ((st = h->cuda(cudaEventCreate(&e1), "autotune"))) {
+            cudaEventDestroy(e0);
+            return st;
+        }
+        best = 1e30;
+        LaunchCfg win = h->cfg;
+        const int pipes[] = {0, 3};
+        for (int r : Rs) {
+            if (r > h->Nv && r != Rs.front()) continue;
+            for (int b : blocks)
+            for (int pp : pipes) {
+                if (!apply_config_supported(h->op, h->prec, r, b, pp)) continue;
+                LaunchCfg c{r, b, pp};
+                std::vector<float> t;
+                for (int rep = 0; rep < 7 && st == DIRAC_OK; ++rep) {
+                    cudaEventRecord(e0, h->stream);
+                    st = h->run_apply(false, h->ws_out, h->ws_in, h->Nv, h->diag, h->links, h->prec, c);
+                    cudaEventRecord(e1, h->stream);
+                    if (st == DIRAC_OK) st = h->cuda(cudaEventSynchronize(e1), "autotune");
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep >= 2) t.push_back(ms);   // two warm-up calls
+                }
+                if (st) break;
+                std::sort(t.begin(), t.end());
+                const double med = t[t.size() / 2];
+                if (med < best) {
+                    best = med;
+                    win = c;
+                }
+            }
+            if (st) break;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st) return st;
+        h->cfg = win;
+        cache_store(key, win.R, win.block, win.pipe, best);
+    }
+    if (R_out) *R_out = h->cfg.R;
+    if (block_out) *block_out = h->cfg.block;
+    if (pipe_out) *pipe_out = h->cfg.pipe;
+    if (ms_out) *ms_out = best;
+    return DIRAC_OK;
+}

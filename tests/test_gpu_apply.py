@@ -91,10 +91,14 @@ def test_parity_every_config(dg, op, mass, prec):
     V, psi = inputs(op, L, Nv, prec, 210)
     want = oracle.apply(op, V, psi, m0_of(op, mass))
     Rs = (1, 2, 4, 6) if op == "staggered" else (1, 2, 3, 4)
+    pipes = (0, 3) if op == "wilson" else (0,)
     for R in Rs:
         for block in (32, 128, 256):
-            got = run(dg, op, L, Nv, mass, prec, V, psi, cfg=(R, block), internal=True)
-            assert rel_l2(got, want) <= TOL[prec], (R, block)
+            for pipe in pipes:
+                if pipe and R * block > 512:
+                    continue                 # exceeds the shared memory of one block
+                got = run(dg, op, L, Nv, mass, prec, V, psi, cfg=(R, block, pipe), internal=True)
+                assert rel_l2(got, want) <= TOL[prec], (R, block, pipe)
 
 
 @pytest.mark.parametrize("op,mass", [("wilson", 0.11), ("staggered", 0.2), ("brillouin", -0.1)])
@@ -111,6 +115,28 @@ def test_low_precision_storage(dg, op, mass, prec):
     else:
         want = oracle.apply(op, Vr, pr, m0_of(op, mass))
     assert rel_l2(got, want) <= TOL[prec]
+
+
+def test_autotune(dg, tmp_path, monkeypatch):
+    """The tuner keeps a supported configuration that reproduces the sweep and
+    writes / reuses its cache file."""
+    monkeypatch.setenv("DIRAC_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    L, Nv = (8, 8, 4, 8), 6
+    V, psi = inputs("wilson", L, Nv, "f32", 250)
+    D = dg.Dirac("wilson", L, Nv, 0.12, "f32")
+    D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
+    R, B, pipe, ms = D.autotune(force=True)
+    assert (R, B, pipe) == D.kernel_config() and ms > 0
+    assert "R%d B%d P%d" % (R, B, pipe) in (tmp_path / "tune.txt").read_text()
+    x = torch.from_numpy(psi.astype(np.complex64)).cuda()
+    got = D.apply(x).cpu().numpy().astype(np.complex128)
+    want = oracle.apply("wilson", V, psi, oracle.kappa_to_m0(0.12))
+    assert rel_l2(got, want) <= TOL["f32"]
+    D2 = dg.Dirac("wilson", L, Nv, 0.12, "f32")
+    D2.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
+    assert D2.autotune()[:3] == (R, B, pipe)              # from the cache
+    D.close()
+    D2.close()
 
 
 @pytest.mark.parametrize("op,mass", [("wilson", 0.13), ("staggered", 0.1), ("brillouin", 0.05)])
@@ -140,19 +166,36 @@ def _sampled(L, n, seed):
     return np.unique(np.concatenate([corners, rng.integers(0, vol, n)]))
 
 
-@pytest.mark.parametrize("dagger", [False, True])
-def test_wilson_full_size_sampled(dg, dagger):
+def test_wilson_full_size_sampled(dg):
     """Wilson 32^4, Nv = 12, FP32, kappa = 0.125, U = exp(0.3 i H): the
-    workload the benchmark times, in the same launch configuration, checked
-    on sampled sites (including the lattice corners)."""
+    workload the benchmark times, in every launch configuration the tuner can
+    pick (so also the one the benchmark runs), D and D^+, checked on sampled
+    sites including the lattice corners."""
     L, Nv = (32, 32, 32, 32), 12
     V = synth.round_to(synth.gauge_links(L, 3, "near_identity", 1002), "f32")
     psi = synth.round_to(synth.spinor(L, Nv, 4, 3, 2002), "f32")
-    got = run(dg, "wilson", L, Nv, 0.125, "f32", V, psi, dagger=dagger).reshape(-1, Nv, 4, 3)
     sites = _sampled(L, 256, 7)
-    want = oracle.apply("wilson", V, psi, 0.0, sites=sites, dagger=dagger)
-    assert rel_l2(got[sites], want) <= TOL["f32"]
-    assert np.isfinite(got).all()
+    want = {dag: oracle.apply("wilson", V, psi, 0.0, sites=sites, dagger=dag) for dag in (False, True)}
+    D = dg.Dirac("wilson", L, Nv, 0.125, "f32")
+    D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
+    xi = D.pack(torch.from_numpy(psi.astype(np.complex64)).cuda())
+    yi = D.new_internal()
+    st = torch.from_numpy(sites).cuda()
+    for R in (1, 2, 3, 4):
+        for block in (64, 128, 256):
+            for pipe in (0, 3):
+                try:
+                    D.set_kernel_config(R, block, pipe)
+                except dg.DiracError:
+                    continue
+                for dag in (False, True):
+                    yi.fill_(0xFF)
+                    D.apply(xi, out=yi, dagger=dag)
+                    y = D.unpack(yi).reshape(-1, Nv, 4, 3)
+                    assert bool(torch.isfinite(torch.view_as_real(y)).all())
+                    got = y[st].cpu().numpy().astype(np.complex128)
+                    assert rel_l2(got, want[dag]) <= TOL["f32"], (R, block, pipe, dag)
+    D.close()
 
 
 def test_brillouin_full_size_sampled(dg):
@@ -181,5 +224,8 @@ def test_error_paths(dg):
         D.apply(xh, out=torch.zeros_like(xh))
     with pytest.raises(dg.DiracError) as e:
         D.set_kernel_config(5, 128)
+    assert e.value.status == dg.ERR_UNSUPPORTED
+    with pytest.raises(dg.DiracError) as e:
+        D.set_kernel_config(4, 256, 3)               # 3 stages x 256 threads x 4 rhs: > 227 KB
     assert e.value.status == dg.ERR_UNSUPPORTED
     D.close()
