@@ -259,8 +259,8 @@ class Dirac:
               self.h, "dirac_force")
         return out
 
-    def set_kernel_config(self, R: int, block: int):
-        check(lib().dirac_set_kernel_config(self.h, R, block), self.h, "dirac_set_kernel_config")
+    def set_kernel_config(self, R: int, block: int, pipe: int = 0):
+        check(lib().dirac_set_kernel_config(self.h, R, block, pipe), self.h, "dirac_set_kernel_config")
 
     def autotune(self, force: bool = False):
         """Pick the fastest (R, block, pipe) for this handle; returns (R, block, pipe, ms per sweep)."""
@@ -271,10 +271,10 @@ class Dirac:
         return R.value, B.value, Pp.value, ms.value
 
     def kernel_config(self):
-        R, B = I(), I()
-        check(lib().dirac_get_kernel_config(self.h, ctypes.byref(R), ctypes.byref(B)), self.h,
+        R, B, Pp = I(), I(), I()
+        check(lib().dirac_get_kernel_config(self.h, ctypes.byref(R), ctypes.byref(B), ctypes.byref(Pp)), self.h,
               "dirac_get_kernel_config")
-        return R.value, B.value
+        return R.value, B.value, Pp.value
 
 
 # per-site, per-right-hand-side model flop counts at Nc = 3 (complex mult-add = 8,

@@ -102,3 +102,54 @@ def test_flop_model_reproduces_paper_intensity_ratio(dg):
     assert max(ratios) - min(ratios) < 0.15                      # almost invariant in Nv
     # the paper rounds to "a factor 2.5"
     assert abs(ratios[2] - gold["intensity_ratio_brillouin_over_wilson"]["value"]) < 0.2
+
+
+def test_binding_calls_match_the_c_signatures(dg, monkeypatch):
+    """Every Dirac method passes exactly the arguments its C entry point
+    declares (checked against a stand-in library; no device work)."""
+    import torch
+
+    calls = []
+
+    class FakeFn:
+        def __init__(self, name):
+            self.name = name
+
+        def __call__(self, *args):
+            argtypes = dg.SIGNATURES[self.name][1]
+            assert len(args) == len(argtypes), (self.name, len(args), len(argtypes))
+            calls.append(self.name)
+            return dg.OK if dg.SIGNATURES[self.name][0] is ctypes.c_int else b""
+
+    class FakeLib:
+        def __getattr__(self, name):
+            assert name in dg.SIGNATURES, name
+            return FakeFn(name)
+
+    monkeypatch.setattr(dg, "_lib", FakeLib())
+    monkeypatch.setattr(dg, "_stream_ptr", lambda stream=None: ctypes.c_void_p(0))
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    D = dg.Dirac.__new__(dg.Dirac)
+    D.op, D.L, D.Nv, D.mass, D.prec, D.Nc = "wilson", (4, 4, 4, 4), 2, 0.12, "f32", 3
+    D.device = torch.device("cpu")
+    D._stream = None
+    D.h = ctypes.c_void_p(1)
+    D.canon_dtype = torch.complex64
+    x = torch.zeros(D.canonical_shape, dtype=torch.complex64)
+    V = torch.zeros((4, 4, 4, 4, 4, 3, 3), dtype=torch.complex64)
+    D.set_links(V)
+    D.set_mass(0.11)
+    D.field_bytes()
+    D.pack(x, out=torch.zeros(8, dtype=torch.uint8))
+    D.unpack(torch.zeros(8, dtype=torch.uint8), out=x.clone())
+    D.apply(x, out=x.clone())
+    D.apply_dagger(x, out=x.clone())
+    D.force(x, x, out=V.clone())
+    D.set_kernel_config(2, 128, 3)
+    D.kernel_config()
+    D.autotune()
+    D.solve(x.to(torch.complex128), x0=x.to(torch.complex128))
+    D.close()
+    for name in ("dirac_set_links", "dirac_apply", "dirac_apply_dagger", "dirac_force", "dirac_solve",
+                 "dirac_set_kernel_config", "dirac_get_kernel_config", "dirac_autotune", "dirac_destroy"):
+        assert name in calls, name
