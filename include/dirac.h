@@ -192,6 +192,36 @@ DIRAC_API dirac_status dirac_solve(dirac_handle* h, void* x, const void* b, doub
                                    int max_inner, double inner_tol, double* rel_residual,
                                    dirac_solve_stats* stats);
 
+/* Per-system result of dirac_solve_batched. */
+typedef struct {
+    int converged;          /* 1 if every column of the system reached tol */
+    int outer_iterations;   /* refinement steps, max over the system's columns */
+    double residual_max;    /* max over its columns of |b - D x| / |b|, FP64 */
+} dirac_system_stats;
+
+/* Solve nsys systems D(m_i) x_i = b_i that share the handle's gauge field,
+ * each with its own number of right-hand sides Nv_i and mass m_i (same
+ * meaning as in dirac_create: staggered m, Wilson kappa, Brillouin m0), by the
+ * defect correction of dirac_solve.  The handle's Nv is the number of
+ * resident right-hand-side slots: columns of the systems are admitted from a
+ * queue (in system order) into free slots; all resident columns share every
+ * sweep (one launch for all systems, the mass entering as a per-column
+ * diagonal), each has its own scalars and stopping test, and a column is
+ * written back to x_i and its slot refilled as soon as it converges.  Groups
+ * of 8 inner iterations run as one captured CUDA graph.
+ *   Nv_i, mass_i      host arrays of nsys entries
+ *   x_i, b_i          host arrays of nsys device pointers to canonical FP64
+ *                     fields with Nv_i right-hand sides; x_i holds the start
+ *   rel_residual      host array of sum_i Nv_i doubles (system-major) or NULL
+ *   sys_stats         host array of nsys entries or NULL
+ *   stats             host struct (totals) or NULL
+ * Blocks until every column converged or hit max_outer.  Returns DIRAC_OK,
+ * DIRAC_NOT_CONVERGED, DIRAC_BREAKDOWN or an error. */
+DIRAC_API dirac_status dirac_solve_batched(dirac_handle* h, int nsys, const int* Nv_i, const double* mass_i,
+                                           void* const* x_i, const void* const* b_i, double tol, int max_outer,
+                                           int max_inner, double inner_tol, double* rel_residual,
+                                           dirac_system_stats* sys_stats, dirac_solve_stats* stats);
+
 /* Kernel configuration: R = right-hand sides per thread (1..4 for Wilson and
  * Brillouin, 1, 2, 4 or 6 for staggered), block = threads per block (a
  * multiple of 32, 32..256), pipe = 0 (direct loads) or 3 (Wilson only: a

@@ -70,7 +70,14 @@ SIGNATURES = {
     "dirac_solve": (I, [P, P, P, D, I, I, D, P, P]),
     "dirac_force": (I, [P, P, P, P, I]),
     "dirac_autotune": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
+    "dirac_solve_batched": (I, [P, I, P, P, P, P, D, I, I, D, P, P, P]),
 }
+
+
+class SystemStats(ctypes.Structure):
+    """dirac_system_stats of include/dirac.h."""
+    _fields_ = [("converged", ctypes.c_int), ("outer_iterations", ctypes.c_int),
+                ("residual_max", ctypes.c_double)]
 
 
 class SolveStats(ctypes.Structure):
@@ -248,6 +255,37 @@ class Dirac:
             check(status, self.h, "dirac_solve")
         return x, res, st.as_dict(), status
 
+    def solve_batched(self, bs, masses, x0s=None, tol: float = 1e-10, max_outer: int = 30,
+                      max_inner: int = 4000, inner_tol: float | None = None):
+        """Solve the systems D(m_i) x_i = b_i sharing this handle's links; this
+        handle's Nv is the number of resident right-hand-side slots.  bs: list of
+        canonical complex128 device tensors (Nt,Nz,Ny,Nx,Nv_i,...).  Returns
+        (xs, per-column residuals, per-system stats, totals, status)."""
+        import numpy as np
+        torch = _torch()
+        if inner_tol is None:
+            inner_tol = {"f64": 1e-10, "f32": 1e-5, "f16": 2e-3, "bf16": 1e-2}[self.prec]
+        nsys = len(bs)
+        bs = [b.to(torch.complex128).contiguous() for b in bs]
+        xs = [torch.zeros_like(b) for b in bs] if x0s is None else \
+            [x.to(torch.complex128).contiguous().clone() for x in x0s]
+        nv = (ctypes.c_int * nsys)(*[int(b.shape[4]) for b in bs])
+        ms = (ctypes.c_double * nsys)(*[float(m) for m in masses])
+        xp = (ctypes.c_void_p * nsys)(*[x.data_ptr() for x in xs])
+        bp = (ctypes.c_void_p * nsys)(*[b.data_ptr() for b in bs])
+        res = np.zeros(sum(nv), dtype=np.float64)
+        sst = (SystemStats * nsys)()
+        st = SolveStats()
+        self._sync_stream()
+        status = lib().dirac_solve_batched(self.h, nsys, ctypes.cast(nv, P), ctypes.cast(ms, P), ctypes.cast(xp, P),
+                                           ctypes.cast(bp, P), float(tol), int(max_outer), int(max_inner),
+                                           float(inner_tol), res.ctypes.data_as(P), ctypes.cast(sst, P),
+                                           ctypes.byref(st))
+        if status not in (OK, NOT_CONVERGED):
+            check(status, self.h, "dirac_solve_batched")
+        sys_stats = [{k: getattr(x, k) for k, _ in SystemStats._fields_} for x in sst]
+        return xs, res, sys_stats, st.as_dict(), status
+
     def force(self, psi, g, out=None):
         """Link gradient of Re <g, D psi>: canonical links shape, complex128 (f64) / complex64."""
         torch = _torch()
@@ -275,6 +313,16 @@ class Dirac:
         check(lib().dirac_get_kernel_config(self.h, ctypes.byref(R), ctypes.byref(B), ctypes.byref(Pp)), self.h,
               "dirac_get_kernel_config")
         return R.value, B.value, Pp.value
+
+
+def pipe_config_fits(prec: str, R: int, block: int, pipe: int) -> bool:
+    """Whether a pipelined Wilson launch shape fits the 227 KB of shared memory
+    of one block (the rule dirac_set_kernel_config applies)."""
+    if pipe == 0:
+        return True
+    k = {"f64": 12, "f32": 6, "bf16": 3, "f16": 3}[prec]
+    lb = {"f64": 16, "f32": 8, "bf16": 4, "f16": 4}[prec]
+    return (R * k * 16 + 9 * lb) * pipe * block <= 227 * 1024
 
 
 # per-site, per-right-hand-side model flop counts at Nc = 3 (complex mult-add = 8,

@@ -111,14 +111,17 @@ ApplyArgs dirac_handle::args(void* out, const void* in, int nv, double diag_valu
     a.out = out;
     a.links = links;
     a.diag = diag_value;
+    a.diag_v = nullptr;
     return a;
 }
 
 dirac_status dirac_handle::run_apply(bool dagger, void* out, const void* in, int nv,
-                                     double diag_value, const void* link_ptr, int p, LaunchCfg c)
+                                     double diag_value, const void* link_ptr, int p, LaunchCfg c,
+                                     const double* diag_v)
 {
     ApplyArgs a = args(out, in, nv, diag_value);
     a.links = link_ptr;
+    a.diag_v = diag_v;
     return cuda(launch_apply(op, p, dagger, a, c, stream), "apply kernel launch");
 }
 

@@ -48,7 +48,7 @@ struct dirac_handle {
     dirac_status build_W64();
     dirac::ApplyArgs args(void* out, const void* in, int nv, double diag_value) const;
     dirac_status run_apply(bool dagger, void* out, const void* in, int nv, double diag_value,
-                           const void* link_ptr, int p, dirac::LaunchCfg c);
+                           const void* link_ptr, int p, dirac::LaunchCfg c, const double* diag_v = nullptr);
     void free_solver_workspace();
 };
 

@@ -48,6 +48,13 @@ cudaError_t launch_pack_spinor(int prec, int nsc, const Geom& g, int Nv, const v
 cudaError_t launch_unpack_spinor(int prec, int nsc, const Geom& g, int Nv, const void* internal,
                                  void* canon, bool canon_f64, cudaStream_t st);
 
+// column c of a canonical FP64 field with Nsrc right-hand sides <-> slot v of an
+// internal FP64 field
+cudaError_t launch_pack_column64(int nsc, const Geom& g, int Nsrc, int c, const void* canon, int v, void* internal,
+                                 cudaStream_t st);
+cudaError_t launch_unpack_column64(int nsc, const Geom& g, int v, const void* internal, int Nsrc, int c, void* canon,
+                                   cudaStream_t st);
+
 // canonical links V[s][mu][a][b] -> FP64 internal [mu][9][s]
 cudaError_t launch_links_to_f64(const Geom& g, const void* canon, bool canon_f64, void* V64,
                                 cudaStream_t st);

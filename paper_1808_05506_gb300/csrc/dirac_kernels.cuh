@@ -34,7 +34,13 @@ struct ApplyArgs {
     void* out;            // internal spinor layout
     const void* links;    // internal link layout (V_mu or the 40 stored W)
     double diag;          // (4 + m0) Wilson, m staggered, (m0 + 15/8) Brillouin
+    const double* diag_v; // per-right-hand-side diagonal (device, Nv entries) or null: diag for all
 };
+
+template <typename A> DEV_INLINE A diag_of(const ApplyArgs& a, int v)
+{
+    return a.diag_v ? (A)a.diag_v[v] : (A)a.diag;
+}
 
 // ---------------------------------------------------------------- Wilson
 // h = u + S B_MU d  (u: spins 0,1; d: spins 2,3), per colour
@@ -118,11 +124,11 @@ DEV_INLINE void wilson_site(const ApplyArgs& a, long s, int group)
     wilson_hop<T, R, 2, SB, true>(a, s + bwd[2], s + bwd[2], v0, acc);
     wilson_hop<T, R, 3, SF, false>(a, s + fwd[3], s, v0, acc);
     wilson_hop<T, R, 3, SB, true>(a, s + bwd[3], s + bwd[3], v0, acc);
-    const A dg = (A)a.diag;
     const A mh = (A)(-0.5);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (v0 + r < a.Nv) {
+            const A dg = diag_of<A>(a, v0 + r);
             cx<A> p[12];
             load_spinor<T, 12>(a.in, a.g.vol, v0 + r, s, p);
 #pragma unroll
@@ -268,11 +274,11 @@ DEV_INLINE void wilson_pipe_step(const ApplyArgs& a, const long* nb, const long*
     } else {
         using A = typename Store<T>::A;
         using L = SpinorLayout<T, 12>;
-        const A dg = (A)a.diag;
         const A mh = (A)(-0.5);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (v0 + r < a.Nv) {
+                const A dg = diag_of<A>(a, v0 + r);
                 cx<A> p[12];
 #pragma unroll
                 for (int k = 0; k < P::K; ++k) {
@@ -362,11 +368,11 @@ DEV_INLINE void staggered_site(const ApplyArgs& a, long s, int group)
             }
         }
     }
-    const A dg = (A)a.diag;
     const A hf = DAG ? A(-0.5) : A(0.5);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (v0 + r < a.Nv) {
+            const A dg = diag_of<A>(a, v0 + r);
             cx<A> p[3];
             load_spinor<T, 3>(a.in, a.g.vol, v0 + r, s, p);
 #pragma unroll
@@ -459,10 +465,10 @@ DEV_INLINE void brillouin_site(const ApplyArgs& a, long s, int group, const BriD
             }
         }
     }
-    const A dg = (A)a.diag;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (v0 + r < a.Nv) {
+            const A dg = diag_of<A>(a, v0 + r);
             cx<A> p[12];
             load_spinor<T, 12>(a.in, a.g.vol, v0 + r, s, p);
 #pragma unroll

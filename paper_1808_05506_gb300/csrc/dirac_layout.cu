@@ -84,6 +84,53 @@ cudaError_t launch_unpack_spinor(int prec, int nsc, const Geom& g, int Nv, const
     DISPATCH_PREC_NSC(unpack_T, g, Nv, internal, canon, canon_f64, st)
 }
 
+// one column c of a canonical FP64 field with Nsrc right-hand sides <-> slot v
+// of an internal FP64 field (the batched solver's queue of systems)
+template <int NSC>
+__global__ void k_pack_column(Geom g, int Nsrc, int c, const double* __restrict__ canon, int v, void* internal)
+{
+    const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.vol) return;
+    const double* src = canon + ((size_t)s * Nsrc + c) * NSC * 2;
+    cx<double> p[NSC];
+#pragma unroll
+    for (int k = 0; k < NSC; ++k) p[k] = cx<double>{src[2 * k], src[2 * k + 1]};
+    store_spinor<double, NSC>(internal, g.vol, v, s, p);
+}
+
+template <int NSC>
+__global__ void k_unpack_column(Geom g, int v, const void* internal, int Nsrc, int c, double* __restrict__ canon)
+{
+    const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.vol) return;
+    cx<double> p[NSC];
+    load_spinor<double, NSC>(internal, g.vol, v, s, p);
+    double* dst = canon + ((size_t)s * Nsrc + c) * NSC * 2;
+#pragma unroll
+    for (int k = 0; k < NSC; ++k) {
+        dst[2 * k] = p[k].re;
+        dst[2 * k + 1] = p[k].im;
+    }
+}
+
+cudaError_t launch_pack_column64(int nsc, const Geom& g, int Nsrc, int c, const void* canon, int v, void* internal,
+                                 cudaStream_t st)
+{
+    const unsigned nb = (unsigned)((g.vol + 255) / 256);
+    if (nsc == 12) k_pack_column<12><<<nb, 256, 0, st>>>(g, Nsrc, c, (const double*)canon, v, internal);
+    else k_pack_column<3><<<nb, 256, 0, st>>>(g, Nsrc, c, (const double*)canon, v, internal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_column64(int nsc, const Geom& g, int v, const void* internal, int Nsrc, int c, void* canon,
+                                   cudaStream_t st)
+{
+    const unsigned nb = (unsigned)((g.vol + 255) / 256);
+    if (nsc == 12) k_unpack_column<12><<<nb, 256, 0, st>>>(g, v, internal, Nsrc, c, (double*)canon);
+    else k_unpack_column<3><<<nb, 256, 0, st>>>(g, v, internal, Nsrc, c, (double*)canon);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- links
 template <typename CT>
 __global__ void k_links_to_f64(Geom g, const CT* __restrict__ canon, double2* V64)

@@ -149,7 +149,16 @@ def test_binding_calls_match_the_c_signatures(dg, monkeypatch):
     D.kernel_config()
     D.autotune()
     D.solve(x.to(torch.complex128), x0=x.to(torch.complex128))
+    D.solve_batched([x.to(torch.complex128)] * 2, [0.12, 0.121])
     D.close()
     for name in ("dirac_set_links", "dirac_apply", "dirac_apply_dagger", "dirac_force", "dirac_solve",
-                 "dirac_set_kernel_config", "dirac_get_kernel_config", "dirac_autotune", "dirac_destroy"):
+                 "dirac_set_kernel_config", "dirac_get_kernel_config", "dirac_autotune", "dirac_destroy",
+                 "dirac_solve_batched"):
         assert name in calls, name
+
+
+def test_pipe_config_rule(dg):
+    assert dg.pipe_config_fits("f32", 2, 128, 3)
+    assert not dg.pipe_config_fits("f32", 4, 256, 3)
+    assert not dg.pipe_config_fits("f64", 1, 256, 3)
+    assert dg.pipe_config_fits("bf16", 4, 256, 3)

@@ -95,7 +95,7 @@ def test_parity_every_config(dg, op, mass, prec):
     for R in Rs:
         for block in (32, 128, 256):
             for pipe in pipes:
-                if pipe and R * block > 512:
+                if pipe and not dg.pipe_config_fits(prec, R, block, pipe):
                     continue                 # exceeds the shared memory of one block
                 got = run(dg, op, L, Nv, mass, prec, V, psi, cfg=(R, block, pipe), internal=True)
                 assert rel_l2(got, want) <= TOL[prec], (R, block, pipe)
@@ -184,10 +184,9 @@ def test_wilson_full_size_sampled(dg):
     for R in (1, 2, 3, 4):
         for block in (64, 128, 256):
             for pipe in (0, 3):
-                try:
-                    D.set_kernel_config(R, block, pipe)
-                except dg.DiracError:
+                if pipe and not dg.pipe_config_fits("f32", R, block, pipe):
                     continue
+                D.set_kernel_config(R, block, pipe)
                 for dag in (False, True):
                     yi.fill_(0xFF)
                     D.apply(xi, out=yi, dagger=dag)
