@@ -262,6 +262,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--lattice", default=None, help="Nx,Ny,Nz,Nt (a smaller case for profiling)")
     ap.add_argument("--prec", default=None, choices=["f32", "bf16", "f16", "f64"])
+    ap.add_argument("--kernel", default=None, help="R,block,pipe: fixed launch shape instead of the autotuner")
     args = ap.parse_args()
     global WORKLOAD
     if args.lattice:
@@ -282,7 +283,10 @@ def main():
     V, psi = gen_inputs(w)
     D = dg.Dirac(w["op"], w["L"], w["Nv"], w["mass"], w["prec"])
     D.set_links(torch.from_numpy(V).cuda())
-    D.autotune()                       # best of the built launch shapes on this GPU
+    if args.kernel:
+        D.set_kernel_config(*(int(v) for v in args.kernel.split(",")))
+    else:
+        D.autotune()                   # best of the built launch shapes on this GPU
     xin = torch.from_numpy(psi).cuda()
     x = D.pack(xin)
     y = D.new_internal()

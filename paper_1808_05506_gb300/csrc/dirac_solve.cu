@@ -93,6 +93,8 @@ struct SolverWS {
     double* scal = nullptr;                                   // per-rhs scalar slots
     int* iflags = nullptr;                                    // active[W], breakdown, nactive
     double *bb, *rr64, *scale, *coef, *rr0, *rr, *gamma, *gnew, *delta, *alpha, *beta, *diag_v, *itol2;
+    cudaStream_t cs = nullptr;          // private stream: graphs cannot be captured on the legacy stream
+    cudaEvent_t ev = nullptr;
     cudaGraphExec_t gexec = nullptr;
     // what the graph was captured with
     LaunchCfg g_cfg{0, 0, 0};
@@ -107,6 +109,8 @@ void dirac_handle::free_solver_workspace()
     SolverWS* w = (SolverWS*)sw;
     if (!w) return;
     if (w->gexec) cudaGraphExecDestroy(w->gexec);
+    if (w->ev) cudaEventDestroy(w->ev);
+    if (w->cs) cudaStreamDestroy(w->cs);
     void** ptrs[] = {&w->b64, &w->x64, &w->r64, &w->e, &w->r, &w->s, &w->p, &w->t};
     for (void** q : ptrs) release(*q);
     void* pp = w->part;
@@ -154,6 +158,8 @@ static dirac_status ensure_solver_ws(dirac_handle* h, SolverWS** out)
     w->itol2 = w->scal + (size_t)nslots * h->Nv;
     if ((st = h->alloc(&pp, ((size_t)h->Nv + 2) * sizeof(int), "solver flags"))) return st;
     w->iflags = (int*)pp;
+    if ((st = h->cuda(cudaStreamCreateWithFlags(&w->cs, cudaStreamNonBlocking), "solver stream"))) return st;
+    if ((st = h->cuda(cudaEventCreateWithFlags(&w->ev, cudaEventDisableTiming), "solver event"))) return st;
     h->sw_bytes = 3 * f64 + 5 * fp;
     h->sw_nv = h->Nv;
     *out = w;
@@ -314,6 +320,26 @@ static dirac_status fp64_residual(dirac_handle* h, SolverWS* w, const double* di
     return h->cuda(cudaStreamSynchronize(S), "solve: sync");
 }
 
+// Runs a solve on the workspace's private stream, ordered after the work
+// already enqueued on the handle's stream; the handle's stream is restored on
+// every return path.  The solvers block until done, so later work on the
+// caller's stream is ordered after them as well.
+struct OnPrivateStream {
+    dirac_handle* h;
+    cudaStream_t saved;
+    OnPrivateStream(dirac_handle* h_, SolverWS* w) : h(h_), saved(h_->stream)
+    {
+        cudaEventRecord(w->ev, saved);
+        cudaStreamWaitEvent(w->cs, w->ev, 0);
+        h->stream = w->cs;
+    }
+    ~OnPrivateStream()
+    {
+        cudaStreamSynchronize(h->stream);
+        h->stream = saved;
+    }
+};
+
 static dirac_status check_solver_args(dirac_handle* h, double tol, int max_outer, int max_inner, double inner_tol,
                                       const char* name)
 {
@@ -339,6 +365,7 @@ extern "C" DIRAC_API dirac_status dirac_solve(dirac_handle* h, void* x, const vo
     if (h->op == OP_BRILLOUIN && (st = h->build_W64())) return st;
     SolverWS* w;
     if ((st = ensure_solver_ws(h, &w))) return st;
+    OnPrivateStream guard(h, w);
     const int Nv = h->Nv, nsc = nsc_of(h->op);
     const size_t n = (size_t)nsc * h->g.vol;
     cudaStream_t S = h->stream;
@@ -420,6 +447,7 @@ extern "C" DIRAC_API dirac_status dirac_solve_batched(dirac_handle* h, int nsys,
     if (h->op == OP_BRILLOUIN && (st = h->build_W64())) return st;
     SolverWS* w;
     if ((st = ensure_solver_ws(h, &w))) return st;
+    OnPrivateStream guard(h, w);
     const int W = w->W, nsc = nsc_of(h->op);
     const size_t n = (size_t)nsc * h->g.vol;
     cudaStream_t S = h->stream;
