@@ -165,7 +165,7 @@ def sweep_rate(dg, torch, w, steps, warmup):
     cfg = D.kernel_config()
     D.close()
     return {"gflops": flops / t / 1e9, "gbs": byts / t / 1e9, "ms": t * 1e3, "R": cfg[0], "block": cfg[1],
-            "pipe": cfg[2]}
+            "variant": cfg[2]}
 
 
 class OracleSample:
@@ -262,7 +262,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--lattice", default=None, help="Nx,Ny,Nz,Nt (a smaller case for profiling)")
     ap.add_argument("--prec", default=None, choices=["f32", "bf16", "f16", "f64"])
-    ap.add_argument("--kernel", default=None, help="R,block,pipe: fixed launch shape instead of the autotuner")
+    ap.add_argument("--kernel", default=None, help="R,block,variant: fixed launch shape instead of the autotuner")
     args = ap.parse_args()
     global WORKLOAD
     if args.lattice:
@@ -350,7 +350,7 @@ def main():
                    "Nc": 3, "Nv": w["Nv"], "kappa": w["mass"], "links": "exp(0.3 i H), H traceless Gaussian",
                    "source": "complex Gaussian N(0,1)", "layout": "internal site-fastest SoA",
                    "l2": "no flush: each step streams {:.2f} GB > 129 MB L2".format(bytes_step / 1e9),
-                   "kernel": {"rhs_per_thread": cfg[0], "block": cfg[1], "pipe": cfg[2]},
+                   "kernel": {"rhs_per_thread": cfg[0], "block": cfg[1], "variant": cfg[2]},
                    "parallelism": f"replicas x{ws}"},
         "hbm_gbs": achieved,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",

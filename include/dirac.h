@@ -222,24 +222,31 @@ DIRAC_API dirac_status dirac_solve_batched(dirac_handle* h, int nsys, const int*
                                            int max_inner, double inner_tol, double* rel_residual,
                                            dirac_system_stats* sys_stats, dirac_solve_stats* stats);
 
-/* Kernel configuration: R = right-hand sides per thread (1..4 for Wilson and
- * Brillouin, 1, 2, 4 or 6 for staggered), block = threads per block (a
- * multiple of 32, 32..256), pipe = 0 (direct loads) or 3 (Wilson only: a
- * three-stage cp.async pipeline that keeps the next two hops' spinors and
- * links in flight in shared memory; needs R * 3 * block * (bytes per hop)
- * <= 227 KB).  UNSUPPORTED for other values. */
-DIRAC_API dirac_status dirac_set_kernel_config(dirac_handle* h, int R, int block, int pipe);
-DIRAC_API dirac_status dirac_get_kernel_config(const dirac_handle* h, int* R, int* block, int* pipe);
+/* Kernel configuration (the launch shape of the sweeps):
+ *   R        right-hand sides per thread (1..4 for Wilson and Brillouin; 1, 2, 4
+ *            or 6 for staggered); each link is loaded once per thread and
+ *            applied to its R right-hand sides from registers
+ *   block    threads per block (variants 0 and 3; a multiple of 32, 32..256) or
+ *            sites per block (variant 1; 32 or 64)
+ *   variant  0: the right-hand-side groups of a site run in consecutive blocks;
+ *            1: the groups of the same sites share one block, so that each link
+ *               comes from L2 once per block and is reused through L1;
+ *            3: (Wilson) variant 0 with a three-stage cp.async pipeline that
+ *               keeps the next two hops in flight in shared memory; needs
+ *               3 * block * (R * spinor bytes + link bytes) <= 227 KB.
+ * UNSUPPORTED for other values. */
+DIRAC_API dirac_status dirac_set_kernel_config(dirac_handle* h, int R, int block, int variant);
+DIRAC_API dirac_status dirac_get_kernel_config(const dirac_handle* h, int* R, int* block, int* variant);
 
 /* Autotuner (the paper's "best of breed" selection, Sec. 4 and Sec. 6: time
  * every built variant on this machine and keep the winner): times each
- * supported (R, block) of dirac_set_kernel_config on the handle's own
+ * supported (R, block, variant) of dirac_set_kernel_config on the handle's own
  * workspace and keeps the fastest in the handle.  With the environment
  * variable DIRAC_TUNE_CACHE naming a writable file, results are cached per
  * (operator, precision, lattice, Nv, GPU name) and reused unless force != 0.
- * Synchronous.  R, block, pipe, ms (host, may be NULL) receive the choice and
- * its median time per sweep in milliseconds (from the cache when reused). */
-DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int* R, int* block, int* pipe, double* ms);
+ * Synchronous.  R, block, variant, ms (host, may be NULL) receive the choice
+ * and its median time per sweep in milliseconds (from the cache when reused). */
+DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int* R, int* block, int* variant, double* ms);
 
 /* One-line description of the last error on h (or of the last failed
  * dirac_create when h is NULL).  Static or handle-owned storage. */

@@ -297,11 +297,13 @@ class Dirac:
               self.h, "dirac_force")
         return out
 
-    def set_kernel_config(self, R: int, block: int, pipe: int = 0):
-        check(lib().dirac_set_kernel_config(self.h, R, block, pipe), self.h, "dirac_set_kernel_config")
+    def set_kernel_config(self, R: int, block: int, variant: int = 0):
+        """Launch shape: R right-hand sides per thread, block, variant (0 direct,
+        1 groups in block, 3 pipelined Wilson); see dirac_set_kernel_config."""
+        check(lib().dirac_set_kernel_config(self.h, R, block, variant), self.h, "dirac_set_kernel_config")
 
     def autotune(self, force: bool = False):
-        """Pick the fastest (R, block, pipe) for this handle; returns (R, block, pipe, ms per sweep)."""
+        """Pick the fastest (R, block, variant) for this handle; returns (R, block, variant, ms per sweep)."""
         R, B, Pp, ms = I(), I(), I(), D()
         self._sync_stream()
         check(lib().dirac_autotune(self.h, 1 if force else 0, ctypes.byref(R), ctypes.byref(B), ctypes.byref(Pp),
@@ -315,14 +317,26 @@ class Dirac:
         return R.value, B.value, Pp.value
 
 
-def pipe_config_fits(prec: str, R: int, block: int, pipe: int) -> bool:
-    """Whether a pipelined Wilson launch shape fits the 227 KB of shared memory
-    of one block (the rule dirac_set_kernel_config applies)."""
-    if pipe == 0:
+VARIANTS = {"staggered": (0, 1), "wilson": (0, 1, 3), "brillouin": (0, 1)}
+
+
+def config_supported(op: str, prec: str, R: int, block: int, variant: int) -> bool:
+    """The rule dirac_set_kernel_config applies (without a handle)."""
+    if block < 32 or block > 256 or block % 32:
+        return False
+    if op == "staggered" and R not in (1, 2, 4, 6):
+        return False
+    if op != "staggered" and not 1 <= R <= 4:
+        return False
+    if variant == 0:
         return True
-    k = {"f64": 12, "f32": 6, "bf16": 3, "f16": 3}[prec]
-    lb = {"f64": 16, "f32": 8, "bf16": 4, "f16": 4}[prec]
-    return (R * k * 16 + 9 * lb) * pipe * block <= 227 * 1024
+    if variant == 1:
+        return block <= 64
+    if variant == 3 and op == "wilson":
+        k = {"f64": 12, "f32": 6, "bf16": 3, "f16": 3}[prec]
+        lb = {"f64": 16, "f32": 8, "bf16": 4, "f16": 4}[prec]
+        return (R * k * 16 + 9 * lb) * 3 * block <= 227 * 1024
+    return False
 
 
 # per-site, per-right-hand-side model flop counts at Nc = 3 (complex mult-add = 8,

@@ -23,10 +23,31 @@ __global__ void __launch_bounds__(256) k_brillouin(ApplyArgs a, int ngroups)
     brillouin_site<T, R, DAG>(a, s, group, c_bri_dirs);
 }
 
-template <typename T, int R>
-static cudaError_t go(bool dag, const ApplyArgs& a, int block, cudaStream_t st)
+// V_GROUPS: blockDim = (sites, groups); block b covers a run of sites and a
+// chunk of gy right-hand-side groups
+template <typename T, int R, bool DAG>
+__global__ void __launch_bounds__(192, 2) k_brillouin_groups(ApplyArgs a, int ngroups, int gy)
 {
+    const int nchunks = (ngroups + gy - 1) / gy;
+    const long b = blockIdx.x;
+    const int group = (int)(b % nchunks) * gy + threadIdx.y;
+    const long s = (b / nchunks) * blockDim.x + threadIdx.x;
+    if (s >= a.g.vol || group >= ngroups) return;
+    brillouin_site<T, R, DAG>(a, s, group, c_bri_dirs);
+}
+
+template <typename T, int R>
+static cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
+{
+    const int block = c.block;
     const int ngroups = (a.Nv + R - 1) / R;
+    if (c.variant == V_GROUPS) {
+        const int gy = groups_per_block(block, ngroups);
+        const long nb = ((a.g.vol + block - 1) / block) * (long)((ngroups + gy - 1) / gy);
+        if (dag) k_brillouin_groups<T, R, true><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+        else k_brillouin_groups<T, R, false><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+        return cudaGetLastError();
+    }
     const long nblk = ((a.g.vol + block - 1) / block) * (long)ngroups;
     if (dag) k_brillouin<T, R, true><<<(unsigned)nblk, block, 0, st>>>(a, ngroups);
     else k_brillouin<T, R, false><<<(unsigned)nblk, block, 0, st>>>(a, ngroups);
@@ -36,12 +57,12 @@ static cudaError_t go(bool dag, const ApplyArgs& a, int block, cudaStream_t st)
 template <typename T>
 static cudaError_t go_T(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
 {
-    if (c.pipe != 0) return cudaErrorInvalidValue;
+    if (c.variant != V_DIRECT && c.variant != V_GROUPS) return cudaErrorInvalidValue;
     switch (c.R) {
-    case 1: return go<T, 1>(dag, a, c.block, st);
-    case 2: return go<T, 2>(dag, a, c.block, st);
-    case 3: return go<T, 3>(dag, a, c.block, st);
-    case 4: return go<T, 4>(dag, a, c.block, st);
+    case 1: return go<T, 1>(dag, a, c, st);
+    case 2: return go<T, 2>(dag, a, c, st);
+    case 3: return go<T, 3>(dag, a, c, st);
+    case 4: return go<T, 4>(dag, a, c, st);
     default: return cudaErrorInvalidValue;
     }
 }

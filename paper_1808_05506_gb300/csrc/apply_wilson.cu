@@ -30,13 +30,33 @@ __global__ void __launch_bounds__(256) k_wilson_pipe(ApplyArgs a, int ngroups)
     wilson_site_pipe<T, R, DAG, ST>(a, s, group, smem, threadIdx.x, blockDim.x);
 }
 
+// V_GROUPS: blockDim = (sites, groups); block b covers a run of sites and a
+// chunk of gy right-hand-side groups
+template <typename T, int R, bool DAG>
+__global__ void __launch_bounds__(192, 2) k_wilson_groups(ApplyArgs a, int ngroups, int gy)
+{
+    const int nchunks = (ngroups + gy - 1) / gy;
+    const long b = blockIdx.x;
+    const int group = (int)(b % nchunks) * gy + threadIdx.y;
+    const long s = (b / nchunks) * blockDim.x + threadIdx.x;
+    if (s >= a.g.vol || group >= ngroups) return;
+    wilson_site<T, R, DAG>(a, s, group);
+}
+
 template <typename T, int R>
 static cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
 {
     const int block = c.block;
     const int ngroups = (a.Nv + R - 1) / R;
     const long nblk = ((a.g.vol + block - 1) / block) * (long)ngroups;
-    if (c.pipe == 3) {
+    if (c.variant == V_GROUPS) {
+        const int gy = groups_per_block(block, ngroups);
+        const long nb = ((a.g.vol + block - 1) / block) * (long)((ngroups + gy - 1) / gy);
+        if (dag) k_wilson_groups<T, R, true><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+        else k_wilson_groups<T, R, false><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+        return cudaGetLastError();
+    }
+    if (c.variant == V_PIPE3) {
         const size_t smem = WilsonPipe<T, R>::stage_bytes_per_thread * 3 * block;
         auto kern = dag ? k_wilson_pipe<T, R, true, 3> : k_wilson_pipe<T, R, false, 3>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

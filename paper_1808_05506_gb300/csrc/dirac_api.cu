@@ -385,22 +385,22 @@ dirac_status dirac_apply_dagger(dirac_handle* h, void* out, const void* in, dira
 }
 
 // ------------------------------------------------------------------ config
-dirac_status dirac_set_kernel_config(dirac_handle* h, int R, int block, int pipe)
+dirac_status dirac_set_kernel_config(dirac_handle* h, int R, int block, int variant)
 {
     if (!h) return DIRAC_ERR_INVALID_ARG;
-    if (!apply_config_supported(h->op, h->prec, R, block, pipe))
-        return h->fail(DIRAC_ERR_UNSUPPORTED, "dirac_set_kernel_config: R = %d, block = %d, pipe = %d not built",
-                       R, block, pipe);
-    h->cfg = LaunchCfg{R, block, pipe};
+    if (!apply_config_supported(h->op, h->prec, R, block, variant))
+        return h->fail(DIRAC_ERR_UNSUPPORTED, "dirac_set_kernel_config: R = %d, block = %d, variant = %d not built",
+                       R, block, variant);
+    h->cfg = LaunchCfg{R, block, variant};
     return DIRAC_OK;
 }
 
-dirac_status dirac_get_kernel_config(const dirac_handle* h, int* R, int* block, int* pipe)
+dirac_status dirac_get_kernel_config(const dirac_handle* h, int* R, int* block, int* variant)
 {
-    if (!h || !R || !block || !pipe) return DIRAC_ERR_INVALID_ARG;
+    if (!h || !R || !block || !variant) return DIRAC_ERR_INVALID_ARG;
     *R = h->cfg.R;
     *block = h->cfg.block;
-    *pipe = h->cfg.pipe;
+    *variant = h->cfg.variant;
     return DIRAC_OK;
 }
 
@@ -413,13 +413,14 @@ const char* dirac_last_error(const dirac_handle* h)
 // ------------------------------------------------------------------ dispatch
 namespace dirac {
 
-bool apply_config_supported(int op, int prec, int R, int block, int pipe)
+bool apply_config_supported(int op, int prec, int R, int block, int variant)
 {
     if (block < 32 || block > 256 || block % 32) return false;
-    if (op == OP_STAGGERED) return pipe == 0 && (R == 1 || R == 2 || R == 4 || R == 6);
-    if (R < 1 || R > 4) return false;
-    if (pipe == 0) return true;
-    return op == OP_WILSON && pipe == 3 && wilson_pipe_smem(prec, R, block, 3) <= 227 * 1024;
+    const bool Rok = (op == OP_STAGGERED) ? (R == 1 || R == 2 || R == 4 || R == 6) : (R >= 1 && R <= 4);
+    if (!Rok) return false;
+    if (variant == V_DIRECT) return true;
+    if (variant == V_GROUPS) return block <= 64;
+    return op == OP_WILSON && variant == V_PIPE3 && wilson_pipe_smem(prec, R, block, 3) <= 227 * 1024;
 }
 
 LaunchCfg default_config(int op, int prec, int Nv)
@@ -429,11 +430,11 @@ LaunchCfg default_config(int op, int prec, int Nv)
     if (op == OP_STAGGERED) {
         int R = (Nv % 6 == 0) ? 6 : (Nv % 4 == 0 ? 4 : (Nv % 2 == 0 ? 2 : 1));
         if (prec == P_F64 && R > 4) R = 4;
-        return LaunchCfg{R, 128, 0};
+        return LaunchCfg{R, 128, V_DIRECT};
     }
-    if (prec == P_F64) return LaunchCfg{(Nv % 2 == 0) ? 2 : 1, 128, 0};
+    if (prec == P_F64) return LaunchCfg{(Nv % 2 == 0) ? 2 : 1, 128, V_DIRECT};
     int R = (Nv % 2 == 0) ? 2 : 1;
-    return LaunchCfg{R, 128, 0};
+    return LaunchCfg{R, 128, V_DIRECT};
 }
 
 cudaError_t launch_apply(int op, int prec, bool dagger, const ApplyArgs& a, LaunchCfg cfg, cudaStream_t st)

@@ -139,40 +139,23 @@ __global__ void k_xpay(size_t n, const void* __restrict__ s, const double* __res
     }
 }
 
-// dst = scale_v * src (any storage types), optional partial |dst|^2
-template <typename TS, typename TD>
+// dst = scale_v * src within one storage type, optional partial |dst|^2
+template <typename T>
 __global__ void k_scale_copy(size_t n, const void* __restrict__ src, const double* __restrict__ scale, void* dst,
                              double* part)
 {
-    using AD = typename Store<TD>::A;
+    using A = typename Store<T>::A;
     const int v = blockIdx.y;
     const size_t base = (size_t)v * n;
     const double c = scale ? scale[v] : 1.0;
     double s = 0.0;
     for (size_t i = (size_t)blockIdx.x * BT + threadIdx.x; i < n; i += (size_t)gridDim.x * BT) {
-        auto x = ld_one<TS>(src, base + i);
-        cx<AD> y{(AD)(c * (double)x.re), (AD)(c * (double)x.im)};
-        st_one<TD>(dst, base + i, y);
+        auto x = ld_one<T>(src, base + i);
+        cx<A> y{(A)(c * (double)x.re), (A)(c * (double)x.im)};
+        st_one<T>(dst, base + i, y);
         s += norm2c(y);
     }
     if (part) block_partial(s, part, (size_t)v * gridDim.x + blockIdx.x);
-}
-
-// x64 += coef_v * e  (e in storage type T, x in FP64)
-template <typename T>
-__global__ void k_axpy_to64(size_t n, const double* __restrict__ coef, const void* __restrict__ e, void* x64)
-{
-    const int v = blockIdx.y;
-    const size_t base = (size_t)v * n;
-    const double c = coef[v];
-    if (c == 0.0) return;
-    for (size_t i = (size_t)blockIdx.x * BT + threadIdx.x; i < n; i += (size_t)gridDim.x * BT) {
-        auto ev = ld_one<T>(e, base + i);
-        cx<double> xv = ld_one<double>(x64, base + i);
-        xv.re = fma(c, (double)ev.re, xv.re);
-        xv.im = fma(c, (double)ev.im, xv.im);
-        st_one<double>(x64, base + i, xv);
-    }
 }
 
 // r64 = b64 - a64, partial |r|^2 (FP64 fields)
@@ -189,6 +172,56 @@ __global__ void k_residual64(size_t n, const void* __restrict__ b, const void* _
         s += rv.re * rv.re + rv.im * rv.im;
     }
     block_partial(s, part, (size_t)v * gridDim.x + blockIdx.x);
+}
+
+// Fields of different storage types pack the complex numbers of a site into
+// 16-byte elements differently, so conversions between them go site by site
+// through load_spinor / store_spinor (one thread per site and right-hand side).
+
+// dst = scale_v * src across storage types, optional partial |dst|^2
+template <typename TS, typename TD, int NSC>
+__global__ void k_convert(long vol, const void* __restrict__ src, const double* __restrict__ scale, void* dst,
+                          double* part)
+{
+    using AS = typename Store<TS>::A;
+    using AD = typename Store<TD>::A;
+    const int v = blockIdx.y;
+    const double c = scale ? scale[v] : 1.0;
+    double s2 = 0.0;
+    for (long s = (long)blockIdx.x * BT + threadIdx.x; s < vol; s += (long)gridDim.x * BT) {
+        cx<AS> a[NSC];
+        cx<AD> b[NSC];
+        load_spinor<TS, NSC>(src, vol, v, s, a);
+#pragma unroll
+        for (int k = 0; k < NSC; ++k) {
+            b[k] = cx<AD>{(AD)(c * (double)a[k].re), (AD)(c * (double)a[k].im)};
+            s2 += norm2c(b[k]);
+        }
+        store_spinor<TD, NSC>(dst, vol, v, s, b);
+    }
+    if (part) block_partial(s2, part, (size_t)v * gridDim.x + blockIdx.x);
+}
+
+// x64 += coef_v * e  (e in storage type T, x in FP64), site by site
+template <typename T, int NSC>
+__global__ void k_axpy_to64(long vol, const double* __restrict__ coef, const void* __restrict__ e, void* x64)
+{
+    using A = typename Store<T>::A;
+    const int v = blockIdx.y;
+    const double c = coef[v];
+    if (c == 0.0) return;
+    for (long s = (long)blockIdx.x * BT + threadIdx.x; s < vol; s += (long)gridDim.x * BT) {
+        cx<A> ev[NSC];
+        cx<double> xv[NSC];
+        load_spinor<T, NSC>(e, vol, v, s, ev);
+        load_spinor<double, NSC>(x64, vol, v, s, xv);
+#pragma unroll
+        for (int k = 0; k < NSC; ++k) {
+            xv[k].re = fma(c, (double)ev[k].re, xv[k].re);
+            xv[k].im = fma(c, (double)ev[k].im, xv[k].im);
+        }
+        store_spinor<double, NSC>(x64, vol, v, s, xv);
+    }
 }
 
 // ---------------------------------------------------------------- launchers
@@ -247,11 +280,11 @@ cudaError_t blas_xpay(int prec, size_t n, int Nv, const void* s, const double* b
     return cudaGetLastError();
 }
 
-template <typename TS>
-static cudaError_t scale_copy_from(int dprec, dim3 g, size_t n, const void* src, const double* scale, void* dst,
-                                   double* part, cudaStream_t st)
+template <typename TS, int NSC>
+static cudaError_t convert_from(int dprec, dim3 g, long vol, const void* src, const double* scale, void* dst,
+                                double* part, cudaStream_t st)
 {
-#define GO(T) k_scale_copy<TS, T><<<g, BT, 0, st>>>(n, src, scale, dst, part)
+#define GO(T) k_convert<TS, T, NSC><<<g, BT, 0, st>>>(vol, src, scale, dst, part)
     switch (dprec) {
     case P_F64: GO(double); break;
     case P_F32: GO(float); break;
@@ -263,30 +296,49 @@ static cudaError_t scale_copy_from(int dprec, dim3 g, size_t n, const void* src,
     return cudaGetLastError();
 }
 
-cudaError_t blas_scale_copy(int sprec, int dprec, size_t n, int Nv, const void* src, const double* scale,
-                            void* dst, double* part, double* nrm2, cudaStream_t st)
+template <int NSC>
+static cudaError_t convert_nsc(int sprec, int dprec, dim3 g, long vol, const void* src, const double* scale,
+                               void* dst, double* part, cudaStream_t st)
 {
-    dim3 g = grid_of(n, Nv);
-    cudaError_t e;
     switch (sprec) {
-    case P_F64: e = scale_copy_from<double>(dprec, g, n, src, scale, dst, part, st); break;
-    case P_F32: e = scale_copy_from<float>(dprec, g, n, src, scale, dst, part, st); break;
-    case P_BF16: e = scale_copy_from<__nv_bfloat16>(dprec, g, n, src, scale, dst, part, st); break;
-    case P_F16: e = scale_copy_from<__half>(dprec, g, n, src, scale, dst, part, st); break;
+    case P_F64: return convert_from<double, NSC>(dprec, g, vol, src, scale, dst, part, st);
+    case P_F32: return convert_from<float, NSC>(dprec, g, vol, src, scale, dst, part, st);
+    case P_BF16: return convert_from<__nv_bfloat16, NSC>(dprec, g, vol, src, scale, dst, part, st);
+    case P_F16: return convert_from<__half, NSC>(dprec, g, vol, src, scale, dst, part, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t blas_convert(int sprec, int dprec, int nsc, long vol, int Nv, const void* src, const double* scale,
+                         void* dst, double* part, double* nrm2, cudaStream_t st)
+{
+    dim3 g = grid_of((size_t)vol * 4, Nv);   // about 4 sites per thread
+    cudaError_t e = (nsc == 12) ? convert_nsc<12>(sprec, dprec, g, vol, src, scale, dst, part, st)
+                                : convert_nsc<3>(sprec, dprec, g, vol, src, scale, dst, part, st);
     if (e != cudaSuccess) return e;
     if (part && nrm2) k_reduce_partials<<<Nv, BT, 0, st>>>(part, g.x, nrm2, 0);
     return cudaGetLastError();
 }
 
-cudaError_t blas_axpy_to64(int prec, size_t n, int Nv, const double* coef, const void* e, void* x64,
+cudaError_t blas_axpy_to64(int prec, int nsc, long vol, int Nv, const double* coef, const void* e, void* x64,
                            cudaStream_t st)
 {
-    dim3 g = grid_of(n, Nv);
-#define GO(T) k_axpy_to64<T><<<g, BT, 0, st>>>(n, coef, e, x64)
+    dim3 g = grid_of((size_t)vol * 4, Nv);
+#define GO(T) (nsc == 12 ? (k_axpy_to64<T, 12><<<g, BT, 0, st>>>(vol, coef, e, x64)) \
+                         : (k_axpy_to64<T, 3><<<g, BT, 0, st>>>(vol, coef, e, x64)))
     PREC_SWITCH(prec, GO)
 #undef GO
+    return cudaGetLastError();
+}
+
+cudaError_t blas_scale_copy(int prec, size_t n, int Nv, const void* src, const double* scale, void* dst,
+                            double* part, double* nrm2, cudaStream_t st)
+{
+    dim3 g = grid_of(n, Nv);
+#define GO(T) k_scale_copy<T><<<g, BT, 0, st>>>(n, src, scale, dst, part)
+    PREC_SWITCH(prec, GO)
+#undef GO
+    if (part && nrm2) k_reduce_partials<<<Nv, BT, 0, st>>>(part, g.x, nrm2, 0);
     return cudaGetLastError();
 }
 

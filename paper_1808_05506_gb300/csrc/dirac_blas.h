@@ -20,11 +20,15 @@ cudaError_t blas_cgls_step(int prec, size_t n, int Nv, const double* alpha, void
                            const void* t, double* part, double* rr, cudaStream_t st);
 // p = s + beta_v p
 cudaError_t blas_xpay(int prec, size_t n, int Nv, const void* s, const double* beta, void* p, cudaStream_t st);
-// dst = scale_v src (scale NULL: 1); nrm2_v = |dst_v|^2 if part and nrm2 are given
-cudaError_t blas_scale_copy(int sprec, int dprec, size_t n, int Nv, const void* src, const double* scale,
-                            void* dst, double* part, double* nrm2, cudaStream_t st);
-// x64 += coef_v e
-cudaError_t blas_axpy_to64(int prec, size_t n, int Nv, const double* coef, const void* e, void* x64,
+// dst = scale_v src within one storage type (scale NULL: 1); nrm2_v = |dst_v|^2
+// if part and nrm2 are given
+cudaError_t blas_scale_copy(int prec, size_t n, int Nv, const void* src, const double* scale, void* dst,
+                            double* part, double* nrm2, cudaStream_t st);
+// the same across storage types (site by site, since the element packing differs)
+cudaError_t blas_convert(int sprec, int dprec, int nsc, long vol, int Nv, const void* src, const double* scale,
+                         void* dst, double* part, double* nrm2, cudaStream_t st);
+// x64 += coef_v e, site by site
+cudaError_t blas_axpy_to64(int prec, int nsc, long vol, int Nv, const double* coef, const void* e, void* x64,
                            cudaStream_t st);
 // r = b - a (FP64), rr_v = |r_v|^2
 cudaError_t blas_residual64(size_t n, int Nv, const void* b, const void* a, void* r, double* part, double* rr,

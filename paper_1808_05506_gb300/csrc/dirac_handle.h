@@ -17,7 +17,7 @@ struct dirac_handle {
     double diag = 0.0;        // the site-diagonal coefficient of the sweep
     cudaStream_t stream = nullptr;
     int device = 0;
-    dirac::LaunchCfg cfg{1, 128, 0};
+    dirac::LaunchCfg cfg{1, 128, dirac::V_DIRECT};
 
     void* links = nullptr;    // storage-precision links [m][9][site] (m = mu, or 40 stored W)
     void* links64 = nullptr;  // FP64 V_mu [4][9][site]

@@ -19,13 +19,29 @@ inline size_t cbytes(int prec)
     return prec == P_F64 ? 16 : (prec == P_F32 ? 8 : 4);
 }
 
-struct LaunchCfg {
-    int R;       // right-hand sides per thread
-    int block;   // threads per block
-    int pipe;    // 0: direct loads; ST >= 2: cp.async pipeline with ST stages (Wilson)
+// Launch variants of a sweep
+enum Variant {
+    V_DIRECT = 0,   // one thread per (site, group of R right-hand sides); the groups of a
+                    // site sit in consecutive blocks
+    V_GROUPS = 1,   // the groups of the same sites share a block (blockDim.y), so each
+                    // link is fetched from L2 once per block and reused through L1
+    V_PIPE3 = 3     // Wilson: V_DIRECT with a 3-stage cp.async pipeline in shared memory
 };
 
-bool apply_config_supported(int op, int prec, int R, int block, int pipe);
+struct LaunchCfg {
+    int R;         // right-hand sides per thread
+    int block;     // V_DIRECT, V_PIPE3: threads per block; V_GROUPS: sites per block
+    int variant;   // Variant
+};
+
+// threads per block of V_GROUPS: block sites x gy groups with block * gy <= 192
+inline int groups_per_block(int block, int ngroups)
+{
+    int gy = 192 / block;
+    return gy < ngroups ? gy : ngroups;
+}
+
+bool apply_config_supported(int op, int prec, int R, int block, int variant);
 size_t wilson_pipe_smem(int prec, int R, int block, int stages);
 
 // out = D in (or D^+ in) on internal-layout fields

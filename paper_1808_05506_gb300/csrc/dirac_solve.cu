@@ -28,6 +28,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <deque>
 #include <vector>
 
@@ -39,6 +41,17 @@ using namespace dirac;
 namespace dirac {
 
 constexpr int GRAPH_ITERS = 8;
+
+// DIRAC_TRACE=1 in the environment prints the refinement history to stderr
+static bool trace_on()
+{
+    static int on = -1;
+    if (on < 0) {
+        const char* e = getenv("DIRAC_TRACE");
+        on = (e && *e && *e != '0') ? 1 : 0;
+    }
+    return on == 1;
+}
 
 // per right-hand side: alpha = gamma / delta for active ones (else 0); flags breakdown
 __global__ void k_cgls_alpha(int Nv, const double* gamma, const double* delta, const int* active,
@@ -193,7 +206,7 @@ static dirac_status enqueue_iteration(dirac_handle* h, SolverWS* w, const double
 
 static dirac_status ensure_graph(dirac_handle* h, SolverWS* w, const double* diag_v)
 {
-    if (w->gexec && w->g_cfg.R == h->cfg.R && w->g_cfg.block == h->cfg.block && w->g_cfg.pipe == h->cfg.pipe &&
+    if (w->gexec && w->g_cfg.R == h->cfg.R && w->g_cfg.block == h->cfg.block && w->g_cfg.variant == h->cfg.variant &&
         w->g_links == h->links && w->g_diag == diag_v)
         return DIRAC_OK;
     if (w->gexec) {
@@ -239,7 +252,7 @@ static dirac_status inner_cgls(dirac_handle* h, SolverWS* w, const double* diag_
     // s = D^+ r, p = s, gamma = |s|^2
     if ((st = h->run_apply(true, w->s, w->r, W, h->diag, h->links, P, h->cfg, diag_v))) return st;
     S_->sweeps++;
-    if ((st = h->cuda(blas_scale_copy(P, P, n, W, w->s, nullptr, w->p, w->part, w->gamma, S), "solve: p = s")))
+    if ((st = h->cuda(blas_scale_copy(P, n, W, w->s, nullptr, w->p, w->part, w->gamma, S), "solve: p = s")))
         return st;
     int done = 0, first = 1;
     while (done < max_inner) {
@@ -266,6 +279,15 @@ static dirac_status inner_cgls(dirac_handle* h, SolverWS* w, const double* diag_
             *breakdown_out = true;
             break;
         }
+        if (trace_on()) {
+            std::vector<double> rr(W), rr0(W);
+            cudaMemcpy(rr.data(), w->rr, W * sizeof(double), cudaMemcpyDeviceToHost);
+            cudaMemcpy(rr0.data(), w->rr0, W * sizeof(double), cudaMemcpyDeviceToHost);
+            double mx = 0;
+            for (int v = 0; v < W; ++v)
+                if (rr0[v] > 0) mx = std::max(mx, std::sqrt(rr[v] / rr0[v]));
+            fprintf(stderr, "[dirac] inner it %d: active %d, max |r|/|r_hat| %.3e\n", done, flags[1], mx);
+        }
         if (flags[1] == 0) break;
     }
     return DIRAC_OK;
@@ -291,13 +313,14 @@ static dirac_status refine_step(dirac_handle* h, SolverWS* w, const double* diag
         return st;
     if ((st = h->cuda(cudaMemcpyAsync(w->iflags, act.data(), W * sizeof(int), cudaMemcpyHostToDevice, S), "copy")))
         return st;
-    if ((st = h->cuda(blas_scale_copy(P_F64, P, n, W, w->r64, w->scale, w->r, w->part, w->rr0, S), "solve: r_hat")))
+    if ((st = h->cuda(blas_convert(P_F64, P, nsc_of(h->op), h->g.vol, W, w->r64, w->scale, w->r, w->part, w->rr0, S),
+                      "solve: r_hat")))
         return st;
     bool bd = false;
     if ((st = inner_cgls(h, w, diag_v, max_inner, inner_tol, S_, &bd))) return st;
     // x += (|r| / sqrt(n)) e in FP64 (the update is kept even after a breakdown:
     // the next FP64 residual decides)
-    return h->cuda(blas_axpy_to64(P, n, W, w->coef, w->e, w->x64, S), "solve: x update");
+    return h->cuda(blas_axpy_to64(P, nsc_of(h->op), h->g.vol, W, w->coef, w->e, w->x64, S), "solve: x update");
 }
 
 // r64 = b64 - D x64 in FP64; rr64 (host) = |r|^2 per slot
@@ -389,6 +412,7 @@ extern "C" DIRAC_API dirac_status dirac_solve(dirac_handle* h, void* x, const vo
         bool all = true, finite = true;
         for (int v = 0; v < Nv; ++v) {
             res[v] = bb[v] > 0.0 ? std::sqrt(rr64[v] / bb[v]) : std::sqrt(rr64[v]);
+            if (trace_on()) fprintf(stderr, "[dirac] outer %d rhs %d: |r|/|b| %.3e\n", outer, v, res[v]);
             if (!std::isfinite(res[v])) finite = false;
             act[v] = res[v] > tol;
             all = all && !act[v];

@@ -71,7 +71,7 @@ static void cache_store(const std::string& key, int R, int B, int Pp, double ms)
 }
 
 extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int* R_out, int* block_out,
-                                                 int* pipe_out, double* ms_out)
+                                                 int* variant_out, double* ms_out)
 {
     if (!h) return DIRAC_ERR_INVALID_ARG;
     if (!h->have_links) return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_autotune: call dirac_set_links first");
@@ -86,7 +86,7 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
         if ((st = h->cuda(cudaMemsetAsync(h->ws_in, 0, h->field_bytes_internal(h->Nv), h->stream), "autotune")))
             return st;
         std::vector<int> Rs = (h->op == OP_STAGGERED) ? std::vector<int>{1, 2, 4, 6} : std::vector<int>{1, 2, 3, 4};
-        const int blocks[] = {64, 128, 256};
+        const int blocks[] = {32, 64, 128, 256};
         cudaEvent_t e0, e1;
         if ((st = h->cuda(cudaEventCreate(&e0), "autotune"))) return st;
         if ((st = h->cuda(cudaEventCreate(&e1), "autotune"))) {
@@ -95,11 +95,11 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
         }
         best = 1e30;
         LaunchCfg win = h->cfg;
-        const int pipes[] = {0, 3};
+        const int variants[] = {V_DIRECT, V_GROUPS, V_PIPE3};
         for (int r : Rs) {
             if (r > h->Nv && r != Rs.front()) continue;
             for (int b : blocks)
-            for (int pp : pipes) {
+            for (int pp : variants) {
                 if (!apply_config_supported(h->op, h->prec, r, b, pp)) continue;
                 LaunchCfg c{r, b, pp};
                 std::vector<float> t;
@@ -126,11 +126,11 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
         cudaEventDestroy(e1);
         if (st) return st;
         h->cfg = win;
-        cache_store(key, win.R, win.block, win.pipe, best);
+        cache_store(key, win.R, win.block, win.variant, best);
     }
     if (R_out) *R_out = h->cfg.R;
     if (block_out) *block_out = h->cfg.block;
-    if (pipe_out) *pipe_out = h->cfg.pipe;
+    if (variant_out) *variant_out = h->cfg.variant;
     if (ms_out) *ms_out = best;
     return DIRAC_OK;
 }

@@ -157,8 +157,12 @@ def test_binding_calls_match_the_c_signatures(dg, monkeypatch):
         assert name in calls, name
 
 
-def test_pipe_config_rule(dg):
-    assert dg.pipe_config_fits("f32", 2, 128, 3)
-    assert not dg.pipe_config_fits("f32", 4, 256, 3)
-    assert not dg.pipe_config_fits("f64", 1, 256, 3)
-    assert dg.pipe_config_fits("bf16", 4, 256, 3)
+def test_config_rule(dg):
+    assert dg.config_supported("wilson", "f32", 2, 128, 3)
+    assert not dg.config_supported("wilson", "f32", 4, 256, 3)
+    assert not dg.config_supported("wilson", "f64", 1, 256, 3)
+    assert dg.config_supported("wilson", "bf16", 4, 256, 3)
+    assert dg.config_supported("staggered", "f32", 6, 32, 1)
+    assert not dg.config_supported("staggered", "f32", 3, 32, 1)
+    assert not dg.config_supported("brillouin", "f32", 2, 128, 1)
+    assert not dg.config_supported("brillouin", "f32", 2, 128, 3)

@@ -91,14 +91,13 @@ def test_parity_every_config(dg, op, mass, prec):
     V, psi = inputs(op, L, Nv, prec, 210)
     want = oracle.apply(op, V, psi, m0_of(op, mass))
     Rs = (1, 2, 4, 6) if op == "staggered" else (1, 2, 3, 4)
-    pipes = (0, 3) if op == "wilson" else (0,)
     for R in Rs:
-        for block in (32, 128, 256):
-            for pipe in pipes:
-                if pipe and not dg.pipe_config_fits(prec, R, block, pipe):
-                    continue                 # exceeds the shared memory of one block
-                got = run(dg, op, L, Nv, mass, prec, V, psi, cfg=(R, block, pipe), internal=True)
-                assert rel_l2(got, want) <= TOL[prec], (R, block, pipe)
+        for block in (32, 64, 128, 256):
+            for variant in dg.VARIANTS[op]:
+                if not dg.config_supported(op, prec, R, block, variant):
+                    continue
+                got = run(dg, op, L, Nv, mass, prec, V, psi, cfg=(R, block, variant), internal=True)
+                assert rel_l2(got, want) <= TOL[prec], (R, block, variant)
 
 
 @pytest.mark.parametrize("op,mass", [("wilson", 0.11), ("staggered", 0.2), ("brillouin", -0.1)])
@@ -125,16 +124,16 @@ def test_autotune(dg, tmp_path, monkeypatch):
     V, psi = inputs("wilson", L, Nv, "f32", 250)
     D = dg.Dirac("wilson", L, Nv, 0.12, "f32")
     D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
-    R, B, pipe, ms = D.autotune(force=True)
-    assert (R, B, pipe) == D.kernel_config() and ms > 0
-    assert "R%d B%d P%d" % (R, B, pipe) in (tmp_path / "tune.txt").read_text()
+    R, B, variant, ms = D.autotune(force=True)
+    assert (R, B, variant) == D.kernel_config() and ms > 0
+    assert "R%d B%d P%d" % (R, B, variant) in (tmp_path / "tune.txt").read_text()
     x = torch.from_numpy(psi.astype(np.complex64)).cuda()
     got = D.apply(x).cpu().numpy().astype(np.complex128)
     want = oracle.apply("wilson", V, psi, oracle.kappa_to_m0(0.12))
     assert rel_l2(got, want) <= TOL["f32"]
     D2 = dg.Dirac("wilson", L, Nv, 0.12, "f32")
     D2.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
-    assert D2.autotune()[:3] == (R, B, pipe)              # from the cache
+    assert D2.autotune()[:3] == (R, B, variant)           # from the cache
     D.close()
     D2.close()
 
@@ -182,18 +181,18 @@ def test_wilson_full_size_sampled(dg):
     yi = D.new_internal()
     st = torch.from_numpy(sites).cuda()
     for R in (1, 2, 3, 4):
-        for block in (64, 128, 256):
-            for pipe in (0, 3):
-                if pipe and not dg.pipe_config_fits("f32", R, block, pipe):
+        for block in (32, 64, 128, 256):
+            for variant in (0, 1, 3):
+                if not dg.config_supported("wilson", "f32", R, block, variant):
                     continue
-                D.set_kernel_config(R, block, pipe)
+                D.set_kernel_config(R, block, variant)
                 for dag in (False, True):
                     yi.fill_(0xFF)
                     D.apply(xi, out=yi, dagger=dag)
                     y = D.unpack(yi).reshape(-1, Nv, 4, 3)
                     assert bool(torch.isfinite(torch.view_as_real(y)).all())
                     got = y[st].cpu().numpy().astype(np.complex128)
-                    assert rel_l2(got, want[dag]) <= TOL["f32"], (R, block, pipe, dag)
+                    assert rel_l2(got, want[dag]) <= TOL["f32"], (R, block, variant, dag)
     D.close()
 
 
@@ -226,5 +225,7 @@ def test_error_paths(dg):
     assert e.value.status == dg.ERR_UNSUPPORTED
     with pytest.raises(dg.DiracError) as e:
         D.set_kernel_config(4, 256, 3)               # 3 stages x 256 threads x 4 rhs: > 227 KB
+    with pytest.raises(dg.DiracError):
+        D.set_kernel_config(2, 128, 1)               # variant 1 takes 32 or 64 sites per block
     assert e.value.status == dg.ERR_UNSUPPORTED
     D.close()
