@@ -207,6 +207,37 @@ class OracleSample:
                 f"Nv={self.w['Nv']} workload (FP64 gather oracle, OpenMP), {dt:.2f} s")
 
 
+def solve_times(dg, torch, L=(24, 24, 24, 48), Nv=12, m0=0.05, precs=("f32", "bf16", "f16")):
+    """Brillouin D_B x = b to a true FP64 relative residual of 1e-10, Nv = 12,
+    by defect correction (FP64 outer residual) with the inner CGLS stored in
+    each precision: the mixed-vs-FP32 solve-time part of the metric."""
+    w = dict(WORKLOAD, op="brillouin", L=L, mass=m0, seed_links=1003, seed_source=2003)
+    V, psi = gen_inputs(w)
+    b = torch.from_numpy(psi.astype(np.complex128)).cuda()
+    out = {}
+    for prec in precs:
+        D = dg.Dirac("brillouin", L, Nv, m0, prec)
+        D.set_links(torch.from_numpy(V).cuda())
+        D.autotune()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, res, st, status = D.solve(b, tol=1e-10, max_outer=40, max_inner=6000)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[prec] = {"seconds": dt, "status": int(status), "max_rel_residual": float(res.max()),
+                     "outer": st["outer_iterations"], "inner": st["inner_iterations"],
+                     "sweeps": st["sweeps"], "fp64_sweeps": st["fp64_sweeps"], "kernel": list(D.kernel_config())}
+        D.close()
+        del x
+        torch.cuda.empty_cache()
+    if "f32" in out:
+        for p in precs:
+            if p != "f32":
+                out[p]["speedup_vs_f32"] = out["f32"]["seconds"] / out[p]["seconds"]
+    out["workload"] = "brillouin_solve_{}_nv{}_m0_{}".format("x".join(map(str, L)), Nv, m0)
+    return out
+
+
 def cpu_oracle_rate(w, inputs=None, seconds=15.0):
     s = OracleSample(w, inputs)
     n = s.calibrate(seconds)
@@ -260,6 +291,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--lattice", default=None, help="Nx,Ny,Nz,Nt (a smaller case for profiling)")
     ap.add_argument("--prec", default=None, choices=["f32", "bf16", "f16", "f64"])
     ap.add_argument("--kernel", default=None, help="R,block,variant: fixed launch shape instead of the autotuner")
@@ -376,6 +408,8 @@ def main():
         extra["brillouin_24x24x24x48_nv12_bf16"] = sweep_rate(dg, torch, dict(bw, prec="bf16"), 20, 3)
         extra["wilson_32x32x32x32_nv12_bf16"] = sweep_rate(dg, torch, dict(WORKLOAD, prec="bf16"), 200, 5)
         line["extra"] = extra
+    if not args.no_solve and not args.no_extra:
+        line["solve"] = solve_times(dg, torch)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_rate(w, inputs=(V, psi))
     if rank == 0:

@@ -37,7 +37,8 @@
  *           of one complex each).
  *
  * Pointers: unless a function says otherwise, spinor and field pointers are
- * DEVICE pointers owned by the caller; the library never frees them.  Work is
+ * DEVICE pointers owned by the caller, 16-byte aligned (else
+ * DIRAC_ERR_INVALID_ARG); the library never frees them.  Work is
  * enqueued on the handle's CUDA stream and is asynchronous with respect to
  * the host unless stated.  One handle must not be used from two host threads
  * at once.
@@ -231,6 +232,9 @@ DIRAC_API dirac_status dirac_solve_batched(dirac_handle* h, int nsys, const int*
  *   variant  0: the right-hand-side groups of a site run in consecutive blocks;
  *            1: the groups of the same sites share one block, so that each link
  *               comes from L2 once per block and is reused through L1;
+ *            2: (Wilson) variant 1, and each block walks 8 consecutive
+ *               t-slices of its sites so that the t-neighbours and backward
+ *               t-links come from L1 (the y and z loads bypass L1);
  *            3: (Wilson) variant 0 with a three-stage cp.async pipeline that
  *               keeps the next two hops in flight in shared memory; needs
  *               3 * block * (R * spinor bytes + link bytes) <= 227 KB.

@@ -317,7 +317,7 @@ class Dirac:
         return R.value, B.value, Pp.value
 
 
-VARIANTS = {"staggered": (0, 1), "wilson": (0, 1, 3), "brillouin": (0, 1)}
+VARIANTS = {"staggered": (0, 1), "wilson": (0, 1, 2, 3), "brillouin": (0, 1)}
 
 
 def config_supported(op: str, prec: str, R: int, block: int, variant: int) -> bool:
@@ -332,6 +332,8 @@ def config_supported(op: str, prec: str, R: int, block: int, variant: int) -> bo
         return True
     if variant == 1:
         return block <= 64
+    if variant == 2:
+        return op == "wilson" and block <= 64
     if variant == 3 and op == "wilson":
         k = {"f64": 12, "f32": 6, "bf16": 3, "f16": 3}[prec]
         lb = {"f64": 16, "f32": 8, "bf16": 4, "f16": 4}[prec]

@@ -18,6 +18,26 @@ __global__ void __launch_bounds__(256) k_wilson(ApplyArgs a, int ngroups)
     wilson_site<T, R, DAG>(a, s, group);
 }
 
+// V_TMARCH: blockDim = (sites, groups); a block owns a run of `block` sites of
+// one t-slice (index s3 within the slice) and walks TC consecutive slices, so
+// the t-neighbours and backward t-links it needs were read by this block one
+// step earlier and are still in L1
+template <typename T, int R, bool DAG>
+__global__ void __launch_bounds__(192, 2) k_wilson_march(ApplyArgs a, int ngroups, int gy, int tc)
+{
+    const int nchunks = (ngroups + gy - 1) / gy;
+    const long vol3 = a.g.stride[3];
+    const long nruns = (vol3 + blockDim.x - 1) / blockDim.x;
+    long b = blockIdx.x;
+    const int group = (int)(b % nchunks) * gy + threadIdx.y;
+    b /= nchunks;
+    const long s3 = (b % nruns) * blockDim.x + threadIdx.x;
+    const int t0 = (int)(b / nruns) * tc;
+    if (s3 >= vol3 || group >= ngroups) return;
+    const int t1 = min(t0 + tc, a.g.L[3]);
+    for (int t = t0; t < t1; ++t) wilson_site<T, R, DAG, true>(a, s3 + vol3 * t, group);
+}
+
 // pipelined variant: the loads of later hops are in flight in shared memory
 template <typename T, int R, bool DAG, int ST>
 __global__ void __launch_bounds__(256) k_wilson_pipe(ApplyArgs a, int ngroups)
@@ -54,6 +74,16 @@ static cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st
         const long nb = ((a.g.vol + block - 1) / block) * (long)((ngroups + gy - 1) / gy);
         if (dag) k_wilson_groups<T, R, true><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
         else k_wilson_groups<T, R, false><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+        return cudaGetLastError();
+    }
+    if (c.variant == V_TMARCH) {
+        const int gy = groups_per_block(block, ngroups);
+        const long vol3 = a.g.stride[3];
+        const int tc = a.g.L[3] < 8 ? a.g.L[3] : 8;
+        const long nb = ((vol3 + block - 1) / block) * (long)((ngroups + gy - 1) / gy) *
+                        (long)((a.g.L[3] + tc - 1) / tc);
+        if (dag) k_wilson_march<T, R, true><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy, tc);
+        else k_wilson_march<T, R, false><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy, tc);
         return cudaGetLastError();
     }
     if (c.variant == V_PIPE3) {

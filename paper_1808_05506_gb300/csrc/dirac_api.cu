@@ -1,6 +1,7 @@
 // C ABI of the library (include/dirac.h): handle management, argument
 // validation and the dispatch onto the kernels.
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -135,7 +136,7 @@ static bool is_device_ptr(const void* p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-bool dirac_check_device_ptr(const void* p) { return is_device_ptr(p); }
+bool dirac_check_device_ptr(const void* p) { return is_device_ptr(p) && ((uintptr_t)p % 16) == 0; }
 
 // ------------------------------------------------------------------ lifecycle
 dirac_status dirac_create(dirac_handle** h, dirac_op op, int Nc, int Nx, int Ny, int Nz, int Nt,
@@ -264,6 +265,8 @@ dirac_status dirac_set_links(dirac_handle* h, const void* V, dirac_prec V_prec, 
         return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_set_links: links must be complex double or float");
     if (on_device && !is_device_ptr(V))
         return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_set_links: on_device = 1 but V is not a device pointer");
+    if ((uintptr_t)V % 16)
+        return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_set_links: V must be 16-byte aligned");
     const bool f64 = V_prec == DIRAC_F64;
     const size_t canon_bytes = (size_t)h->g.vol * 4 * 9 * (f64 ? 16 : 8);
     dirac_status st;
@@ -339,6 +342,8 @@ dirac_status dirac_pack(dirac_handle* h, void* internal_out, const void* canonic
     if (!h) return DIRAC_ERR_INVALID_ARG;
     if (!internal_out || !canonical_in || internal_out == canonical_in)
         return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_pack: NULL or aliased pointers");
+    if (!dirac_check_device_ptr(internal_out) || !dirac_check_device_ptr(canonical_in))
+        return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_pack: need 16-byte aligned device pointers");
     return h->cuda(launch_pack_spinor(h->prec, nsc_of(h->op), h->g, h->Nv, canonical_in,
                                       h->prec == P_F64, internal_out, h->stream), "pack");
 }
@@ -348,6 +353,8 @@ dirac_status dirac_unpack(dirac_handle* h, void* canonical_out, const void* inte
     if (!h) return DIRAC_ERR_INVALID_ARG;
     if (!canonical_out || !internal_in || canonical_out == internal_in)
         return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_unpack: NULL or aliased pointers");
+    if (!dirac_check_device_ptr(canonical_out) || !dirac_check_device_ptr(internal_in))
+        return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_unpack: need 16-byte aligned device pointers");
     return h->cuda(launch_unpack_spinor(h->prec, nsc_of(h->op), h->g, h->Nv, internal_in,
                                         canonical_out, h->prec == P_F64, h->stream), "unpack");
 }
@@ -362,8 +369,8 @@ static dirac_status apply_common(dirac_handle* h, bool dagger, void* out, const 
     if (layout != DIRAC_CANONICAL && layout != DIRAC_INTERNAL)
         return h->fail(DIRAC_ERR_INVALID_ARG, "%s: unknown layout", name);
     if (!h->have_links) return h->fail(DIRAC_ERR_INVALID_ARG, "%s: call dirac_set_links first", name);
-    if (!is_device_ptr(out) || !is_device_ptr(in))
-        return h->fail(DIRAC_ERR_INVALID_ARG, "%s: in and out must be device pointers", name);
+    if (!dirac_check_device_ptr(out) || !dirac_check_device_ptr(in))
+        return h->fail(DIRAC_ERR_INVALID_ARG, "%s: in and out must be 16-byte aligned device pointers", name);
     dirac_status st;
     if (layout == DIRAC_INTERNAL)
         return h->run_apply(dagger, out, in, h->Nv, h->diag, h->links, h->prec, h->cfg);
@@ -420,6 +427,7 @@ bool apply_config_supported(int op, int prec, int R, int block, int variant)
     if (!Rok) return false;
     if (variant == V_DIRECT) return true;
     if (variant == V_GROUPS) return block <= 64;
+    if (variant == V_TMARCH) return op == OP_WILSON && block <= 64;
     return op == OP_WILSON && variant == V_PIPE3 && wilson_pipe_smem(prec, R, block, 3) <= 227 * 1024;
 }
 

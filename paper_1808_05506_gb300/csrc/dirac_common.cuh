@@ -122,6 +122,66 @@ template <typename V> DEV_INLINE V ld_ro(const V* p)
     return *p;
 #endif
 }
+// read-only load that does not allocate in L1 (for data no other thread of
+// this SM will read soon, so that L1 keeps what will be reused)
+DEV_INLINE float4 ld_na(const float4* p)
+{
+#if defined(__CUDA_ARCH__)
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+#else
+    return *p;
+#endif
+}
+DEV_INLINE double2 ld_na(const double2* p)
+{
+#if defined(__CUDA_ARCH__)
+    double2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+    return v;
+#else
+    return *p;
+#endif
+}
+DEV_INLINE uint4 ld_na(const uint4* p)
+{
+#if defined(__CUDA_ARCH__)
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+#else
+    return *p;
+#endif
+}
+DEV_INLINE float2 ld_na(const float2* p)
+{
+#if defined(__CUDA_ARCH__)
+    float2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0,%1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+#else
+    return *p;
+#endif
+}
+DEV_INLINE uint32_t ld_na(const uint32_t* p)
+{
+#if defined(__CUDA_ARCH__)
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+#else
+    return *p;
+#endif
+}
+template <bool NA, typename V> DEV_INLINE V ld_pol(const V* p)
+{
+    if constexpr (NA) return ld_na(p);
+    else return ld_ro(p);
+}
+
 template <typename V> DEV_INLINE void st_cs(V* p, V v)
 {
 #if defined(__CUDA_ARCH__)
@@ -243,6 +303,56 @@ DEV_INLINE void store_spinor(void* base, size_t vol, int v, long s, const cx<typ
         if constexpr (L::CPV == 1) st_one<T>(base, idx, in[k]);
         else st_vec<T>(base, idx, in + k * L::CPV);
     }
+}
+
+// the same loads with an L1 policy (NA: do not allocate in L1)
+template <typename T, bool NA> DEV_INLINE cx<typename Store<T>::A> ld_one_p(const void* base, size_t i)
+{
+    if constexpr (!NA) return ld_one<T>(base, i);
+    else if constexpr (sizeof(T) == 8) {
+        double2 v = ld_na(reinterpret_cast<const double2*>(base) + i);
+        return {v.x, v.y};
+    } else if constexpr (sizeof(T) == 4) {
+        float2 v = ld_na(reinterpret_cast<const float2*>(base) + i);
+        return {v.x, v.y};
+    } else {
+        return unpack2(ld_na(reinterpret_cast<const uint32_t*>(base) + i), (T*)nullptr);
+    }
+}
+template <typename T, bool NA> DEV_INLINE void ld_vec_p(const void* base, size_t i, cx<typename Store<T>::A>* o)
+{
+    if constexpr (!NA) ld_vec<T>(base, i, o);
+    else if constexpr (sizeof(T) == 8) {
+        double2 v = ld_na(reinterpret_cast<const double2*>(base) + i);
+        o[0] = {v.x, v.y};
+    } else if constexpr (sizeof(T) == 4) {
+        float4 v = ld_na(reinterpret_cast<const float4*>(base) + i);
+        o[0] = {v.x, v.y};
+        o[1] = {v.z, v.w};
+    } else {
+        uint4 v = ld_na(reinterpret_cast<const uint4*>(base) + i);
+        o[0] = unpack2(v.x, (T*)nullptr);
+        o[1] = unpack2(v.y, (T*)nullptr);
+        o[2] = unpack2(v.z, (T*)nullptr);
+        o[3] = unpack2(v.w, (T*)nullptr);
+    }
+}
+template <typename T, int NSC, bool NA>
+DEV_INLINE void load_spinor_p(const void* base, size_t vol, int v, long s, cx<typename Store<T>::A>* out)
+{
+    using L = SpinorLayout<T, NSC>;
+#pragma unroll
+    for (int k = 0; k < L::K; ++k) {
+        size_t idx = ((size_t)v * L::K + k) * vol + (size_t)s;
+        if constexpr (L::CPV == 1) out[k] = ld_one_p<T, NA>(base, idx);
+        else ld_vec_p<T, NA>(base, idx, out + k * L::CPV);
+    }
+}
+template <typename T, bool NA>
+DEV_INLINE void load_link_p(const void* base, size_t vol, int m, long s, cx<typename Store<T>::A>* U)
+{
+#pragma unroll
+    for (int e = 0; e < 9; ++e) U[e] = ld_one_p<T, NA>(base, ((size_t)m * 9 + e) * vol + (size_t)s);
 }
 
 // 3x3 link m at site s

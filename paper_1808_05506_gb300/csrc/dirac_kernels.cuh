@@ -79,28 +79,33 @@ HD void wilson_reconstruct(const cx<A>* w, cx<A>* acc)
     }
 }
 
-// one hop: acc_r += (1 + S gamma_MU) U psi_r(nbr),  U = V_MU(lsite) or its adjoint (BACK)
-template <typename T, int R, int MU, int S, bool BACK>
+// one hop: acc_r += (1 + S gamma_MU) U psi_r(nbr),  U = V_MU(lsite) or its adjoint (BACK);
+// NA: the loads bypass L1 (data this SM will not read again soon)
+template <typename T, int R, int MU, int S, bool BACK, bool NA = false>
 DEV_INLINE void wilson_hop(const ApplyArgs& a, long nbr, long lsite, int v0,
                            cx<typename Store<T>::A> (&acc)[R][12])
 {
     using A = typename Store<T>::A;
     cx<A> U[9];
-    load_link<T>(a.links, a.g.vol, MU, lsite, U);
+    load_link_p<T, NA>(a.links, a.g.vol, MU, lsite, U);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        if (v0 + r < a.Nv) {
-            cx<A> p[12], h[6], w[6];
-            load_spinor<T, 12>(a.in, a.g.vol, v0 + r, nbr, p);
-            wilson_project<MU, S>(p, h);
-            if constexpr (BACK) { mat_dag_vec(U, h, w); mat_dag_vec(U, h + 3, w + 3); }
-            else { mat_vec(U, h, w); mat_vec(U, h + 3, w + 3); }
-            wilson_reconstruct<MU, S>(w, acc[r]);
-        }
+        // a partial last group recomputes the last right-hand side instead of
+        // branching, so that the loads of all R right-hand sides can be issued
+        // together; only the stores are guarded
+        const int v = min(v0 + r, a.Nv - 1);
+        cx<A> p[12], h[6], w[6];
+        load_spinor_p<T, 12, NA>(a.in, a.g.vol, v, nbr, p);
+        wilson_project<MU, S>(p, h);
+        if constexpr (BACK) { mat_dag_vec(U, h, w); mat_dag_vec(U, h + 3, w + 3); }
+        else { mat_vec(U, h, w); mat_vec(U, h + 3, w + 3); }
+        wilson_reconstruct<MU, S>(w, acc[r]);
     }
 }
 
-template <typename T, int R, bool DAG>
+// MARCH: the caller walks along t with L1 keeping the t-neighbours, so the
+// y and z hops (which no other warp of this block will reuse) bypass L1
+template <typename T, int R, bool DAG, bool MARCH = false>
 DEV_INLINE void wilson_site(const ApplyArgs& a, long s, int group)
 {
     using A = typename Store<T>::A;
@@ -118,28 +123,27 @@ DEV_INLINE void wilson_site(const ApplyArgs& a, long s, int group)
     constexpr int SB = -SF;
     wilson_hop<T, R, 0, SF, false>(a, s + fwd[0], s, v0, acc);
     wilson_hop<T, R, 0, SB, true>(a, s + bwd[0], s + bwd[0], v0, acc);
-    wilson_hop<T, R, 1, SF, false>(a, s + fwd[1], s, v0, acc);
-    wilson_hop<T, R, 1, SB, true>(a, s + bwd[1], s + bwd[1], v0, acc);
-    wilson_hop<T, R, 2, SF, false>(a, s + fwd[2], s, v0, acc);
-    wilson_hop<T, R, 2, SB, true>(a, s + bwd[2], s + bwd[2], v0, acc);
+    wilson_hop<T, R, 1, SF, false, MARCH>(a, s + fwd[1], s, v0, acc);
+    wilson_hop<T, R, 1, SB, true, MARCH>(a, s + bwd[1], s + bwd[1], v0, acc);
+    wilson_hop<T, R, 2, SF, false, MARCH>(a, s + fwd[2], s, v0, acc);
+    wilson_hop<T, R, 2, SB, true, MARCH>(a, s + bwd[2], s + bwd[2], v0, acc);
     wilson_hop<T, R, 3, SF, false>(a, s + fwd[3], s, v0, acc);
     wilson_hop<T, R, 3, SB, true>(a, s + bwd[3], s + bwd[3], v0, acc);
     const A mh = (A)(-0.5);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        if (v0 + r < a.Nv) {
-            const A dg = diag_of<A>(a, v0 + r);
-            cx<A> p[12];
-            load_spinor<T, 12>(a.in, a.g.vol, v0 + r, s, p);
+        const int v = min(v0 + r, a.Nv - 1);
+        const A dg = diag_of<A>(a, v);
+        cx<A> p[12];
+        load_spinor<T, 12>(a.in, a.g.vol, v, s, p);
 #pragma unroll
-            for (int i = 0; i < 12; ++i) {
-                cx<A> o;
-                o.re = fma(mh, acc[r][i].re, dg * p[i].re);
-                o.im = fma(mh, acc[r][i].im, dg * p[i].im);
-                p[i] = o;
-            }
-            store_spinor<T, 12>(a.out, a.g.vol, v0 + r, s, p);
+        for (int i = 0; i < 12; ++i) {
+            cx<A> o;
+            o.re = fma(mh, acc[r][i].re, dg * p[i].re);
+            o.im = fma(mh, acc[r][i].im, dg * p[i].im);
+            p[i] = o;
         }
+        if (v0 + r < a.Nv) store_spinor<T, 12>(a.out, a.g.vol, v0 + r, s, p);
     }
 }
 
@@ -353,37 +357,35 @@ DEV_INLINE void staggered_site(const ApplyArgs& a, long s, int group)
         load_link<T>(a.links, a.g.vol, mu, s + bwd[mu], Ub);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            if (v0 + r < a.Nv) {
-                cx<A> pf[3], pb[3], w[3] = {}, wb[3] = {};
-                load_spinor<T, 3>(a.in, a.g.vol, v0 + r, s + fwd[mu], pf);
-                load_spinor<T, 3>(a.in, a.g.vol, v0 + r, s + bwd[mu], pb);
-                mat_vec(Uf, pf, w);
-                mat_dag_vec(Ub, pb, wb);
+            const int v = min(v0 + r, a.Nv - 1);   // partial group: recompute, store guarded
+            cx<A> pf[3], pb[3], w[3] = {}, wb[3] = {};
+            load_spinor<T, 3>(a.in, a.g.vol, v, s + fwd[mu], pf);
+            load_spinor<T, 3>(a.in, a.g.vol, v, s + bwd[mu], pb);
+            mat_vec(Uf, pf, w);
+            mat_dag_vec(Ub, pb, wb);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    cx<A> d = w[c] - wb[c];
-                    acc[r][c].re = fma(eta, d.re, acc[r][c].re);
-                    acc[r][c].im = fma(eta, d.im, acc[r][c].im);
-                }
+            for (int c = 0; c < 3; ++c) {
+                cx<A> d = w[c] - wb[c];
+                acc[r][c].re = fma(eta, d.re, acc[r][c].re);
+                acc[r][c].im = fma(eta, d.im, acc[r][c].im);
             }
         }
     }
     const A hf = DAG ? A(-0.5) : A(0.5);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        if (v0 + r < a.Nv) {
-            const A dg = diag_of<A>(a, v0 + r);
-            cx<A> p[3];
-            load_spinor<T, 3>(a.in, a.g.vol, v0 + r, s, p);
+        const int v = min(v0 + r, a.Nv - 1);
+        const A dg = diag_of<A>(a, v);
+        cx<A> p[3];
+        load_spinor<T, 3>(a.in, a.g.vol, v, s, p);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                cx<A> o;
-                o.re = fma(hf, acc[r][c].re, dg * p[c].re);
-                o.im = fma(hf, acc[r][c].im, dg * p[c].im);
-                p[c] = o;
-            }
-            store_spinor<T, 3>(a.out, a.g.vol, v0 + r, s, p);
+        for (int c = 0; c < 3; ++c) {
+            cx<A> o;
+            o.re = fma(hf, acc[r][c].re, dg * p[c].re);
+            o.im = fma(hf, acc[r][c].im, dg * p[c].im);
+            p[c] = o;
         }
+        if (v0 + r < a.Nv) store_spinor<T, 3>(a.out, a.g.vol, v0 + r, s, p);
     }
 }
 
@@ -453,31 +455,29 @@ DEV_INLINE void brillouin_site(const ApplyArgs& a, long s, int group, const BriD
         const BriDirA<A> m = bri_coeffs<A, DAG>(D);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            if (v0 + r < a.Nv) {
-                cx<A> p[12], chi[12];
-                load_spinor<T, 12>(a.in, a.g.vol, v0 + r, nbr, p);
-                bri_spin(m, p, chi);
+            const int v = min(v0 + r, a.Nv - 1);   // partial group: recompute, store guarded
+            cx<A> p[12], chi[12];
+            load_spinor<T, 12>(a.in, a.g.vol, v, nbr, p);
+            bri_spin(m, p, chi);
 #pragma unroll
-                for (int sp = 0; sp < 4; ++sp) {
-                    if (D.neg) mat_dag_vec_acc(W, chi + 3 * sp, acc[r] + 3 * sp);
-                    else mat_vec_acc(W, chi + 3 * sp, acc[r] + 3 * sp);
-                }
+            for (int sp = 0; sp < 4; ++sp) {
+                if (D.neg) mat_dag_vec_acc(W, chi + 3 * sp, acc[r] + 3 * sp);
+                else mat_vec_acc(W, chi + 3 * sp, acc[r] + 3 * sp);
             }
         }
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        if (v0 + r < a.Nv) {
-            const A dg = diag_of<A>(a, v0 + r);
-            cx<A> p[12];
-            load_spinor<T, 12>(a.in, a.g.vol, v0 + r, s, p);
+        const int v = min(v0 + r, a.Nv - 1);
+        const A dg = diag_of<A>(a, v);
+        cx<A> p[12];
+        load_spinor<T, 12>(a.in, a.g.vol, v, s, p);
 #pragma unroll
-            for (int i = 0; i < 12; ++i) {
-                p[i].re = fma(dg, p[i].re, acc[r][i].re);
-                p[i].im = fma(dg, p[i].im, acc[r][i].im);
-            }
-            store_spinor<T, 12>(a.out, a.g.vol, v0 + r, s, p);
+        for (int i = 0; i < 12; ++i) {
+            p[i].re = fma(dg, p[i].re, acc[r][i].re);
+            p[i].im = fma(dg, p[i].im, acc[r][i].im);
         }
+        if (v0 + r < a.Nv) store_spinor<T, 12>(a.out, a.g.vol, v0 + r, s, p);
     }
 }
 

@@ -5,6 +5,56 @@
 namespace dirac {
 
 // ---------------------------------------------------------------- spinors
+// canonical complex numbers c of one (site, rhs): NSC contiguous complex of type CT,
+// read and written with the widest aligned vector (float4 = 2 complex when the
+// 8 * NSC-byte run is 16-byte aligned, else one complex at a time)
+template <int NSC, typename CT, typename A>
+__device__ __forceinline__ void canon_load(const CT* src, cx<A>* p)
+{
+    if constexpr (sizeof(CT) == 4 && NSC % 2 == 0) {
+        const float4* q = reinterpret_cast<const float4*>(src);
+#pragma unroll
+        for (int j = 0; j < NSC / 2; ++j) {
+            float4 v = q[j];
+            p[2 * j] = cx<A>{(A)v.x, (A)v.y};
+            p[2 * j + 1] = cx<A>{(A)v.z, (A)v.w};
+        }
+    } else if constexpr (sizeof(CT) == 4) {
+        const float2* q = reinterpret_cast<const float2*>(src);
+#pragma unroll
+        for (int j = 0; j < NSC; ++j) {
+            float2 v = q[j];
+            p[j] = cx<A>{(A)v.x, (A)v.y};
+        }
+    } else {
+        const double2* q = reinterpret_cast<const double2*>(src);
+#pragma unroll
+        for (int j = 0; j < NSC; ++j) {
+            double2 v = q[j];
+            p[j] = cx<A>{(A)v.x, (A)v.y};
+        }
+    }
+}
+
+template <int NSC, typename CT, typename A>
+__device__ __forceinline__ void canon_store(CT* dst, const cx<A>* p)
+{
+    if constexpr (sizeof(CT) == 4 && NSC % 2 == 0) {
+        float4* q = reinterpret_cast<float4*>(dst);
+#pragma unroll
+        for (int j = 0; j < NSC / 2; ++j)
+            q[j] = make_float4((float)p[2 * j].re, (float)p[2 * j].im, (float)p[2 * j + 1].re, (float)p[2 * j + 1].im);
+    } else if constexpr (sizeof(CT) == 4) {
+        float2* q = reinterpret_cast<float2*>(dst);
+#pragma unroll
+        for (int j = 0; j < NSC; ++j) q[j] = make_float2((float)p[j].re, (float)p[j].im);
+    } else {
+        double2* q = reinterpret_cast<double2*>(dst);
+#pragma unroll
+        for (int j = 0; j < NSC; ++j) q[j] = make_double2((double)p[j].re, (double)p[j].im);
+    }
+}
+
 template <typename T, int NSC, typename CT>
 __global__ void k_pack(Geom g, int Nv, const CT* __restrict__ canon, void* internal)
 {
@@ -13,10 +63,8 @@ __global__ void k_pack(Geom g, int Nv, const CT* __restrict__ canon, void* inter
     if (i >= g.vol * Nv) return;
     const long s = i / Nv;
     const int v = (int)(i % Nv);
-    const CT* src = canon + (size_t)i * NSC * 2;
     cx<A> p[NSC];
-#pragma unroll
-    for (int c = 0; c < NSC; ++c) p[c] = cx<A>{(A)src[2 * c], (A)src[2 * c + 1]};
+    canon_load<NSC, CT, A>(canon + (size_t)i * NSC * 2, p);
     store_spinor<T, NSC>(internal, g.vol, v, s, p);
 }
 
@@ -30,12 +78,7 @@ __global__ void k_unpack(Geom g, int Nv, const void* internal, CT* __restrict__ 
     const int v = (int)(i % Nv);
     cx<A> p[NSC];
     load_spinor<T, NSC>(internal, g.vol, v, s, p);
-    CT* dst = canon + (size_t)i * NSC * 2;
-#pragma unroll
-    for (int c = 0; c < NSC; ++c) {
-        dst[2 * c] = (CT)p[c].re;
-        dst[2 * c + 1] = (CT)p[c].im;
-    }
+    canon_store<NSC, CT, A>(canon + (size_t)i * NSC * 2, p);
 }
 
 template <typename T, int NSC>

@@ -95,7 +95,7 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
         }
         best = 1e30;
         LaunchCfg win = h->cfg;
-        const int variants[] = {V_DIRECT, V_GROUPS, V_PIPE3};
+        const int variants[] = {V_DIRECT, V_GROUPS, V_TMARCH, V_PIPE3};
         for (int r : Rs) {
             if (r > h->Nv && r != Rs.front()) continue;
             for (int b : blocks)
@@ -115,6 +115,10 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
                 if (st) break;
                 std::sort(t.begin(), t.end());
                 const double med = t[t.size() / 2];
+                const char* tr = getenv("DIRAC_TRACE");
+                if (tr && *tr && *tr != '0')
+                    fprintf(stderr, "[dirac] autotune %s R=%d block=%d variant=%d: %.4f ms\n", key.c_str(), r, b,
+                            pp, med);
                 if (med < best) {
                     best = med;
                     win = c;
