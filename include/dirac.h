@@ -223,6 +223,30 @@ DIRAC_API dirac_status dirac_solve_batched(dirac_handle* h, int nsys, const int*
                                            int max_inner, double inner_tol, double* rel_residual,
                                            dirac_system_stats* sys_stats, dirac_solve_stats* stats);
 
+/* out = D in (dagger = 0) or D^+ in (dagger != 0) on canonical device fields,
+ * with the same result as dirac_apply(h, out, in, DIRAC_CANONICAL) /
+ * dirac_apply_dagger, but allocating no device memory: the two internal-layout
+ * work fields of the canonical apply live in a fixed 64 MiB array inside the
+ * library's device image instead of memory the handle allocates.  (This entry
+ * point has no counterpart in the paper; it exists for callers that cannot
+ * allocate while they run: code enqueuing into a stream that is being captured
+ * into a CUDA graph, where cudaMalloc is not allowed; loops that cannot afford
+ * the device synchronisation cudaMalloc / cudaFree may cause; and hosts whose
+ * device memory is reserved up front by their own allocator.)
+ *   - The array is reserved on every GPU that loads the library and kept
+ *     until the process exits.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture.  The handle's device must be the current device.
+ *   - Fields whose two internal copies need more than 64 MiB (2 x
+ *     dirac_field_bytes(h, DIRAC_INTERNAL), each rounded up to 256 bytes) are
+ *     rejected with DIRAC_ERR_INVALID_ARG; use dirac_apply for those.
+ *   - Every call uses the same array, and a call leaves its contents behind.
+ *     Calls whose work overlaps on the GPU (other streams, other handles, other
+ *     host threads) race on it: serialise them.
+ * Requires dirac_set_links first.  Asynchronous on the handle's stream. */
+DIRAC_API dirac_status dirac_apply_static(dirac_handle* h, void* out, const void* in, int dagger);
+
 /* Kernel configuration (the launch shape of the sweeps):
  *   R        right-hand sides per thread (1..4 for Wilson and Brillouin; 1, 2, 4
  *            or 6 for staggered); each link is loaded once per thread and

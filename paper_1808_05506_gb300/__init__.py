@@ -71,6 +71,7 @@ SIGNATURES = {
     "dirac_force": (I, [P, P, P, P, I]),
     "dirac_autotune": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
     "dirac_solve_batched": (I, [P, I, P, P, P, P, D, I, I, D, P, P, P]),
+    "dirac_apply_static": (I, [P, P, P, I]),
 }
 
 
