@@ -72,6 +72,7 @@ SIGNATURES = {
     "dirac_autotune": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
     "dirac_solve_batched": (I, [P, I, P, P, P, P, D, I, I, D, P, P, P]),
     "dirac_apply_static": (I, [P, P, P, I]),
+    "dirac_sync": (I, [P]),
 }
 
 
@@ -311,6 +312,11 @@ class Dirac:
                                    ctypes.byref(ms)), self.h, "dirac_autotune")
         return R.value, B.value, Pp.value, ms.value
 
+    def sync(self):
+        """Wait for the handle's stream; raises DiracError(TIMEOUT) if a kernel's
+        bounded wait ran out."""
+        check(lib().dirac_sync(self.h), self.h, "dirac_sync")
+
     def kernel_config(self):
         R, B, Pp = I(), I(), I()
         check(lib().dirac_get_kernel_config(self.h, ctypes.byref(R), ctypes.byref(B), ctypes.byref(Pp)), self.h,
@@ -318,13 +324,22 @@ class Dirac:
         return R.value, B.value, Pp.value
 
 
-VARIANTS = {"staggered": (0, 1), "wilson": (0, 1, 2, 3), "brillouin": (0, 1)}
+VARIANTS = {"staggered": (0, 1), "wilson": (0, 1, 2, 3, 4), "brillouin": (0, 1)}
 
 
-def config_supported(op: str, prec: str, R: int, block: int, variant: int) -> bool:
-    """The rule dirac_set_kernel_config applies (without a handle)."""
+def config_supported(op: str, prec: str, R: int, block: int, variant: int, L=None) -> bool:
+    """The rule dirac_set_kernel_config applies (without a handle); L = (Nx, Ny, Nz, Nt)
+    is needed for variant 4."""
     if block < 32 or block > 256 or block % 32:
         return False
+    if variant == 4:
+        if op != "wilson" or prec == "f64" or R not in (1, 2) or L is None or block > 128:
+            return False
+        Lx, Ly = L[0], L[1]
+        if block % Lx or Lx % 4 or Ly % (block // Lx):
+            return False
+        k, lb, nst = (6, 8, 3) if prec == "f32" else (3, 4, 4)
+        return 256 + nst * (2 * R * k * block * 16 + 9 * block * lb) <= 227 * 1024
     if op == "staggered" and R not in (1, 2, 4, 6):
         return False
     if op != "staggered" and not 1 <= R <= 4:

@@ -5,6 +5,7 @@
 // blocks cover the right-hand-side groups of the same sites, so the other
 // groups find the links in L2.
 #include "dirac_internal.h"
+#include "wilson_tma.cuh"
 
 namespace dirac {
 
@@ -36,6 +37,140 @@ __global__ void __launch_bounds__(192, 2) k_wilson_march(ApplyArgs a, int ngroup
     if (s3 >= vol3 || group >= ngroups) return;
     const int t1 = min(t0 + tc, a.g.L[3]);
     for (int t = t0; t < t1; ++t) wilson_site<T, R, DAG, true>(a, s3 + vol3 * t, group);
+}
+
+// V_TMA: persistent CTAs; one producer warp streams the stages of each tile
+// with bulk copies, G * S consumer threads compute from shared memory
+constexpr int kTimeoutCode = 7;   // DIRAC_TIMEOUT
+
+template <typename T> struct TmaStages { static constexpr int value = sizeof(T) >= 4 ? 3 : 4; };
+
+template <typename T, int R, int G, bool DAG>
+__global__ void __launch_bounds__(G * 128 + 32, 1) k_wilson_tma(TmaArgs ta)
+{
+    constexpr int RB = R * G;
+    constexpr int NST = TmaStages<T>::value;
+    using Lay = TmaLayout<T, RB>;
+    using A = typename Store<T>::A;
+    extern __shared__ __align__(16) char smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + NST;
+    char* bufs = smem + 256;
+    const size_t sb = Lay::stage_bytes(ta.S);
+    const int ncons = ta.S * G;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int b = 0; b < NST; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], ncons / 32);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const Geom& g = ta.a.g;
+    if (tid >= ncons) {
+        // producer: lane 0 of the last warp
+        if ((tid & 31) != 0) return;
+        unsigned long seq = 0;
+        bool ok = true;
+        for (long tile = blockIdx.x; tile < ta.ntiles && ok; tile += gridDim.x) {
+            const TmaTile Tt = tma_tile(g, ta.ny, tile);
+            for (int q = 0; q < ta.rounds && ok; ++q)
+                for (int d = 0; d < TMA_STAGES_PER_ROUND; ++d) {
+                    const int b = (int)(seq % NST);
+                    const unsigned long u = seq / NST;
+                    if (u > 0 && !mbar_wait(&empty[b], (unsigned)((u - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    tma_issue_stage<T, RB>(ta, Tt, q, d, bufs + b * sb, &full[b]);
+                    ++seq;
+                }
+        }
+        if (!ok) {
+            if (ta.err) atomicExch(ta.err, kTimeoutCode);
+            // let the copies already issued land before the CTA can exit
+            const unsigned long first = seq > (unsigned long)NST ? seq - NST : 0;
+            for (unsigned long s2 = first; s2 < seq; ++s2) mbar_wait(&full[s2 % NST], (unsigned)((s2 / NST) & 1));
+        }
+        return;
+    }
+    const int i = tid % ta.S, sub = tid / ta.S;
+    unsigned long seq = 0;
+    for (long tile = blockIdx.x; tile < ta.ntiles; tile += gridDim.x) {
+        const TmaTile Tt = tma_tile(g, ta.ny, tile);
+        const long site = tma_row_site(g, Tt, i / g.L[0], 0) + i % g.L[0];
+        for (int q = 0; q < ta.rounds; ++q) {
+            cx<A> acc[R][12];
+            for (int d = 0; d < TMA_STAGES_PER_ROUND; ++d, ++seq) {
+                const int b = (int)(seq % NST);
+                if (!mbar_wait(&full[b], (unsigned)((seq / NST) & 1))) {
+                    if (ta.err) atomicExch(ta.err, kTimeoutCode);
+                    return;
+                }
+                tma_consume_stage<T, R, RB, DAG>(ta, d, bufs + b * sb, i, sub, q, acc);
+                __syncwarp();
+                if ((tid & 31) == 0) mbar_arrive(&empty[b]);
+            }
+            const A mh = (A)(-0.5);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int v = q * RB + sub * R + r;
+                if (v < ta.a.Nv) {
+                    cx<A> o[12];
+#pragma unroll
+                    for (int c = 0; c < 12; ++c) o[c] = cx<A>{mh * acc[r][c].re, mh * acc[r][c].im};
+                    store_spinor<T, 12>(ta.a.out, g.vol, v, site, o);
+                }
+            }
+        }
+    }
+}
+
+// the tile of the TMA variant for sites-per-tile S: ny = S / Lx complete rows
+bool wilson_tma_geometry(const Geom& g, int S, int* ny)
+{
+    if (S % 32 || S > 128 || S % g.L[0]) return false;
+    const int n = S / g.L[0];
+    if (n < 1 || g.L[1] % n) return false;
+    if (g.L[0] % 4) return false;   // 16-byte rows of 16-bit links
+    *ny = n;
+    return true;
+}
+
+size_t wilson_tma_smem(int prec, int R, int S)
+{
+    const int RB = 2 * R;
+    const size_t K = prec == P_F32 ? 6 : 3;
+    const size_t LB = prec == P_F32 ? 8 : 4;
+    const int nst = prec == P_F32 ? 3 : 4;
+    return 256 + (size_t)nst * ((size_t)RB * K * S * 16 + 9 * S * LB);
+}
+
+template <typename T, int R>
+static cudaError_t go_tma(bool dag, const ApplyArgs& a, int S, cudaStream_t st)
+{
+    constexpr int G = 2;
+    int ny = 0;
+    if (!wilson_tma_geometry(a.g, S, &ny)) return cudaErrorInvalidValue;
+    TmaArgs ta;
+    ta.a = a;
+    ta.ny = ny;
+    ta.S = S;
+    ta.ntiles = a.g.vol / S;
+    ta.rounds = (a.Nv + R * G - 1) / (R * G);
+    ta.err = a.err;
+    const int prec = sizeof(T) == 4 ? P_F32 : P_BF16;
+    const size_t smem = wilson_tma_smem(prec, R, S);
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long grid = ta.ntiles < nsm ? ta.ntiles : nsm;
+    auto kern = dag ? k_wilson_tma<T, R, G, true> : k_wilson_tma<T, R, G, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)grid, G * S + 32, smem, st>>>(ta);
+    return cudaGetLastError();
 }
 
 // pipelined variant: the loads of later hops are in flight in shared memory
@@ -102,6 +237,16 @@ static cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st
 template <typename T>
 static cudaError_t go_T(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
 {
+    if (c.variant == V_TMA) {
+        if constexpr (sizeof(T) == 8) return cudaErrorInvalidValue;
+        else {
+            switch (c.R) {
+            case 1: return go_tma<T, 1>(dag, a, c.block, st);
+            case 2: return go_tma<T, 2>(dag, a, c.block, st);
+            default: return cudaErrorInvalidValue;
+            }
+        }
+    }
     switch (c.R) {
     case 1: return go<T, 1>(dag, a, c, st);
     case 2: return go<T, 2>(dag, a, c, st);

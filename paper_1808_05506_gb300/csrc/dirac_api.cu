@@ -113,6 +113,7 @@ ApplyArgs dirac_handle::args(void* out, const void* in, int nv, double diag_valu
     a.links = links;
     a.diag = diag_value;
     a.diag_v = nullptr;
+    a.err = dev_err;
     return a;
 }
 
@@ -123,6 +124,7 @@ dirac_status dirac_handle::run_apply(bool dagger, void* out, const void* in, int
     ApplyArgs a = args(out, in, nv, diag_value);
     a.links = link_ptr;
     a.diag_v = diag_v;
+    a.err = dev_err;
     return cuda(launch_apply(op, p, dagger, a, c, stream), "apply kernel launch");
 }
 
@@ -204,6 +206,12 @@ dirac_status dirac_create(dirac_handle** h, dirac_op op, int Nc, int Nx, int Ny,
         return DIRAC_ERR_CUDA;
     }
     H->cfg = default_config(H->op, H->prec, Nv);
+    if (cudaMalloc((void**)&H->dev_err, sizeof(int)) != cudaSuccess || cudaMemset(H->dev_err, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = "dirac_create: cannot allocate the device error word";
+        delete H;
+        return DIRAC_ERR_OOM;
+    }
     if (H->op == OP_BRILLOUIN) {
         cudaError_t e = upload_brillouin_table(H->stream);
         if (e != cudaSuccess) {
@@ -219,6 +227,8 @@ dirac_status dirac_create(dirac_handle** h, dirac_op op, int Nc, int Nx, int Ny,
 
 dirac_handle::~dirac_handle()
 {
+    void* e = dev_err;
+    release(e);
     release(links);
     release(links64);
     release(W64);
@@ -395,7 +405,7 @@ dirac_status dirac_apply_dagger(dirac_handle* h, void* out, const void* in, dira
 dirac_status dirac_set_kernel_config(dirac_handle* h, int R, int block, int variant)
 {
     if (!h) return DIRAC_ERR_INVALID_ARG;
-    if (!apply_config_supported(h->op, h->prec, R, block, variant))
+    if (!apply_config_supported(h->op, h->prec, R, block, variant, h->g))
         return h->fail(DIRAC_ERR_UNSUPPORTED, "dirac_set_kernel_config: R = %d, block = %d, variant = %d not built",
                        R, block, variant);
     h->cfg = LaunchCfg{R, block, variant};
@@ -411,6 +421,20 @@ dirac_status dirac_get_kernel_config(const dirac_handle* h, int* R, int* block, 
     return DIRAC_OK;
 }
 
+dirac_status dirac_sync(dirac_handle* h)
+{
+    if (!h) return DIRAC_ERR_INVALID_ARG;
+    dirac_status st = h->cuda(cudaStreamSynchronize(h->stream), "dirac_sync");
+    if (st) return st;
+    int e = 0;
+    if ((st = h->cuda(cudaMemcpy(&e, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost), "dirac_sync"))) return st;
+    if (e) {
+        cudaMemset(h->dev_err, 0, sizeof(int));
+        return h->fail(DIRAC_TIMEOUT, "dirac_sync: a kernel's bounded wait ran out (status %d)", e);
+    }
+    return DIRAC_OK;
+}
+
 const char* dirac_last_error(const dirac_handle* h)
 {
     if (!h) return g_create_error.c_str();
@@ -420,9 +444,14 @@ const char* dirac_last_error(const dirac_handle* h)
 // ------------------------------------------------------------------ dispatch
 namespace dirac {
 
-bool apply_config_supported(int op, int prec, int R, int block, int variant)
+bool apply_config_supported(int op, int prec, int R, int block, int variant, const Geom& g)
 {
     if (block < 32 || block > 256 || block % 32) return false;
+    if (variant == V_TMA) {
+        int ny = 0;
+        return op == OP_WILSON && prec != P_F64 && (R == 1 || R == 2) && wilson_tma_geometry(g, block, &ny) &&
+               wilson_tma_smem(prec, R, block) <= 227 * 1024;
+    }
     const bool Rok = (op == OP_STAGGERED) ? (R == 1 || R == 2 || R == 4 || R == 6) : (R >= 1 && R <= 4);
     if (!Rok) return false;
     if (variant == V_DIRECT) return true;

@@ -23,6 +23,7 @@ struct dirac_handle {
     void* links64 = nullptr;  // FP64 V_mu [4][9][site]
     void* W64 = nullptr;      // FP64 W [40][9][site] (Brillouin; kept for F64 handles, lazy otherwise)
     bool have_links = false;
+    int* dev_err = nullptr;   // device error word written by kernels whose bounded waits run out
 
     void* ws_in = nullptr;    // internal-layout workspaces of the canonical apply
     void* ws_out = nullptr;

@@ -27,7 +27,9 @@ enum Variant {
                     // link is fetched from L2 once per block and reused through L1
     V_TMARCH = 2,   // Wilson: V_GROUPS, and each block walks 8 consecutive t-slices so that
                     // the t-neighbours come from L1; y/z loads bypass L1
-    V_PIPE3 = 3     // Wilson: V_DIRECT with a 3-stage cp.async pipeline in shared memory
+    V_PIPE3 = 3,    // Wilson: V_DIRECT with a 3-stage cp.async pipeline in shared memory
+    V_TMA = 4       // Wilson (FP32/BF16/FP16): tiles of complete x-rows streamed by bulk copies
+                    // (one producer warp, mbarrier ring); `block` = sites per tile
 };
 
 struct LaunchCfg {
@@ -43,8 +45,10 @@ inline int groups_per_block(int block, int ngroups)
     return gy < ngroups ? gy : ngroups;
 }
 
-bool apply_config_supported(int op, int prec, int R, int block, int variant);
+bool apply_config_supported(int op, int prec, int R, int block, int variant, const Geom& g);
 size_t wilson_pipe_smem(int prec, int R, int block, int stages);
+bool wilson_tma_geometry(const Geom& g, int S, int* ny);
+size_t wilson_tma_smem(int prec, int R, int S);
 
 // out = D in (or D^+ in) on internal-layout fields
 cudaError_t launch_apply(int op, int prec, bool dagger, const ApplyArgs& a, LaunchCfg cfg,

@@ -35,6 +35,7 @@ struct ApplyArgs {
     const void* links;    // internal link layout (V_mu or the 40 stored W)
     double diag;          // (4 + m0) Wilson, m staggered, (m0 + 15/8) Brillouin
     const double* diag_v; // per-right-hand-side diagonal (device, Nv entries) or null: diag for all
+    int* err;             // device error word (kernels with bounded waits record DIRAC_TIMEOUT) or null
 };
 
 template <typename A> DEV_INLINE A diag_of(const ApplyArgs& a, int v)

@@ -78,7 +78,7 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
     const std::string key = tune_key(h);
     int R = 0, B = 0, Pp = 0;
     double best = 0.0;
-    if (!force && cache_lookup(key, &R, &B, &Pp, &best) && apply_config_supported(h->op, h->prec, R, B, Pp)) {
+    if (!force && cache_lookup(key, &R, &B, &Pp, &best) && apply_config_supported(h->op, h->prec, R, B, Pp, h->g)) {
         h->cfg = LaunchCfg{R, B, Pp};
     } else {
         dirac_status st;
@@ -95,14 +95,15 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
         }
         best = 1e30;
         LaunchCfg win = h->cfg;
-        const int variants[] = {V_DIRECT, V_GROUPS, V_TMARCH, V_PIPE3};
+        const int variants[] = {V_DIRECT, V_GROUPS, V_TMARCH, V_PIPE3, V_TMA};
         for (int r : Rs) {
             if (r > h->Nv && r != Rs.front()) continue;
             for (int b : blocks)
             for (int pp : variants) {
-                if (!apply_config_supported(h->op, h->prec, r, b, pp)) continue;
+                if (!apply_config_supported(h->op, h->prec, r, b, pp, h->g)) continue;
                 LaunchCfg c{r, b, pp};
                 std::vector<float> t;
+                cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream);
                 for (int rep = 0; rep < 7 && st == DIRAC_OK; ++rep) {
                     cudaEventRecord(e0, h->stream);
                     st = h->run_apply(false, h->ws_out, h->ws_in, h->Nv, h->diag, h->links, h->prec, c);
@@ -113,6 +114,12 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
                     if (rep >= 2) t.push_back(ms);   // two warm-up calls
                 }
                 if (st) break;
+                int kerr = 0;
+                cudaMemcpy(&kerr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+                if (kerr) {   // a bounded wait ran out in this variant: never pick it
+                    cudaMemset(h->dev_err, 0, sizeof(int));
+                    continue;
+                }
                 std::sort(t.begin(), t.end());
                 const double med = t[t.size() / 2];
                 const char* tr = getenv("DIRAC_TRACE");

@@ -57,10 +57,11 @@ def run(dg, op, L, Nv, mass, prec, V, psi, dagger=False, cfg=None, internal=Fals
         yi = D.new_internal()
         yi.fill_(0xFF)                      # NaN pattern: every element must be overwritten
         D.apply(xi, out=yi, dagger=dagger)
+        D.sync()                                # kernel-side timeouts surface here
         y = D.unpack(yi)
     else:
         y = D.apply(x, dagger=dagger)
-    torch.cuda.synchronize()
+    D.sync()
     D.close()
     return y.cpu().numpy().astype(np.complex128)
 
@@ -94,7 +95,7 @@ def test_parity_every_config(dg, op, mass, prec):
     for R in Rs:
         for block in (32, 64, 128, 256):
             for variant in dg.VARIANTS[op]:
-                if not dg.config_supported(op, prec, R, block, variant):
+                if not dg.config_supported(op, prec, R, block, variant, L):
                     continue
                 got = run(dg, op, L, Nv, mass, prec, V, psi, cfg=(R, block, variant), internal=True)
                 assert rel_l2(got, want) <= TOL[prec], (R, block, variant)
@@ -114,6 +115,20 @@ def test_low_precision_storage(dg, op, mass, prec):
     else:
         want = oracle.apply(op, Vr, pr, m0_of(op, mass))
     assert rel_l2(got, want) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16", "f16"])
+def test_wilson_tma_tiles(dg, prec):
+    """The bulk-copy variant over tile shapes: whole planes, partial planes
+    whose y+1 / y-1 stages wrap around, Nv that leaves a partial round."""
+    for L, Nv, R, S in (((8, 16, 2, 4), 3, 1, 32), ((8, 12, 4, 2), 5, 2, 32), ((32, 8, 4, 4), 7, 2, 128),
+                        ((16, 8, 2, 6), 4, 1, 64), ((24, 8, 4, 4), 6, 2, 96)):
+        V, psi = inputs("wilson", L, Nv, "f32", 260)
+        for dagger in (False, True):
+            got = run(dg, "wilson", L, Nv, 0.124, prec, V, psi, dagger=dagger, cfg=(R, S, 4), internal=True)
+            Vr, pr = rounded_for_oracle(V, psi, prec)
+            want = oracle.apply("wilson", Vr, pr, oracle.kappa_to_m0(0.124), dagger=dagger)
+            assert rel_l2(got, want) <= TOL[prec], (L, Nv, R, S, dagger)
 
 
 def test_autotune(dg, tmp_path, monkeypatch):
@@ -182,13 +197,14 @@ def test_wilson_full_size_sampled(dg):
     st = torch.from_numpy(sites).cuda()
     for R in (1, 2, 3, 4):
         for block in (32, 64, 128, 256):
-            for variant in (0, 1, 3):
-                if not dg.config_supported("wilson", "f32", R, block, variant):
+            for variant in (0, 1, 2, 3, 4):
+                if not dg.config_supported("wilson", "f32", R, block, variant, L):
                     continue
                 D.set_kernel_config(R, block, variant)
                 for dag in (False, True):
                     yi.fill_(0xFF)
                     D.apply(xi, out=yi, dagger=dag)
+                    D.sync()                           # bounded waits of the staged variant report here
                     y = D.unpack(yi).reshape(-1, Nv, 4, 3)
                     assert bool(torch.isfinite(torch.view_as_real(y)).all())
                     got = y[st].cpu().numpy().astype(np.complex128)

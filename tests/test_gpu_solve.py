@@ -166,3 +166,49 @@ def test_solve_batched_c5_shape_reduced(dg):
         cols = sorted({0, nv_list[i] - 1})
         r = oracle_residual("wilson", V, xs[i][..., cols, :, :], bs[i][..., cols, :, :], oracle.kappa_to_m0(kappas[i]))
         assert r.max() <= 1e-10, (i, r)
+
+
+@pytest.mark.skipif(not __import__("os").environ.get("DIRAC_FULL_BATCHED"),
+                    reason="full-size batched configuration (several GPU-minutes): set DIRAC_FULL_BATCHED=1")
+def test_solve_batched_c5_full(dg):
+    """48 Wilson systems on 32^3 x 64, Nv ~ U{1..24}, kappa ~ U[0.120, 0.124],
+    BF16 storage, FP32 arithmetic, FP64 refinement to 1e-10, shared links.
+    The canonical FP64 b and x of all 48 systems (about 600 columns of 403 MB)
+    do not fit one GPU at once, so the systems go through dirac_solve_batched
+    in waves that fill the handle's slots; every column's FP64 residual comes
+    from the library, and two sampled columns per system are re-evaluated by
+    the oracle."""
+    import time
+    L = (32, 32, 32, 64)
+    rng = synth.rng(1005, synth.STREAM_MISC)
+    nv_list = [int(v) for v in rng.integers(1, 25, 48)]
+    kappas = [float(k) for k in rng.uniform(0.120, 0.124, 48)]
+    V = synth.round_to(synth.gauge_links(L, 3, "near_identity", 1005), "f32")
+    D = dg.Dirac("wilson", L, 96, kappas[0], "bf16")
+    D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
+    D.autotune()
+    t0 = time.perf_counter()
+    i, total_cols, worst = 0, 0, 0.0
+    while i < 48:
+        wave = []
+        cols = 0
+        while i < 48 and cols + nv_list[i] <= 160:
+            wave.append(i)
+            cols += nv_list[i]
+            i += 1
+        bs = [torch.from_numpy(synth.spinor(L, nv_list[j], 4, 3, 2005 + j)).cuda() for j in wave]
+        xs, res, sys_stats, tot, status = D.solve_batched(bs, [kappas[j] for j in wave], tol=1e-10,
+                                                          max_outer=60, max_inner=8000)
+        assert status == dg.OK, (wave, tot)
+        worst = max(worst, float(res.max()))
+        for j, b, x in zip(wave, bs, xs):
+            cols_j = sorted({0, nv_list[j] - 1})
+            xc = x[..., cols_j, :, :].cpu().numpy()
+            bc = b[..., cols_j, :, :].cpu().numpy()
+            r = oracle_residual("wilson", V, xc, bc, oracle.kappa_to_m0(kappas[j]))
+            assert r.max() <= 1e-10, (j, r)
+        total_cols += cols
+        del bs, xs
+        torch.cuda.empty_cache()
+    D.close()
+    print(f"batched full: {total_cols} columns, worst residual {worst:.3e}, {time.perf_counter() - t0:.1f} s")
