@@ -346,6 +346,8 @@ def config_supported(op: str, prec: str, R: int, block: int, variant: int, L=Non
         return False
     if variant == 0:
         return True
+    if op == "wilson" and prec == "f64":
+        return False
     if variant == 1:
         return block <= 64
     if variant == 2:

@@ -5,129 +5,12 @@
 // blocks cover the right-hand-side groups of the same sites, so the other
 // groups find the links in L2.
 #include "dirac_internal.h"
-#include "wilson_tma.cuh"
 
 namespace dirac {
 
-template <typename T, int R, bool DAG>
-__global__ void __launch_bounds__(256) k_wilson(ApplyArgs a, int ngroups)
-{
-    const long b = blockIdx.x;
-    const int group = (int)(b % ngroups);
-    const long s = (b / ngroups) * blockDim.x + threadIdx.x;
-    if (s >= a.g.vol) return;
-    wilson_site<T, R, DAG>(a, s, group);
-}
+template <typename T>
+cudaError_t wilson_go_T(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st);
 
-// V_TMARCH: blockDim = (sites, groups); a block owns a run of `block` sites of
-// one t-slice (index s3 within the slice) and walks TC consecutive slices, so
-// the t-neighbours and backward t-links it needs were read by this block one
-// step earlier and are still in L1
-template <typename T, int R, bool DAG>
-__global__ void __launch_bounds__(192, 2) k_wilson_march(ApplyArgs a, int ngroups, int gy, int tc)
-{
-    const int nchunks = (ngroups + gy - 1) / gy;
-    const long vol3 = a.g.stride[3];
-    const long nruns = (vol3 + blockDim.x - 1) / blockDim.x;
-    long b = blockIdx.x;
-    const int group = (int)(b % nchunks) * gy + threadIdx.y;
-    b /= nchunks;
-    const long s3 = (b % nruns) * blockDim.x + threadIdx.x;
-    const int t0 = (int)(b / nruns) * tc;
-    if (s3 >= vol3 || group >= ngroups) return;
-    const int t1 = min(t0 + tc, a.g.L[3]);
-    for (int t = t0; t < t1; ++t) wilson_site<T, R, DAG, true>(a, s3 + vol3 * t, group);
-}
-
-// V_TMA: persistent CTAs; one producer warp streams the stages of each tile
-// with bulk copies, G * S consumer threads compute from shared memory
-constexpr int kTimeoutCode = 7;   // DIRAC_TIMEOUT
-
-template <typename T> struct TmaStages { static constexpr int value = sizeof(T) >= 4 ? 3 : 4; };
-
-template <typename T, int R, int G, bool DAG>
-__global__ void __launch_bounds__(G * 128 + 32, 1) k_wilson_tma(TmaArgs ta)
-{
-    constexpr int RB = R * G;
-    constexpr int NST = TmaStages<T>::value;
-    using Lay = TmaLayout<T, RB>;
-    using A = typename Store<T>::A;
-    extern __shared__ __align__(16) char smem[];
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
-    uint64_t* empty = full + NST;
-    char* bufs = smem + 256;
-    const size_t sb = Lay::stage_bytes(ta.S);
-    const int ncons = ta.S * G;
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        for (int b = 0; b < NST; ++b) {
-            mbar_init(&full[b], 1);
-            mbar_init(&empty[b], ncons / 32);
-        }
-        mbar_fence_init();
-    }
-    __syncthreads();
-    const Geom& g = ta.a.g;
-    if (tid >= ncons) {
-        // producer: lane 0 of the last warp
-        if ((tid & 31) != 0) return;
-        unsigned long seq = 0;
-        bool ok = true;
-        for (long tile = blockIdx.x; tile < ta.ntiles && ok; tile += gridDim.x) {
-            const TmaTile Tt = tma_tile(g, ta.ny, tile);
-            for (int q = 0; q < ta.rounds && ok; ++q)
-                for (int d = 0; d < TMA_STAGES_PER_ROUND; ++d) {
-                    const int b = (int)(seq % NST);
-                    const unsigned long u = seq / NST;
-                    if (u > 0 && !mbar_wait(&empty[b], (unsigned)((u - 1) & 1))) {
-                        ok = false;
-                        break;
-                    }
-                    tma_issue_stage<T, RB>(ta, Tt, q, d, bufs + b * sb, &full[b]);
-                    ++seq;
-                }
-        }
-        if (!ok) {
-            if (ta.err) atomicExch(ta.err, kTimeoutCode);
-            // let the copies already issued land before the CTA can exit
-            const unsigned long first = seq > (unsigned long)NST ? seq - NST : 0;
-            for (unsigned long s2 = first; s2 < seq; ++s2) mbar_wait(&full[s2 % NST], (unsigned)((s2 / NST) & 1));
-        }
-        return;
-    }
-    const int i = tid % ta.S, sub = tid / ta.S;
-    unsigned long seq = 0;
-    for (long tile = blockIdx.x; tile < ta.ntiles; tile += gridDim.x) {
-        const TmaTile Tt = tma_tile(g, ta.ny, tile);
-        const long site = tma_row_site(g, Tt, i / g.L[0], 0) + i % g.L[0];
-        for (int q = 0; q < ta.rounds; ++q) {
-            cx<A> acc[R][12];
-            for (int d = 0; d < TMA_STAGES_PER_ROUND; ++d, ++seq) {
-                const int b = (int)(seq % NST);
-                if (!mbar_wait(&full[b], (unsigned)((seq / NST) & 1))) {
-                    if (ta.err) atomicExch(ta.err, kTimeoutCode);
-                    return;
-                }
-                tma_consume_stage<T, R, RB, DAG>(ta, d, bufs + b * sb, i, sub, q, acc);
-                __syncwarp();
-                if ((tid & 31) == 0) mbar_arrive(&empty[b]);
-            }
-            const A mh = (A)(-0.5);
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int v = q * RB + sub * R + r;
-                if (v < ta.a.Nv) {
-                    cx<A> o[12];
-#pragma unroll
-                    for (int c = 0; c < 12; ++c) o[c] = cx<A>{mh * acc[r][c].re, mh * acc[r][c].im};
-                    store_spinor<T, 12>(ta.a.out, g.vol, v, site, o);
-                }
-            }
-        }
-    }
-}
-
-// the tile of the TMA variant for sites-per-tile S: ny = S / Lx complete rows
 bool wilson_tma_geometry(const Geom& g, int S, int* ny)
 {
     if (S % 32 || S > 128 || S % g.L[0]) return false;
@@ -147,115 +30,6 @@ size_t wilson_tma_smem(int prec, int R, int S)
     return 256 + (size_t)nst * ((size_t)RB * K * S * 16 + 9 * S * LB);
 }
 
-template <typename T, int R>
-static cudaError_t go_tma(bool dag, const ApplyArgs& a, int S, cudaStream_t st)
-{
-    constexpr int G = 2;
-    int ny = 0;
-    if (!wilson_tma_geometry(a.g, S, &ny)) return cudaErrorInvalidValue;
-    TmaArgs ta;
-    ta.a = a;
-    ta.ny = ny;
-    ta.S = S;
-    ta.ntiles = a.g.vol / S;
-    ta.rounds = (a.Nv + R * G - 1) / (R * G);
-    ta.err = a.err;
-    const int prec = sizeof(T) == 4 ? P_F32 : P_BF16;
-    const size_t smem = wilson_tma_smem(prec, R, S);
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const long grid = ta.ntiles < nsm ? ta.ntiles : nsm;
-    auto kern = dag ? k_wilson_tma<T, R, G, true> : k_wilson_tma<T, R, G, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<(unsigned)grid, G * S + 32, smem, st>>>(ta);
-    return cudaGetLastError();
-}
-
-// pipelined variant: the loads of later hops are in flight in shared memory
-template <typename T, int R, bool DAG, int ST>
-__global__ void __launch_bounds__(256) k_wilson_pipe(ApplyArgs a, int ngroups)
-{
-    extern __shared__ __align__(16) char smem[];
-    const long b = blockIdx.x;
-    const int group = (int)(b % ngroups);
-    const long s = (b / ngroups) * blockDim.x + threadIdx.x;
-    if (s >= a.g.vol) return;   // no block-wide synchronisation follows
-    wilson_site_pipe<T, R, DAG, ST>(a, s, group, smem, threadIdx.x, blockDim.x);
-}
-
-// V_GROUPS: blockDim = (sites, groups); block b covers a run of sites and a
-// chunk of gy right-hand-side groups
-template <typename T, int R, bool DAG>
-__global__ void __launch_bounds__(192, 2) k_wilson_groups(ApplyArgs a, int ngroups, int gy)
-{
-    const int nchunks = (ngroups + gy - 1) / gy;
-    const long b = blockIdx.x;
-    const int group = (int)(b % nchunks) * gy + threadIdx.y;
-    const long s = (b / nchunks) * blockDim.x + threadIdx.x;
-    if (s >= a.g.vol || group >= ngroups) return;
-    wilson_site<T, R, DAG>(a, s, group);
-}
-
-template <typename T, int R>
-static cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
-{
-    const int block = c.block;
-    const int ngroups = (a.Nv + R - 1) / R;
-    const long nblk = ((a.g.vol + block - 1) / block) * (long)ngroups;
-    if (c.variant == V_GROUPS) {
-        const int gy = groups_per_block(block, ngroups);
-        const long nb = ((a.g.vol + block - 1) / block) * (long)((ngroups + gy - 1) / gy);
-        if (dag) k_wilson_groups<T, R, true><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
-        else k_wilson_groups<T, R, false><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
-        return cudaGetLastError();
-    }
-    if (c.variant == V_TMARCH) {
-        const int gy = groups_per_block(block, ngroups);
-        const long vol3 = a.g.stride[3];
-        const int tc = a.g.L[3] < 8 ? a.g.L[3] : 8;
-        const long nb = ((vol3 + block - 1) / block) * (long)((ngroups + gy - 1) / gy) *
-                        (long)((a.g.L[3] + tc - 1) / tc);
-        if (dag) k_wilson_march<T, R, true><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy, tc);
-        else k_wilson_march<T, R, false><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy, tc);
-        return cudaGetLastError();
-    }
-    if (c.variant == V_PIPE3) {
-        const size_t smem = WilsonPipe<T, R>::stage_bytes_per_thread * 3 * block;
-        auto kern = dag ? k_wilson_pipe<T, R, true, 3> : k_wilson_pipe<T, R, false, 3>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        kern<<<(unsigned)nblk, block, smem, st>>>(a, ngroups);
-        return cudaGetLastError();
-    }
-    if (dag) k_wilson<T, R, true><<<(unsigned)nblk, block, 0, st>>>(a, ngroups);
-    else k_wilson<T, R, false><<<(unsigned)nblk, block, 0, st>>>(a, ngroups);
-    return cudaGetLastError();
-}
-
-template <typename T>
-static cudaError_t go_T(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
-{
-    if (c.variant == V_TMA) {
-        if constexpr (sizeof(T) == 8) return cudaErrorInvalidValue;
-        else {
-            switch (c.R) {
-            case 1: return go_tma<T, 1>(dag, a, c.block, st);
-            case 2: return go_tma<T, 2>(dag, a, c.block, st);
-            default: return cudaErrorInvalidValue;
-            }
-        }
-    }
-    switch (c.R) {
-    case 1: return go<T, 1>(dag, a, c, st);
-    case 2: return go<T, 2>(dag, a, c, st);
-    case 3: return go<T, 3>(dag, a, c, st);
-    case 4: return go<T, 4>(dag, a, c, st);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
 size_t wilson_pipe_smem(int prec, int R, int block, int stages)
 {
     const size_t K = prec == P_F64 ? 12 : (prec == P_F32 ? 6 : 3);
@@ -266,10 +40,10 @@ size_t wilson_pipe_smem(int prec, int R, int block, int stages)
 cudaError_t launch_apply_wilson(int prec, bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
 {
     switch (prec) {
-    case P_F64: return go_T<double>(dag, a, c, st);
-    case P_F32: return go_T<float>(dag, a, c, st);
-    case P_BF16: return go_T<__nv_bfloat16>(dag, a, c, st);
-    case P_F16: return go_T<__half>(dag, a, c, st);
+    case P_F64: return wilson_go_T<double>(dag, a, c, st);
+    case P_F32: return wilson_go_T<float>(dag, a, c, st);
+    case P_BF16: return wilson_go_T<__nv_bfloat16>(dag, a, c, st);
+    case P_F16: return wilson_go_T<__half>(dag, a, c, st);
     default: return cudaErrorInvalidValue;
     }
 }

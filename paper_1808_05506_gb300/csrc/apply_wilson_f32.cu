@@ -1,0 +1,6 @@
+// Wilson sweeps with f32 storage (instantiation of apply_wilson_impl.cuh).
+#include "apply_wilson_impl.cuh"
+
+namespace dirac {
+template cudaError_t wilson_go_T<float>(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st);
+}  // namespace dirac

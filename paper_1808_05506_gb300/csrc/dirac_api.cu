@@ -455,6 +455,7 @@ bool apply_config_supported(int op, int prec, int R, int block, int variant, con
     const bool Rok = (op == OP_STAGGERED) ? (R == 1 || R == 2 || R == 4 || R == 6) : (R >= 1 && R <= 4);
     if (!Rok) return false;
     if (variant == V_DIRECT) return true;
+    if (op == OP_WILSON && prec == P_F64) return false;   // FP64 Wilson: direct variant only
     if (variant == V_GROUPS) return block <= 64;
     if (variant == V_TMARCH) return op == OP_WILSON && block <= 64;
     return op == OP_WILSON && variant == V_PIPE3 && wilson_pipe_smem(prec, R, block, 3) <= 227 * 1024;
