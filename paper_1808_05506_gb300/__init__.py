@@ -339,7 +339,7 @@ def config_supported(op: str, prec: str, R: int, block: int, variant: int, L=Non
         if block % Lx or Lx % 4 or Ly % (block // Lx):
             return False
         k, lb, nst = (6, 8, 3) if prec == "f32" else (3, 4, 4)
-        return 256 + nst * (2 * R * k * block * 16 + 9 * block * lb) <= 227 * 1024
+        return 256 + 128 + nst * (2 * R * k * block * 16 + 9 * block * lb) <= 227 * 1024
     if op == "staggered" and R not in (1, 2, 4, 6):
         return False
     if op != "staggered" and not 1 <= R <= 4:

@@ -45,7 +45,8 @@ constexpr int kTimeoutCode = 7;   // DIRAC_TIMEOUT
 template <typename T> struct TmaStages { static constexpr int value = sizeof(T) >= 4 ? 3 : 4; };
 
 template <typename T, int R, int G, bool DAG>
-__global__ void __launch_bounds__(G * 128 + 32, 1) k_wilson_tma(TmaArgs ta)
+__global__ void __launch_bounds__(G * 128 + 32, 1) k_wilson_tma(TmaArgs ta, const __grid_constant__ CUtensorMap mspin,
+                                                                 const __grid_constant__ CUtensorMap mlink)
 {
     constexpr int RB = R * G;
     constexpr int NST = TmaStages<T>::value;
@@ -54,7 +55,8 @@ __global__ void __launch_bounds__(G * 128 + 32, 1) k_wilson_tma(TmaArgs ta)
     extern __shared__ __align__(16) char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + NST;
-    char* bufs = smem + 256;
+    // stage buffers start on a 128-byte boundary (tensor-copy destinations)
+    char* bufs = smem + 256 + ((128u - (smem_u32(smem) & 127u)) & 127u);
     const size_t sb = Lay::stage_bytes(ta.S);
     const int ncons = ta.S * G;
     const int tid = threadIdx.x;
@@ -82,7 +84,7 @@ __global__ void __launch_bounds__(G * 128 + 32, 1) k_wilson_tma(TmaArgs ta)
                         ok = false;
                         break;
                     }
-                    tma_issue_stage<T, RB>(ta, Tt, q, d, bufs + b * sb, &full[b]);
+                    tma_issue_stage<T, RB>(ta, &mspin, &mlink, Tt, q, d, bufs + b * sb, &full[b]);
                     ++seq;
                 }
         }
@@ -95,10 +97,14 @@ __global__ void __launch_bounds__(G * 128 + 32, 1) k_wilson_tma(TmaArgs ta)
         return;
     }
     const int i = tid % ta.S, sub = tid / ta.S;
+    const int j = i / g.L[0], x = i % g.L[0];
     unsigned long seq = 0;
     for (long tile = blockIdx.x; tile < ta.ntiles; tile += gridDim.x) {
         const TmaTile Tt = tma_tile(g, ta.ny, tile);
-        const long site = tma_row_site(g, Tt, i / g.L[0], 0) + i % g.L[0];
+        const long site = tma_row_site(g, Tt, j, 0) + x;
+        // rows whose y neighbour lies across the periodic boundary (outside the box)
+        const long gs_up = (Tt.y0 + ta.ny == g.L[1] && j == ta.ny - 1) ? tma_row_site(g, Tt, j, 1) + x : -1;
+        const long gs_dn = (Tt.y0 == 0 && j == 0) ? tma_row_site(g, Tt, j, 2) + x : -1;
         for (int q = 0; q < ta.rounds; ++q) {
             cx<A> acc[R][12];
             for (int d = 0; d < TMA_STAGES_PER_ROUND; ++d, ++seq) {
@@ -107,7 +113,8 @@ __global__ void __launch_bounds__(G * 128 + 32, 1) k_wilson_tma(TmaArgs ta)
                     if (ta.err) atomicExch(ta.err, kTimeoutCode);
                     return;
                 }
-                tma_consume_stage<T, R, RB, DAG>(ta, d, bufs + b * sb, i, sub, q, acc);
+                tma_consume_stage<T, R, RB, DAG>(ta, d, bufs + b * sb, i, sub, q, acc,
+                                                 d == 1 ? gs_up : (d == 2 ? gs_dn : -1));
                 __syncwarp();
                 if ((tid & 31) == 0) mbar_arrive(&empty[b]);
             }
@@ -137,8 +144,13 @@ cudaError_t go_tma(bool dag, const ApplyArgs& a, int S, cudaStream_t st)
     constexpr int G = 2;
     int ny = 0;
     if (!wilson_tma_geometry(a.g, S, &ny)) return cudaErrorInvalidValue;
+    const int prec0 = sizeof(T) == 4 ? P_F32 : P_BF16;
+    CUtensorMap mspin, mlink;
+    const int P = R * G * SpinorLayout<T, 12>::K;
+    if (!wilson_tma_maps(a, prec0, P, ny, &mspin, &mlink)) return cudaErrorInvalidValue;
     TmaArgs ta;
     ta.a = a;
+    ta.P = P;
     ta.ny = ny;
     ta.S = S;
     ta.ntiles = a.g.vol / S;
@@ -153,7 +165,7 @@ cudaError_t go_tma(bool dag, const ApplyArgs& a, int S, cudaStream_t st)
     auto kern = dag ? k_wilson_tma<T, R, G, true> : k_wilson_tma<T, R, G, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)grid, G * S + 32, smem, st>>>(ta);
+    kern<<<(unsigned)grid, G * S + 32, smem, st>>>(ta, mspin, mlink);
     return cudaGetLastError();
 }
 

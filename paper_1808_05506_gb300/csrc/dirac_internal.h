@@ -48,6 +48,8 @@ inline int groups_per_block(int block, int ngroups)
 bool apply_config_supported(int op, int prec, int R, int block, int variant, const Geom& g);
 size_t wilson_pipe_smem(int prec, int R, int block, int stages);
 bool wilson_tma_geometry(const Geom& g, int S, int* ny);
+// tensor maps (CUtensorMap) of the spinor and link arrays for the TMA sweep
+bool wilson_tma_maps(const ApplyArgs& a, int prec, int P, int ny, void* mspin, void* mlink);
 size_t wilson_tma_smem(int prec, int R, int S);
 
 // out = D in (or D^+ in) on internal-layout fields

@@ -104,16 +104,25 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
                 LaunchCfg c{r, b, pp};
                 std::vector<float> t;
                 cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream);
+                bool launched = true;
                 for (int rep = 0; rep < 7 && st == DIRAC_OK; ++rep) {
                     cudaEventRecord(e0, h->stream);
-                    st = h->run_apply(false, h->ws_out, h->ws_in, h->Nv, h->diag, h->links, h->prec, c);
+                    const dirac_status ls =
+                        h->run_apply(false, h->ws_out, h->ws_in, h->Nv, h->diag, h->links, h->prec, c);
+                    if (ls != DIRAC_OK) {
+                        // this launch shape cannot run here (e.g. no tensor-map support): skip it
+                        cudaGetLastError();
+                        launched = false;
+                        break;
+                    }
                     cudaEventRecord(e1, h->stream);
-                    if (st == DIRAC_OK) st = h->cuda(cudaEventSynchronize(e1), "autotune");
+                    st = h->cuda(cudaEventSynchronize(e1), "autotune");
                     float ms = 0.f;
                     cudaEventElapsedTime(&ms, e0, e1);
                     if (rep >= 2) t.push_back(ms);   // two warm-up calls
                 }
                 if (st) break;
+                if (!launched) continue;
                 int kerr = 0;
                 cudaMemcpy(&kerr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
                 if (kerr) {   // a bounded wait ran out in this variant: never pick it

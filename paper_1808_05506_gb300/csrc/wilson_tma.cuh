@@ -5,10 +5,14 @@
 // right-hand sides it streams seven stages through a ring of shared-memory
 // buffers: the tile itself (with the forward x-links), the y+1 / y-1 rows,
 // the z+1 / z-1 and t+1 / t-1 tiles, each with the link planes its hop needs.
-// One producer warp issues the bulk copies (cp.async.bulk, completion counted
-// in bytes on an mbarrier); the consumer warps wait for a stage, apply its
-// hop to R right-hand sides from shared memory, and release the buffer.  The
-// loads therefore stay in flight without occupying registers or the LSU.
+// One producer thread issues two tensor copies per stage (cp.async.bulk.tensor
+// over 5-D views of the spinor and link arrays, completion counted in bytes
+// on an mbarrier); the consumer warps wait for a stage, apply its hop to R
+// right-hand sides from shared memory, and release the buffer.  The loads
+// therefore stay in flight without occupying registers or the LSU.
+// Tensor copies do not wrap around the periodic boundary: where a y stage
+// crosses it, the box row outside the lattice is zero-filled and the threads
+// of that row read their neighbour from global memory instead.
 //
 // Stage buffer layout: spinor planes [RB][K][S] of 16-byte elements, then the
 // 9 link planes [9][S] of one complex each.  The x-hops use the centre tile
@@ -20,6 +24,7 @@
 // shared memory.
 #pragma once
 
+#include <cuda.h>
 #include <type_traits>
 
 #include "dirac_kernels.cuh"
@@ -27,10 +32,11 @@
 namespace dirac {
 
 constexpr int TMA_STAGES_PER_ROUND = 7;   // centre, y+, y-, z+, z-, t+, t-
-constexpr unsigned TMA_SPIN_LIMIT = 1u << 22;
+constexpr unsigned TMA_SPIN_LIMIT = 1u << 25;   // about 1-2 s with the 32 ns back-off
 
 struct TmaArgs {
     ApplyArgs a;
+    int P;           // spinor planes per stage = RB * K
     int ny;          // rows per tile
     int S;           // sites per tile = Lx * ny
     long ntiles;     // number of tiles = vol / S
@@ -109,7 +115,7 @@ DEV_INLINE bool mbar_wait(uint64_t* bar, unsigned parity)
     for (unsigned it = 0; it < TMA_SPIN_LIMIT; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
 #if defined(__CUDA_ARCH__)
-        if (it > 64) __nanosleep(200);
+        if (it > 256) __nanosleep(32);
 #endif
     }
     return false;
@@ -129,6 +135,20 @@ DEV_INLINE void bulk_copy(void* dst, const void* src, unsigned bytes, uint64_t* 
     char* d = static_cast<char*>(dst);
     for (unsigned i = 0; i < bytes; ++i) d[i] = s[i];
     (void)bar;
+#endif
+}
+
+// 5-D tensor copy global -> shared (box given by the tensor map)
+DEV_INLINE void tensor_copy5(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4, uint64_t* bar)
+{
+#if defined(__CUDA_ARCH__)
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5, %6}], [%7];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+        : "memory");
+#else
+    (void)dst; (void)map; (void)c0; (void)c1; (void)c2; (void)c3; (void)c4; (void)bar;
 #endif
 }
 
@@ -184,46 +204,81 @@ DEV_INLINE long tma_link_row_site(const Geom& g, const TmaTile& T, int j, int d)
 }
 DEV_INLINE int tma_link_mu(int d) { return (d + 1) / 2; }   // 0:x 1,2:y 3,4:z 5,6:t
 
-// Producer: issue the copies of stage d of round q for tile T into buf.
+// zt coordinate and first y row of the box stage d holds for tile T (y may be
+// -1 or Ly - ny + 1 .. Ly: the row outside the lattice is zero-filled)
+DEV_INLINE void tma_stage_coords(const Geom& g, const TmaTile& T, int d, int* y, int* zt)
+{
+    int yy = T.y0, z = T.z, t = T.t;
+    switch (d) {
+    case 1: yy += 1; break;
+    case 2: yy -= 1; break;
+    case 3: z = (z + 1) % g.L[2]; break;
+    case 4: z = (z + g.L[2] - 1) % g.L[2]; break;
+    case 5: t = (t + 1) % g.L[3]; break;
+    case 6: t = (t + g.L[3] - 1) % g.L[3]; break;
+    default: break;
+    }
+    *y = yy;
+    *zt = z + g.L[2] * t;
+}
+
+// Producer: issue the two tensor copies of stage d of round q for tile T.
 template <typename T_, int RB>
-DEV_INLINE void tma_issue_stage(const TmaArgs& ta, const TmaTile& T, int q, int d, char* buf, uint64_t* full)
+DEV_INLINE void tma_issue_stage(const TmaArgs& ta, const CUtensorMap* mspin, const CUtensorMap* mlink,
+                                const TmaTile& T, int q, int d, char* buf, uint64_t* full)
 {
     using Lay = TmaLayout<T_, RB>;
-    const Geom& g = ta.a.g;
-    const int S = ta.S, Lx = g.L[0];
-    mbar_arrive_expect_tx(full, (unsigned)Lay::stage_bytes(S));
-    const char* in = static_cast<const char*>(ta.a.in);
-    const char* lk = static_cast<const char*>(ta.a.links);
-    const int mu = tma_link_mu(d);
-    char* lbase = buf + (size_t)RB * Lay::K * S * 16;
-    // the tile's rows are one contiguous run unless a y stage wraps around
-    const bool one_run = (d == 1) ? (T.y0 + ta.ny < g.L[1]) : (d == 2 ? T.y0 > 0 : true);
-    const int nrun = one_run ? 1 : ta.ny;
-    const int run_sites = one_run ? S : Lx;
-    for (int j = 0; j < nrun; ++j) {
-        const long rs = tma_row_site(g, T, j, d);
-        for (int r = 0; r < RB; ++r) {
-            const int v = min(q * RB + r, ta.a.Nv - 1);
-            for (int k = 0; k < Lay::K; ++k) {
-                const size_t gi = ((size_t)v * Lay::K + k) * g.vol + (size_t)rs;
-                char* dst = buf + (((size_t)r * Lay::K + k) * S + (size_t)j * Lx) * 16;
-                bulk_copy(dst, in + gi * 16, (unsigned)(run_sites * 16), full);
-            }
-        }
-        const long ls = tma_link_row_site(g, T, j, d);
-        for (int e = 0; e < 9; ++e) {
-            const size_t gi = ((size_t)mu * 9 + e) * g.vol + (size_t)ls;
-            bulk_copy(lbase + ((size_t)e * S + (size_t)j * Lx) * Lay::LB, lk + gi * Lay::LB,
-                      (unsigned)(run_sites * Lay::LB), full);
-        }
+    mbar_arrive_expect_tx(full, (unsigned)Lay::stage_bytes(ta.S));
+    int y, zt;
+    tma_stage_coords(ta.a.g, T, d, &y, &zt);
+#if !defined(__CUDA_ARCH__)
+    {
+        // host emulation of the two boxes (rows outside the lattice read as zero)
+        const Geom& g = ta.a.g;
+        const int Lx = g.L[0];
+        auto box = [&](const char* src, size_t plane_bytes, int row_bytes, int plane0, int nplanes, int nvalid,
+                       int yb, int ztb, char* dst) {
+            for (int p = 0; p < nplanes; ++p)
+                for (int j = 0; j < ta.ny; ++j) {
+                    char* o = dst + ((size_t)p * ta.ny + j) * row_bytes;
+                    const int yy = yb + j;
+                    if (plane0 + p >= nvalid || yy < 0 || yy >= g.L[1]) {
+                        for (int b = 0; b < row_bytes; ++b) o[b] = 0;
+                        continue;
+                    }
+                    const char* s2 = src + (size_t)(plane0 + p) * plane_bytes +
+                                     ((size_t)ztb * g.L[1] + yy) * (size_t)row_bytes;
+                    for (int b = 0; b < row_bytes; ++b) o[b] = s2[b];
+                }
+        };
+        box(static_cast<const char*>(ta.a.in), (size_t)g.vol * 16, Lx * 16, q * ta.P, ta.P,
+            ta.a.Nv * Lay::K, y, zt, buf);
+        int ly = y, lzt = zt;
+        if (d == 1 || d == 3 || d == 5) tma_stage_coords(g, T, 0, &ly, &lzt);
+        box(static_cast<const char*>(ta.a.links), (size_t)g.vol * Lay::LB, Lx * Lay::LB, tma_link_mu(d) * 9, 9, 36,
+            ly, lzt, buf + (size_t)ta.P * ta.S * 16);
+        (void)mspin;
+        (void)mlink;
+        return;
     }
+#endif
+    // spinor planes [q*RB*K, q*RB*K + P) of the box rows; planes past Nv*K read as zero
+    tensor_copy5(buf, mspin, 0, 0, y, zt, q * ta.P, full);
+    // link planes mu*9 .. mu*9+8 of the forward rows (d = 0, 1, 3, 5) or of the
+    // neighbour rows (d = 2, 4, 6: the backward hop's V_mu(x - mu))
+    int ly = y, lzt = zt;
+    if (d == 1 || d == 3 || d == 5) tma_stage_coords(ta.a.g, T, 0, &ly, &lzt);
+    tensor_copy5(buf + (size_t)ta.P * ta.S * 16, mlink, 0, 0, ly, lzt, tma_link_mu(d) * 9, full);
 }
 
 // Consumer: apply stage d of the current round to this thread's R
 // right-hand sides (sub-group sub covers r_local = sub * R .. sub * R + R - 1).
+// gsite >= 0: this thread's neighbour row fell outside the box (a y stage
+// crossing the periodic boundary): read the spinors at site gsite and, for
+// the backward y hop, the link at gsite from global memory instead
 template <typename T_, int R, int RB, bool DAG>
 DEV_INLINE void tma_consume_stage(const TmaArgs& ta, int d, const char* buf, int i, int sub, int q,
-                                  cx<typename Store<T_>::A> (&acc)[R][12])
+                                  cx<typename Store<T_>::A> (&acc)[R][12], long gsite = -1)
 {
     using A = typename Store<T_>::A;
     using Lay = TmaLayout<T_, RB>;
@@ -231,6 +286,10 @@ DEV_INLINE void tma_consume_stage(const TmaArgs& ta, int d, const char* buf, int
     const int S = ta.S, Lx = ta.a.g.L[0];
     const char* lbase = buf + (size_t)RB * Lay::K * S * 16;
     auto spinor = [&](int rl, int idx, cx<A>* p) {
+        if (gsite >= 0) {
+            load_spinor<T_, 12>(ta.a.in, ta.a.g.vol, min(q * RB + rl, ta.a.Nv - 1), gsite, p);
+            return;
+        }
 #pragma unroll
         for (int k = 0; k < Lay::K; ++k) {
             const char* src = buf + (((size_t)rl * Lay::K + k) * S + idx) * 16;
@@ -239,6 +298,10 @@ DEV_INLINE void tma_consume_stage(const TmaArgs& ta, int d, const char* buf, int
         }
     };
     auto link = [&](int idx, cx<A>* U) {
+        if (gsite >= 0 && d == 2) {
+            load_link<T_>(ta.a.links, ta.a.g.vol, 1, gsite, U);
+            return;
+        }
 #pragma unroll
         for (int e = 0; e < 9; ++e) U[e] = sm_one<T_>(lbase + ((size_t)e * S + idx) * Lay::LB);
     };
