@@ -295,12 +295,16 @@ def main():
     ap.add_argument("--lattice", default=None, help="Nx,Ny,Nz,Nt (a smaller case for profiling)")
     ap.add_argument("--prec", default=None, choices=["f32", "bf16", "f16", "f64"])
     ap.add_argument("--kernel", default=None, help="R,block,variant: fixed launch shape instead of the autotuner")
+    ap.add_argument("--op", default="wilson", choices=["wilson", "staggered", "brillouin"],
+                    help="operator of the timed sweep (the default workload is Wilson; the others are for profiling)")
     args = ap.parse_args()
     global WORKLOAD
     if args.lattice:
         WORKLOAD = dict(WORKLOAD, L=tuple(int(v) for v in args.lattice.split(",")))
     if args.prec:
         WORKLOAD = dict(WORKLOAD, prec=args.prec)
+    if args.op != "wilson":
+        WORKLOAD = dict(WORKLOAD, op=args.op, mass=0.05 if args.op == "brillouin" else 0.0)
     if args.impl == "reference":
         return run_reference(args)
     args.warmup = max(3, args.warmup)
@@ -313,7 +317,8 @@ def main():
 
     w = WORKLOAD
     V, psi = gen_inputs(w)
-    D = dg.Dirac(w["op"], w["L"], w["Nv"], w["mass"], w["prec"])
+    op = w["op"]
+    D = dg.Dirac(op, w["L"], w["Nv"], w["mass"], w["prec"])
     D.set_links(torch.from_numpy(V).cuda())
     if args.kernel:
         D.set_kernel_config(*(int(v) for v in args.kernel.split(",")))
@@ -323,9 +328,9 @@ def main():
     x = D.pack(xin)
     y = D.new_internal()
     vol = int(np.prod(w["L"]))
-    workload = "wilson_apply_{}_nv{}_{}".format("x".join(map(str, w["L"])), w["Nv"], w["prec"])
-    flops_step = dg.flops_per_site_rhs("wilson") * vol * w["Nv"]
-    bytes_step = dg.bytes_per_site("wilson", w["Nv"], w["prec"]) * vol
+    workload = "{}_apply_{}_nv{}_{}".format(op, "x".join(map(str, w["L"])), w["Nv"], w["prec"])
+    flops_step = dg.flops_per_site_rhs(op) * vol * w["Nv"]
+    bytes_step = dg.bytes_per_site(op, w["Nv"], w["prec"]) * vol
     if bytes_step < 4 * 129e6:
         raise SystemExit("the timed step must stream more than the L2 (use a larger --lattice)")
 
@@ -378,7 +383,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "Gflop/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if w["prec"] != "f64" else "f64", "data": "synthetic",
-        "config": {"workload": workload, "op": "wilson", "storage": w["prec"], "lattice": list(w["L"]),
+        "config": {"workload": workload, "op": op, "storage": w["prec"], "lattice": list(w["L"]),
                    "Nc": 3, "Nv": w["Nv"], "kappa": w["mass"], "links": "exp(0.3 i H), H traceless Gaussian",
                    "source": "complex Gaussian N(0,1)", "layout": "internal site-fastest SoA",
                    "l2": "no flush: each step streams {:.2f} GB > 129 MB L2".format(bytes_step / 1e9),
@@ -387,7 +392,9 @@ def main():
         "hbm_gbs": achieved,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
-                     "peak_kind": f"{peak_kind} copy bandwidth", "kernel": "k_wilson<float,R,false>",
+                     "peak_kind": f"{peak_kind} copy bandwidth",
+                     "kernel": "k_{}{}<{},R={}>".format(op, {0: "", 1: "_groups", 2: "_march", 3: "_pipe", 4: "_tma"}[cfg[2]],
+                                                      w["prec"], cfg[0]),
                      "algorithmic_bytes_per_launch": bytes_step},
         "clocks": clk.summary(),
         "e2e": {"value": flops_step / (e2e_ms * 1e-3) / 1e9, "unit": "Gflop/s", "ms_per_step": e2e_ms,
