@@ -122,6 +122,8 @@ void brillouin_tables(BriDir dirs[80], int rep_dir81[40])
         D.q[2] = (r * -dy); D.q[3] = (r * -dx);   // Q01
         D.q[4] = (r * dy);  D.q[5] = (r * -dx);   // Q10
         D.q[6] = (r * dt);  D.q[7] = (r * dz);    // Q11
+        D.af = (float)D.a;
+        for (int e = 0; e < 8; ++e) D.qf[e] = (float)D.q[e];
     }
 }
 

@@ -18,10 +18,9 @@ __global__ void __launch_bounds__(256) k_wilson(ApplyArgs a, int ngroups)
     wilson_site<T, R, DAG>(a, s, group);
 }
 
-// V_TMARCH: blockDim = (sites, groups); a block owns a run of `block` sites of
-// one t-slice (index s3 within the slice) and walks TC consecutive slices, so
-// the t-neighbours and backward t-links it needs were read by this block one
-// step earlier and are still in L1
+// V_TMARCH: blockDim = (sites, groups); a block owns a run of `block` site
+// columns of the (x, y, z) volume and walks `tc` consecutive t-slices with
+// the t hops carried in registers (wilson_column)
 template <typename T, int R, bool DAG>
 __global__ void __launch_bounds__(192, 2) k_wilson_march(ApplyArgs a, int ngroups, int gy, int tc)
 {
@@ -34,8 +33,7 @@ __global__ void __launch_bounds__(192, 2) k_wilson_march(ApplyArgs a, int ngroup
     const long s3 = (b % nruns) * blockDim.x + threadIdx.x;
     const int t0 = (int)(b / nruns) * tc;
     if (s3 >= vol3 || group >= ngroups) return;
-    const int t1 = min(t0 + tc, a.g.L[3]);
-    for (int t = t0; t < t1; ++t) wilson_site<T, R, DAG, true>(a, s3 + vol3 * t, group);
+    wilson_column<T, R, DAG>(a, s3, group, t0, min(t0 + tc, a.g.L[3]));
 }
 
 // V_TMA: persistent CTAs; one producer warp streams the stages of each tile

@@ -457,7 +457,7 @@ bool apply_config_supported(int op, int prec, int R, int block, int variant, con
     if (variant == V_DIRECT) return true;
     if (op == OP_WILSON && prec == P_F64) return false;   // FP64 Wilson: direct variant only
     if (variant == V_GROUPS) return block <= 64;
-    if (variant == V_TMARCH) return op == OP_WILSON && block <= 64;
+    if (variant == V_TMARCH) return op == OP_WILSON && block <= 128;
     return op == OP_WILSON && variant == V_PIPE3 && wilson_pipe_smem(prec, R, block, 3) <= 227 * 1024;
 }
 

@@ -363,6 +363,78 @@ DEV_INLINE void load_link(const void* base, size_t vol, int m, long s, cx<typena
     for (int e = 0; e < 9; ++e) U[e] = ld_one<T>(base, ((size_t)m * 9 + e) * vol + (size_t)s);
 }
 
+// ---- packed FP32 pairs: one fma.rn.f32x2 does the (re, im) halves of a
+// complex update, halving the issue slots of complex arithmetic.  Used by the
+// Brillouin sweep, which is issue-bound; the Wilson and staggered sweeps keep
+// scalar FMAs (the register pairs cost them occupancy and they are bound by
+// memory latency, not by issue)
+struct f2 { float x, y; };
+DEV_INLINE f2 ffma2(f2 a, f2 b, f2 c)
+{
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+    unsigned long long ra, rb, rc, rd;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rc) : "f"(c.x), "f"(c.y));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+    f2 d;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+    return d;
+#else
+    return f2{fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y)};
+#endif
+}
+// acc += s * u  (s real)
+DEV_INLINE cx<float> caxpy2(float s, cx<float> u, cx<float> acc)
+{
+    f2 r = ffma2(f2{s, s}, f2{u.re, u.im}, f2{acc.re, acc.im});
+    return {r.x, r.y};
+}
+// acc += a * b as two packed FMAs: acc += a.re (b.re, b.im) + a.im (-b.im, b.re)
+DEV_INLINE cx<float> cfma2(cx<float> a, cx<float> b, cx<float> acc)
+{
+    f2 r = ffma2(f2{a.re, a.re}, f2{b.re, b.im}, f2{acc.re, acc.im});
+    r = ffma2(f2{a.im, a.im}, f2{-b.im, b.re}, r);
+    return {r.x, r.y};
+}
+// acc += conj(a) * b: acc += a.re (b.re, b.im) + a.im (b.im, -b.re)
+DEV_INLINE cx<float> cfma2_conj(cx<float> a, cx<float> b, cx<float> acc)
+{
+    f2 r = ffma2(f2{a.re, a.re}, f2{b.re, b.im}, f2{acc.re, acc.im});
+    r = ffma2(f2{a.im, a.im}, f2{b.im, -b.re}, r);
+    return {r.x, r.y};
+}
+// acc += U h (3x3 times 3) with packed FMAs: broadcast each h_b, rotate U once
+DEV_INLINE void mat_vec_acc2(const cx<float>* U, const cx<float>* h, cx<float>* acc)
+{
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const f2 hr{h[b].re, h[b].re}, hi{h[b].im, h[b].im};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const cx<float> u = U[3 * a + b];
+            f2 r = ffma2(hr, f2{u.re, u.im}, f2{acc[a].re, acc[a].im});
+            r = ffma2(hi, f2{-u.im, u.re}, r);
+            acc[a] = {r.x, r.y};
+        }
+    }
+}
+// acc += U^dagger h
+DEV_INLINE void mat_dag_vec_acc2(const cx<float>* U, const cx<float>* h, cx<float>* acc)
+{
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const f2 hr{h[b].re, h[b].re}, hi{h[b].im, h[b].im};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const cx<float> u = U[3 * b + a];   // (U^dagger)_ab = conj(U_ba)
+            f2 r = ffma2(hr, f2{u.re, -u.im}, f2{acc[a].re, acc[a].im});
+            r = ffma2(hi, f2{u.im, u.re}, r);
+            acc[a] = {r.x, r.y};
+        }
+    }
+}
+
 // w = U h  /  w = U^dagger h   (3-vectors)
 template <typename A> HD void mat_vec(const cx<A>* U, const cx<A>* h, cx<A>* w)
 {

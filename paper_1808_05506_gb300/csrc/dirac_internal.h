@@ -25,8 +25,8 @@ enum Variant {
                     // site sit in consecutive blocks
     V_GROUPS = 1,   // the groups of the same sites share a block (blockDim.y), so each
                     // link is fetched from L2 once per block and reused through L1
-    V_TMARCH = 2,   // Wilson: V_GROUPS, and each block walks 8 consecutive t-slices so that
-                    // the t-neighbours come from L1; y/z loads bypass L1
+    V_TMARCH = 2,   // Wilson: V_GROUPS over (x, y, z) site columns, each thread walking up to
+                    // 8 consecutive t-slices with the t hops carried in registers
     V_PIPE3 = 3,    // Wilson: V_DIRECT with a 3-stage cp.async pipeline in shared memory
     V_TMA = 4       // Wilson (FP32/BF16/FP16): tiles of complete x-rows streamed by bulk copies
                     // (one producer warp, mbarrier ring); `block` = sites per tile

@@ -104,9 +104,7 @@ DEV_INLINE void wilson_hop(const ApplyArgs& a, long nbr, long lsite, int v0,
     }
 }
 
-// MARCH: the caller walks along t with L1 keeping the t-neighbours, so the
-// y and z hops (which no other warp of this block will reuse) bypass L1
-template <typename T, int R, bool DAG, bool MARCH = false>
+template <typename T, int R, bool DAG>
 DEV_INLINE void wilson_site(const ApplyArgs& a, long s, int group)
 {
     using A = typename Store<T>::A;
@@ -124,10 +122,10 @@ DEV_INLINE void wilson_site(const ApplyArgs& a, long s, int group)
     constexpr int SB = -SF;
     wilson_hop<T, R, 0, SF, false>(a, s + fwd[0], s, v0, acc);
     wilson_hop<T, R, 0, SB, true>(a, s + bwd[0], s + bwd[0], v0, acc);
-    wilson_hop<T, R, 1, SF, false, MARCH>(a, s + fwd[1], s, v0, acc);
-    wilson_hop<T, R, 1, SB, true, MARCH>(a, s + bwd[1], s + bwd[1], v0, acc);
-    wilson_hop<T, R, 2, SF, false, MARCH>(a, s + fwd[2], s, v0, acc);
-    wilson_hop<T, R, 2, SB, true, MARCH>(a, s + bwd[2], s + bwd[2], v0, acc);
+    wilson_hop<T, R, 1, SF, false>(a, s + fwd[1], s, v0, acc);
+    wilson_hop<T, R, 1, SB, true>(a, s + bwd[1], s + bwd[1], v0, acc);
+    wilson_hop<T, R, 2, SF, false>(a, s + fwd[2], s, v0, acc);
+    wilson_hop<T, R, 2, SB, true>(a, s + bwd[2], s + bwd[2], v0, acc);
     wilson_hop<T, R, 3, SF, false>(a, s + fwd[3], s, v0, acc);
     wilson_hop<T, R, 3, SB, true>(a, s + bwd[3], s + bwd[3], v0, acc);
     const A mh = (A)(-0.5);
@@ -145,6 +143,90 @@ DEV_INLINE void wilson_site(const ApplyArgs& a, long s, int group)
             p[i] = o;
         }
         if (v0 + r < a.Nv) store_spinor<T, 12>(a.out, a.g.vol, v0 + r, s, p);
+    }
+}
+
+// ---------------------------------------------------------------- Wilson, t-march
+// One thread owns the site column (x, y, z) for the slices t0 <= t < t1 and
+// one group of R right-hand sides.  Along t each spinor and each t-link is
+// read once: psi(t + 1), loaded for the forward t hop of slice t, is the
+// diagonal term of slice t + 1, and U_t(t), loaded for that hop, also forms
+// the backward t hop of slice t + 1, U_t(t)^+ (1 + S gamma_4) psi(t), which
+// is carried to the next step as a half spinor.  Only the x, y and z hops go
+// to memory at every step.
+template <typename T, int R, bool DAG>
+DEV_INLINE void wilson_column(const ApplyArgs& a, long s3, int group, int t0, int t1)
+{
+    using A = typename Store<T>::A;
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int SB = -SF;
+    const long vol3 = a.g.stride[3];
+    const int Lt = a.g.L[3];
+    const int v0 = group * R;
+    long fwd[4], bwd[4];
+    int x[4];
+    site_offsets(a.g, s3, fwd, bwd, x);   // x, y, z offsets do not depend on t
+    cx<A> pc[R][12];   // psi(t)
+    cx<A> hb[R][6];    // U_t(t - 1)^+ (1 + SB gamma_4) psi(t - 1)
+    {
+        const long sp = s3 + vol3 * (t0 == 0 ? Lt - 1 : t0 - 1);
+        cx<A> U[9];
+        load_link<T>(a.links, a.g.vol, 3, sp, U);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int v = min(v0 + r, a.Nv - 1);
+            cx<A> p[12], h[6];
+            load_spinor<T, 12>(a.in, a.g.vol, v, sp, p);
+            wilson_project<3, SB>(p, h);
+            mat_dag_vec(U, h, hb[r]);
+            mat_dag_vec(U, h + 3, hb[r] + 3);
+            load_spinor<T, 12>(a.in, a.g.vol, v, s3 + vol3 * t0, pc[r]);
+        }
+    }
+    const A mh = (A)(-0.5);
+#pragma unroll 1
+    for (int t = t0; t < t1; ++t) {
+        const long s = s3 + vol3 * t;
+        const long sn = s3 + vol3 * (t + 1 == Lt ? 0 : t + 1);
+        cx<A> acc[R][12];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int i = 0; i < 12; ++i) acc[r][i] = cx<A>{A(0), A(0)};
+        wilson_hop<T, R, 0, SF, false>(a, s + fwd[0], s, v0, acc);
+        wilson_hop<T, R, 0, SB, true>(a, s + bwd[0], s + bwd[0], v0, acc);
+        wilson_hop<T, R, 1, SF, false>(a, s + fwd[1], s, v0, acc);
+        wilson_hop<T, R, 1, SB, true>(a, s + bwd[1], s + bwd[1], v0, acc);
+        wilson_hop<T, R, 2, SF, false>(a, s + fwd[2], s, v0, acc);
+        wilson_hop<T, R, 2, SB, true>(a, s + bwd[2], s + bwd[2], v0, acc);
+        cx<A> U[9];
+        load_link<T>(a.links, a.g.vol, 3, s, U);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int v = min(v0 + r, a.Nv - 1);
+            cx<A> pn[12], h[6], w[6];
+            load_spinor<T, 12>(a.in, a.g.vol, v, sn, pn);
+            // forward t hop of slice t, then the carried backward hop
+            wilson_project<3, SF>(pn, h);
+            mat_vec(U, h, w);
+            mat_vec(U, h + 3, w + 3);
+            wilson_reconstruct<3, SF>(w, acc[r]);
+            wilson_reconstruct<3, SB>(hb[r], acc[r]);
+            // backward t hop of slice t + 1
+            wilson_project<3, SB>(pc[r], h);
+            mat_dag_vec(U, h, hb[r]);
+            mat_dag_vec(U, h + 3, hb[r] + 3);
+            const A dg = diag_of<A>(a, v);
+#pragma unroll
+            for (int i = 0; i < 12; ++i) {
+                cx<A> o;
+                o.re = fma(mh, acc[r][i].re, dg * pc[r][i].re);
+                o.im = fma(mh, acc[r][i].im, dg * pc[r][i].im);
+                acc[r][i] = o;
+                pc[r][i] = pn[i];
+            }
+            if (v0 + r < a.Nv) store_spinor<T, 12>(a.out, a.g.vol, v0 + r, s, acc[r]);
+        }
     }
 }
 
@@ -400,6 +482,8 @@ struct BriDir {
     signed char neg;     // 1: W_dir(x) = W_rep(x + dir)^+
     double a;            // -lambda_k / 2
     double q[8];         // rho_k Q: q00 re, im, q01 re, im, q10 re, im, q11 re, im
+    float af;            // the same coefficients rounded to FP32, for the FP32 sweeps (no
+    float qf[8];         // FP64 -> FP32 conversions in the inner loop)
 };
 
 template <typename A> struct BriDirA { A a; cx<A> q00, q01, q10, q11; };
@@ -409,18 +493,38 @@ HD BriDirA<A> bri_coeffs(const BriDir& D)
 {
     BriDirA<A> c;
     const A sg = DAG ? A(-1) : A(1);
-    c.a = (A)D.a;
-    c.q00 = {sg * (A)D.q[0], sg * (A)D.q[1]};
-    c.q01 = {sg * (A)D.q[2], sg * (A)D.q[3]};
-    c.q10 = {sg * (A)D.q[4], sg * (A)D.q[5]};
-    c.q11 = {sg * (A)D.q[6], sg * (A)D.q[7]};
+    if constexpr (sizeof(A) == 4) {
+        c.a = D.af;
+        c.q00 = {sg * D.qf[0], sg * D.qf[1]};
+        c.q01 = {sg * D.qf[2], sg * D.qf[3]};
+        c.q10 = {sg * D.qf[4], sg * D.qf[5]};
+        c.q11 = {sg * D.qf[6], sg * D.qf[7]};
+    } else {
+        c.a = (A)D.a;
+        c.q00 = {sg * (A)D.q[0], sg * (A)D.q[1]};
+        c.q01 = {sg * (A)D.q[2], sg * (A)D.q[3]};
+        c.q10 = {sg * (A)D.q[4], sg * (A)D.q[5]};
+        c.q11 = {sg * (A)D.q[6], sg * (A)D.q[7]};
+    }
     return c;
 }
 
 // chi = M psi
 template <typename A>
-HD void bri_spin(const BriDirA<A>& m, const cx<A>* p, cx<A>* chi)
+DEV_INLINE void bri_spin(const BriDirA<A>& m, const cx<A>* p, cx<A>* chi)
 {
+    if constexpr (sizeof(A) == 4) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            cx<A> u0 = p[c], u1 = p[3 + c], d0 = p[6 + c], d1 = p[9 + c];
+            cx<A> t;
+            t = cx<A>{m.a * u0.re, m.a * u0.im}; t = cfma2(m.q00, d0, t); chi[c] = cfma2(m.q01, d1, t);
+            t = cx<A>{m.a * u1.re, m.a * u1.im}; t = cfma2(m.q10, d0, t); chi[3 + c] = cfma2(m.q11, d1, t);
+            t = cx<A>{m.a * d0.re, m.a * d0.im}; t = cfma2_conj(m.q00, u0, t); chi[6 + c] = cfma2_conj(m.q10, u1, t);
+            t = cx<A>{m.a * d1.re, m.a * d1.im}; t = cfma2_conj(m.q01, u0, t); chi[9 + c] = cfma2_conj(m.q11, u1, t);
+        }
+        return;
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         cx<A> u0 = p[c], u1 = p[3 + c], d0 = p[6 + c], d1 = p[9 + c];
@@ -445,9 +549,9 @@ DEV_INLINE void brillouin_site(const ApplyArgs& a, long s, int group, const BriD
     for (int r = 0; r < R; ++r)
 #pragma unroll
         for (int i = 0; i < 12; ++i) acc[r][i] = cx<A>{A(0), A(0)};
-#pragma unroll 1
+#pragma unroll 2
     for (int j = 0; j < 80; ++j) {
-        const BriDir D = dirs[j];
+        const BriDir& D = dirs[j];
         long nbr = s;
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) nbr += (D.d[mu] > 0) ? fwd[mu] : (D.d[mu] < 0 ? bwd[mu] : 0);
@@ -462,8 +566,13 @@ DEV_INLINE void brillouin_site(const ApplyArgs& a, long s, int group, const BriD
             bri_spin(m, p, chi);
 #pragma unroll
             for (int sp = 0; sp < 4; ++sp) {
-                if (D.neg) mat_dag_vec_acc(W, chi + 3 * sp, acc[r] + 3 * sp);
-                else mat_vec_acc(W, chi + 3 * sp, acc[r] + 3 * sp);
+                if constexpr (sizeof(A) == 4) {
+                    if (D.neg) mat_dag_vec_acc2(W, chi + 3 * sp, acc[r] + 3 * sp);
+                    else mat_vec_acc2(W, chi + 3 * sp, acc[r] + 3 * sp);
+                } else {
+                    if (D.neg) mat_dag_vec_acc(W, chi + 3 * sp, acc[r] + 3 * sp);
+                    else mat_vec_acc(W, chi + 3 * sp, acc[r] + 3 * sp);
+                }
             }
         }
     }
