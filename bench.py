@@ -41,6 +41,9 @@ PAPER_CONTEXT = {"wilson_sp_knl_gflops": 345, "staggered_sp_knl_gflops": 475,
                  "brillouin_sp_knl_gflops": 790, "note": "one 68-core KNL node, Nc=3, Nv=12 (abstract)"}
 KERNEL_SOURCES = ["paper_1808_05506_gb300/csrc/dirac_kernels.cuh",
                   "paper_1808_05506_gb300/csrc/dirac_common.cuh",
+                  "paper_1808_05506_gb300/csrc/apply_wilson_impl.cuh",
+                  "paper_1808_05506_gb300/csrc/wilson_tma.cuh",
+                  "paper_1808_05506_gb300/csrc/apply_wilson_f32.cu",
                   "paper_1808_05506_gb300/csrc/apply_wilson.cu"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "wilson_apply_traffic.json")
 
@@ -163,9 +166,10 @@ def sweep_rate(dg, torch, w, steps, warmup):
     flops = dg.flops_per_site_rhs(w["op"]) * vol * w["Nv"]
     byts = dg.bytes_per_site(w["op"], w["Nv"], w["prec"]) * vol
     cfg = D.kernel_config()
+    order = D.site_order()
     D.close()
     return {"gflops": flops / t / 1e9, "gbs": byts / t / 1e9, "ms": t * 1e3, "R": cfg[0], "block": cfg[1],
-            "variant": cfg[2]}
+            "variant": cfg[2], "site_order_tchunk": order}
 
 
 class OracleSample:
@@ -294,7 +298,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--lattice", default=None, help="Nx,Ny,Nz,Nt (a smaller case for profiling)")
     ap.add_argument("--prec", default=None, choices=["f32", "bf16", "f16", "f64"])
-    ap.add_argument("--kernel", default=None, help="R,block,variant: fixed launch shape instead of the autotuner")
+    ap.add_argument("--kernel", default=None,
+                    help="R,block,variant[,tchunk]: fixed launch shape (and site order) instead of the autotuner")
     ap.add_argument("--op", default="wilson", choices=["wilson", "staggered", "brillouin"],
                     help="operator of the timed sweep (the default workload is Wilson; the others are for profiling)")
     args = ap.parse_args()
@@ -321,7 +326,10 @@ def main():
     D = dg.Dirac(op, w["L"], w["Nv"], w["mass"], w["prec"])
     D.set_links(torch.from_numpy(V).cuda())
     if args.kernel:
-        D.set_kernel_config(*(int(v) for v in args.kernel.split(",")))
+        k = [int(v) for v in args.kernel.split(",")]
+        D.set_kernel_config(*k[:3])
+        if len(k) > 3:
+            D.set_site_order(k[3])
     else:
         D.autotune()                   # best of the built launch shapes on this GPU
     xin = torch.from_numpy(psi).cuda()
@@ -379,6 +387,7 @@ def main():
         if tf.get("kernel_hash") == kernel_hash() and tf.get("workload") == workload:
             traffic = tf.get("dram_bytes_per_launch")
     cfg = D.kernel_config()
+    site_order = D.site_order()
     line = {
         "metric": METRIC, "value": value, "unit": "Gflop/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -387,13 +396,14 @@ def main():
                    "Nc": 3, "Nv": w["Nv"], "kappa": w["mass"], "links": "exp(0.3 i H), H traceless Gaussian",
                    "source": "complex Gaussian N(0,1)", "layout": "internal site-fastest SoA",
                    "l2": "no flush: each step streams {:.2f} GB > 129 MB L2".format(bytes_step / 1e9),
-                   "kernel": {"rhs_per_thread": cfg[0], "block": cfg[1], "variant": cfg[2]},
+                   "kernel": {"rhs_per_thread": cfg[0], "block": cfg[1], "variant": cfg[2],
+                              "site_order_tchunk": site_order},
                    "parallelism": f"replicas x{ws}"},
         "hbm_gbs": achieved,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
                      "peak_kind": f"{peak_kind} copy bandwidth",
-                     "kernel": "k_{}{}<{},R={}>".format(op, {0: "", 1: "_groups", 2: "_march", 3: "_pipe", 4: "_tma"}[cfg[2]],
+                     "kernel": "k_{}{}<{},R={}>".format(op, {0: "", 1: "_groups", 2: "_march", 3: "_pipe", 4: "_tma", 5: "_xrow"}[cfg[2]],
                                                       w["prec"], cfg[0]),
                      "algorithmic_bytes_per_launch": bytes_step},
         "clocks": clk.summary(),

@@ -251,14 +251,16 @@ DIRAC_API dirac_status dirac_apply_static(dirac_handle* h, void* out, const void
  *   R        right-hand sides per thread (1..4 for Wilson and Brillouin; 1, 2, 4
  *            or 6 for staggered); each link is loaded once per thread and
  *            applied to its R right-hand sides from registers
- *   block    threads per block (variants 0 and 3; a multiple of 32, 32..256) or
- *            sites per block (variant 1; 32 or 64)
+ *   block    threads per block (variants 0 and 3; a multiple of 32, 32..256;
+ *            variant 5: 32..192) or sites per block (variants 1 and 2: 32 or
+ *            64, variant 2 also 128)
  *   variant  0: the right-hand-side groups of a site run in consecutive blocks;
  *            1: the groups of the same sites share one block, so that each link
  *               comes from L2 once per block and is reused through L1;
- *            2: (Wilson) variant 1, and each block walks 8 consecutive
- *               t-slices of its sites so that the t-neighbours and backward
- *               t-links come from L1 (the y and z loads bypass L1);
+ *            2: (Wilson, R <= 2) variant 1 over site columns: each thread walks up
+ *               to 8 consecutive t-slices of its (x, y, z) site, reading each
+ *               spinor and t-link along t once (the t hops are carried from
+ *               one slice to the next in registers);
  *            4: (Wilson, FP32/BF16/FP16, R = 1 or 2) tiles of `block` sites made
  *               of complete x-rows, each tile's neighbour rows and tiles
  *               streamed into shared memory by bulk copies (one producer warp,
@@ -267,14 +269,35 @@ DIRAC_API dirac_status dirac_apply_static(dirac_handle* h, void* out, const void
  *               with Ly divisible by block / Lx and Lx divisible by 4;
  *            3: (Wilson) variant 0 with a three-stage cp.async pipeline that
  *               keeps the next two hops in flight in shared memory; needs
- *               3 * block * (R * spinor bytes + link bytes) <= 227 KB.
+ *               3 * block * (R * spinor bytes + link bytes) <= 227 KB;
+ *            5: (Wilson, FP32/BF16/FP16, R <= 2) variant 2 with a warp on 32
+ *               consecutive sites of the (x, y, z) volume: the x hops are
+ *               exchanged between lanes by warp shuffles instead of loaded;
+ *               needs Lx to divide 32 and Lx * Ly * Lz divisible by 32;
+ *               block / 32 right-hand-side groups share a block.
  * UNSUPPORTED for other values. */
 DIRAC_API dirac_status dirac_set_kernel_config(dirac_handle* h, int R, int block, int variant);
+
 DIRAC_API dirac_status dirac_get_kernel_config(const dirac_handle* h, int* R, int* block, int* variant);
+
+/* Site order of the sweeps of variants 0 and 1 (no counterpart in the paper,
+ * whose KNL code walks the lattice in its storage order): the order in which
+ * consecutive thread blocks take the sites.
+ *   tchunk = 0    lexicographic (x fastest, then y, z, t);
+ *   0 < tchunk <= Nt   the (z, t) planes of Nx*Ny sites are taken in chunks
+ *                 of tchunk t-slices, t faster than z inside a chunk, so that
+ *                 the t-neighbours of a site are swept a few planes after it
+ *                 and are still in L2 (with 12 FP32 right-hand sides a 32^3
+ *                 t-slice and its output are larger than half the L2).
+ * Results do not depend on it.  Kept across dirac_set_kernel_config; chosen
+ * by dirac_autotune.  INVALID_ARG outside 0..Nt. */
+DIRAC_API dirac_status dirac_set_site_order(dirac_handle* h, int tchunk);
+DIRAC_API dirac_status dirac_get_site_order(const dirac_handle* h, int* tchunk);
 
 /* Autotuner (the paper's "best of breed" selection, Sec. 4 and Sec. 6: time
  * every built variant on this machine and keep the winner): times each
- * supported (R, block, variant) of dirac_set_kernel_config on the handle's own
+ * supported (R, block, variant) of dirac_set_kernel_config, variants 0 and 1
+ * with both site orders 0 and min(8, Nt), on the handle's own
  * workspace and keeps the fastest in the handle.  With the environment
  * variable DIRAC_TUNE_CACHE naming a writable file, results are cached per
  * (operator, precision, lattice, Nv, GPU name) and reused unless force != 0.

@@ -66,6 +66,8 @@ SIGNATURES = {
     "dirac_apply_dagger": (I, [P, P, P, I]),
     "dirac_set_kernel_config": (I, [P, I, I, I]),
     "dirac_get_kernel_config": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
+    "dirac_set_site_order": (I, [P, I]),
+    "dirac_get_site_order": (I, [P, ctypes.POINTER(I)]),
     "dirac_last_error": (ctypes.c_char_p, [P]),
     "dirac_solve": (I, [P, P, P, D, I, I, D, P, P]),
     "dirac_force": (I, [P, P, P, P, I]),
@@ -301,8 +303,18 @@ class Dirac:
 
     def set_kernel_config(self, R: int, block: int, variant: int = 0):
         """Launch shape: R right-hand sides per thread, block, variant (0 direct,
-        1 groups in block, 3 pipelined Wilson); see dirac_set_kernel_config."""
+        1 groups in block, 2 Wilson t-march, 3 pipelined Wilson, 4 bulk-copy
+        Wilson, 5 Wilson x-rows per warp); see dirac_set_kernel_config."""
         check(lib().dirac_set_kernel_config(self.h, R, block, variant), self.h, "dirac_set_kernel_config")
+
+    def set_site_order(self, tchunk: int):
+        """Site order of variants 0 and 1 (0 lexicographic, else t-chunks); see dirac_set_site_order."""
+        check(lib().dirac_set_site_order(self.h, tchunk), self.h, "dirac_set_site_order")
+
+    def site_order(self) -> int:
+        t = I()
+        check(lib().dirac_get_site_order(self.h, ctypes.byref(t)), self.h, "dirac_get_site_order")
+        return t.value
 
     def autotune(self, force: bool = False):
         """Pick the fastest (R, block, variant) for this handle; returns (R, block, variant, ms per sweep)."""
@@ -324,12 +336,12 @@ class Dirac:
         return R.value, B.value, Pp.value
 
 
-VARIANTS = {"staggered": (0, 1), "wilson": (0, 1, 2, 3, 4), "brillouin": (0, 1)}
+VARIANTS = {"staggered": (0, 1), "wilson": (0, 1, 2, 3, 4, 5), "brillouin": (0, 1)}
 
 
 def config_supported(op: str, prec: str, R: int, block: int, variant: int, L=None) -> bool:
     """The rule dirac_set_kernel_config applies (without a handle); L = (Nx, Ny, Nz, Nt)
-    is needed for variant 4."""
+    is needed for variants 4 and 5."""
     if block < 32 or block > 256 or block % 32:
         return False
     if variant == 4:
@@ -340,6 +352,10 @@ def config_supported(op: str, prec: str, R: int, block: int, variant: int, L=Non
             return False
         k, lb, nst = (6, 8, 3) if prec == "f32" else (3, 4, 4)
         return 256 + 128 + nst * (2 * R * k * block * 16 + 9 * block * lb) <= 227 * 1024
+    if variant == 5:
+        if op != "wilson" or prec == "f64" or not 1 <= R <= 2 or block > 192 or L is None:
+            return False
+        return 32 % L[0] == 0 and (L[0] * L[1] * L[2]) % 32 == 0
     if op == "staggered" and R not in (1, 2, 4, 6):
         return False
     if op != "staggered" and not 1 <= R <= 4:
@@ -351,7 +367,7 @@ def config_supported(op: str, prec: str, R: int, block: int, variant: int, L=Non
     if variant == 1:
         return block <= 64
     if variant == 2:
-        return op == "wilson" and block <= 64
+        return op == "wilson" and R <= 2 and block <= 128
     if variant == 3 and op == "wilson":
         k = {"f64": 12, "f32": 6, "bf16": 3, "f16": 3}[prec]
         lb = {"f64": 16, "f32": 8, "bf16": 4, "f16": 4}[prec]

@@ -18,9 +18,9 @@ __global__ void __launch_bounds__(256) k_brillouin(ApplyArgs a, int ngroups)
 {
     const long b = blockIdx.x;
     const int group = (int)(b % ngroups);
-    const long s = (b / ngroups) * blockDim.x + threadIdx.x;
-    if (s >= a.g.vol) return;
-    brillouin_site<T, R, DAG>(a, s, group, c_bri_dirs);
+    const long p = (b / ngroups) * blockDim.x + threadIdx.x;
+    if (p >= a.g.vol) return;
+    brillouin_site<T, R, DAG>(a, site_of(a.g, p, a.tc), group, c_bri_dirs);
 }
 
 // V_GROUPS: blockDim = (sites, groups); block b covers a run of sites and a
@@ -31,9 +31,9 @@ __global__ void __launch_bounds__(192, 2) k_brillouin_groups(ApplyArgs a, int ng
     const int nchunks = (ngroups + gy - 1) / gy;
     const long b = blockIdx.x;
     const int group = (int)(b % nchunks) * gy + threadIdx.y;
-    const long s = (b / nchunks) * blockDim.x + threadIdx.x;
-    if (s >= a.g.vol || group >= ngroups) return;
-    brillouin_site<T, R, DAG>(a, s, group, c_bri_dirs);
+    const long p = (b / nchunks) * blockDim.x + threadIdx.x;
+    if (p >= a.g.vol || group >= ngroups) return;
+    brillouin_site<T, R, DAG>(a, site_of(a.g, p, a.tc), group, c_bri_dirs);
 }
 
 template <typename T, int R>

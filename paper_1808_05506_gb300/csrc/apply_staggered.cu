@@ -13,9 +13,9 @@ __global__ void __launch_bounds__(256) k_staggered(ApplyArgs a, int ngroups)
 {
     const long b = blockIdx.x;
     const int group = (int)(b % ngroups);
-    const long s = (b / ngroups) * blockDim.x + threadIdx.x;
-    if (s >= a.g.vol) return;
-    staggered_site<T, R, DAG>(a, s, group);
+    const long p = (b / ngroups) * blockDim.x + threadIdx.x;
+    if (p >= a.g.vol) return;
+    staggered_site<T, R, DAG>(a, site_of(a.g, p, a.tc), group);
 }
 
 // V_GROUPS: blockDim = (sites, groups); block b covers a run of sites and a
@@ -26,9 +26,9 @@ __global__ void __launch_bounds__(192, 2) k_staggered_groups(ApplyArgs a, int ng
     const int nchunks = (ngroups + gy - 1) / gy;
     const long b = blockIdx.x;
     const int group = (int)(b % nchunks) * gy + threadIdx.y;
-    const long s = (b / nchunks) * blockDim.x + threadIdx.x;
-    if (s >= a.g.vol || group >= ngroups) return;
-    staggered_site<T, R, DAG>(a, s, group);
+    const long p = (b / nchunks) * blockDim.x + threadIdx.x;
+    if (p >= a.g.vol || group >= ngroups) return;
+    staggered_site<T, R, DAG>(a, site_of(a.g, p, a.tc), group);
 }
 
 template <typename T, int R>

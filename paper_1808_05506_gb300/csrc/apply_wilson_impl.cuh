@@ -13,9 +13,9 @@ __global__ void __launch_bounds__(256) k_wilson(ApplyArgs a, int ngroups)
 {
     const long b = blockIdx.x;
     const int group = (int)(b % ngroups);
-    const long s = (b / ngroups) * blockDim.x + threadIdx.x;
-    if (s >= a.g.vol) return;
-    wilson_site<T, R, DAG>(a, s, group);
+    const long p = (b / ngroups) * blockDim.x + threadIdx.x;
+    if (p >= a.g.vol) return;
+    wilson_site<T, R, DAG>(a, site_of(a.g, p, a.tc), group);
 }
 
 // V_TMARCH: blockDim = (sites, groups); a block owns a run of `block` site
@@ -34,6 +34,23 @@ __global__ void __launch_bounds__(192, 2) k_wilson_march(ApplyArgs a, int ngroup
     const int t0 = (int)(b / nruns) * tc;
     if (s3 >= vol3 || group >= ngroups) return;
     wilson_column<T, R, DAG>(a, s3, group, t0, min(t0 + tc, a.g.L[3]));
+}
+
+// V_XROW: blockDim = (32, gy); warp y of block b takes right-hand-side group
+// (b % nchunks) * gy + y on the 32-site run (b / nchunks) % nruns of the
+// (x, y, z) volume and the t-chunk (b / nchunks) / nruns (wilson_xrow)
+template <typename T, int R, bool DAG>
+__global__ void __launch_bounds__(192, 2) k_wilson_xrow(ApplyArgs a, int ngroups, int gy, int tc)
+{
+    const int nchunks = (ngroups + gy - 1) / gy;
+    const long nruns = a.g.stride[3] / 32;
+    long b = blockIdx.x;
+    const int group = (int)(b % nchunks) * gy + threadIdx.y;
+    b /= nchunks;
+    const long s3 = (b % nruns) * 32 + threadIdx.x;
+    const int t0 = (int)(b / nruns) * tc;
+    if (group >= ngroups) return;   // a whole warp
+    wilson_xrow<T, R, DAG>(a, s3, threadIdx.x, group, t0, min(t0 + tc, a.g.L[3]));
 }
 
 // V_TMA: persistent CTAs; one producer warp streams the stages of each tile
@@ -187,9 +204,9 @@ __global__ void __launch_bounds__(192, 2) k_wilson_groups(ApplyArgs a, int ngrou
     const int nchunks = (ngroups + gy - 1) / gy;
     const long b = blockIdx.x;
     const int group = (int)(b % nchunks) * gy + threadIdx.y;
-    const long s = (b / nchunks) * blockDim.x + threadIdx.x;
-    if (s >= a.g.vol || group >= ngroups) return;
-    wilson_site<T, R, DAG>(a, s, group);
+    const long p = (b / nchunks) * blockDim.x + threadIdx.x;
+    if (p >= a.g.vol || group >= ngroups) return;
+    wilson_site<T, R, DAG>(a, site_of(a.g, p, a.tc), group);
 }
 
 template <typename T, int R>
@@ -206,6 +223,16 @@ cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
         else k_wilson_groups<T, R, false><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
         return cudaGetLastError();
     }
+    if constexpr (R <= 2) {
+    if (c.variant == V_XROW) {
+        // the host checked 32 % Lx == 0 and vol3 % 32 == 0: every warp is full
+        const int gy = min(c.block / 32, ngroups);
+        const int tc = a.g.L[3] < 8 ? a.g.L[3] : 8;
+        const long nb = (a.g.stride[3] / 32) * (long)((ngroups + gy - 1) / gy) * (long)((a.g.L[3] + tc - 1) / tc);
+        if (dag) k_wilson_xrow<T, R, true><<<(unsigned)nb, dim3(32, gy), 0, st>>>(a, ngroups, gy, tc);
+        else k_wilson_xrow<T, R, false><<<(unsigned)nb, dim3(32, gy), 0, st>>>(a, ngroups, gy, tc);
+        return cudaGetLastError();
+    }
     if (c.variant == V_TMARCH) {
         const int gy = groups_per_block(block, ngroups);
         const long vol3 = a.g.stride[3];
@@ -216,6 +243,7 @@ cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
         else k_wilson_march<T, R, false><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy, tc);
         return cudaGetLastError();
     }
+    }   // R <= 2: the carried variants spill beyond two right-hand sides per thread
     if (c.variant == V_PIPE3) {
         const size_t smem = WilsonPipe<T, R>::stage_bytes_per_thread * 3 * block;
         auto kern = dag ? k_wilson_pipe<T, R, true, 3> : k_wilson_pipe<T, R, false, 3>;

@@ -114,6 +114,7 @@ ApplyArgs dirac_handle::args(void* out, const void* in, int nv, double diag_valu
     a.diag = diag_value;
     a.diag_v = nullptr;
     a.err = dev_err;
+    a.tc = 0;
     return a;
 }
 
@@ -125,6 +126,7 @@ dirac_status dirac_handle::run_apply(bool dagger, void* out, const void* in, int
     a.links = link_ptr;
     a.diag_v = diag_v;
     a.err = dev_err;
+    a.tc = (c.variant == V_DIRECT || c.variant == V_GROUPS) ? c.order : 0;
     return cuda(launch_apply(op, p, dagger, a, c, stream), "apply kernel launch");
 }
 
@@ -408,7 +410,24 @@ dirac_status dirac_set_kernel_config(dirac_handle* h, int R, int block, int vari
     if (!apply_config_supported(h->op, h->prec, R, block, variant, h->g))
         return h->fail(DIRAC_ERR_UNSUPPORTED, "dirac_set_kernel_config: R = %d, block = %d, variant = %d not built",
                        R, block, variant);
-    h->cfg = LaunchCfg{R, block, variant};
+    h->cfg = LaunchCfg{R, block, variant, h->cfg.order};
+    return DIRAC_OK;
+}
+
+dirac_status dirac_set_site_order(dirac_handle* h, int tchunk)
+{
+    if (!h) return DIRAC_ERR_INVALID_ARG;
+    if (tchunk < 0 || tchunk > h->g.L[3])
+        return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_set_site_order: tchunk = %d not in 0..Nt = %d", tchunk,
+                       h->g.L[3]);
+    h->cfg.order = tchunk;
+    return DIRAC_OK;
+}
+
+dirac_status dirac_get_site_order(const dirac_handle* h, int* tchunk)
+{
+    if (!h || !tchunk) return DIRAC_ERR_INVALID_ARG;
+    *tchunk = h->cfg.order;
     return DIRAC_OK;
 }
 
@@ -452,12 +471,15 @@ bool apply_config_supported(int op, int prec, int R, int block, int variant, con
         return op == OP_WILSON && prec != P_F64 && (R == 1 || R == 2) && wilson_tma_geometry(g, block, &ny) &&
                wilson_tma_smem(prec, R, block) <= 227 * 1024;
     }
+    if (variant == V_XROW)
+        return op == OP_WILSON && prec != P_F64 && R >= 1 && R <= 2 && block <= 192 && 32 % g.L[0] == 0 &&
+               g.stride[3] % 32 == 0;
     const bool Rok = (op == OP_STAGGERED) ? (R == 1 || R == 2 || R == 4 || R == 6) : (R >= 1 && R <= 4);
     if (!Rok) return false;
     if (variant == V_DIRECT) return true;
     if (op == OP_WILSON && prec == P_F64) return false;   // FP64 Wilson: direct variant only
     if (variant == V_GROUPS) return block <= 64;
-    if (variant == V_TMARCH) return op == OP_WILSON && block <= 128;
+    if (variant == V_TMARCH) return op == OP_WILSON && R <= 2 && block <= 128;
     return op == OP_WILSON && variant == V_PIPE3 && wilson_pipe_smem(prec, R, block, 3) <= 227 * 1024;
 }
 

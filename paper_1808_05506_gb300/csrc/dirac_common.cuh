@@ -435,6 +435,17 @@ DEV_INLINE void mat_dag_vec_acc2(const cx<float>* U, const cx<float>* h, cx<floa
     }
 }
 
+// value of v held by lane src of this warp (all 32 lanes take part)
+template <typename A> DEV_INLINE cx<A> shfl_cx(cx<A> v, int src)
+{
+#if defined(__CUDA_ARCH__)
+    return {__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src)};
+#else
+    (void)src;
+    return v;   // host builds of the kernel bodies have no warps
+#endif
+}
+
 // w = U h  /  w = U^dagger h   (3-vectors)
 template <typename A> HD void mat_vec(const cx<A>* U, const cx<A>* h, cx<A>* w)
 {
@@ -515,6 +526,26 @@ struct Geom {
     long stride[4];  // 1, Nx, Nx Ny, Nx Ny Nz
     long vol;
 };
+
+// Processing order of the sites.  With tc = 0 the p-th site is site p
+// (lexicographic).  With tc > 0 the (z, t) planes of Lx Ly sites are visited
+// in chunks of tc t-slices, and inside a chunk t runs faster than z, so a
+// site's t-neighbours are swept a few planes after it rather than a whole
+// (x, y, z) volume later; the last chunk may be shorter.  A bijection on
+// 0 <= p < vol.
+HD long site_of(const Geom& g, long p, int tc)
+{
+    if (tc <= 0) return p;
+    const long P = g.stride[2];
+    const long q = p / P, w = p - q * P;
+    const long chunk = (long)g.L[2] * tc;
+    const int tb = (int)(q / chunk);
+    const long r = q - tb * chunk;
+    const int t0 = tb * tc;
+    const int n = (g.L[3] - t0 < tc) ? g.L[3] - t0 : tc;
+    const int z = (int)(r / n), ti = (int)(r - (long)z * n);
+    return w + P * (z + (long)g.L[2] * (t0 + ti));
+}
 
 // neighbour offsets of site s: fwd[mu] = (s + mu) - s, bwd[mu] = (s - mu) - s (periodic)
 HD void site_offsets(const Geom& g, long s, long* fwd, long* bwd, int* x)

@@ -28,14 +28,19 @@ enum Variant {
     V_TMARCH = 2,   // Wilson: V_GROUPS over (x, y, z) site columns, each thread walking up to
                     // 8 consecutive t-slices with the t hops carried in registers
     V_PIPE3 = 3,    // Wilson: V_DIRECT with a 3-stage cp.async pipeline in shared memory
-    V_TMA = 4       // Wilson (FP32/BF16/FP16): tiles of complete x-rows streamed by bulk copies
+    V_TMA = 4,      // Wilson (FP32/BF16/FP16): tiles of complete x-rows streamed by bulk copies
                     // (one producer warp, mbarrier ring); `block` = sites per tile
+    V_XROW = 5      // Wilson (FP32/BF16/FP16), Lx dividing 32: a warp holds 32 consecutive sites
+                    // of the (x, y, z) volume (whole x-rows) and walks up to 8 t-slices; x hops
+                    // by warp shuffles, t hops carried in registers; `block` = threads
+                    // (block / 32 right-hand-side groups per block)
 };
 
 struct LaunchCfg {
     int R;         // right-hand sides per thread
     int block;     // V_DIRECT, V_PIPE3: threads per block; V_GROUPS: sites per block
     int variant;   // Variant
+    int order = 0; // V_DIRECT, V_GROUPS: site order of the grid (site_of t-chunk, 0 lexicographic)
 };
 
 // threads per block of V_GROUPS: block sites x gy groups with block * gy <= 192

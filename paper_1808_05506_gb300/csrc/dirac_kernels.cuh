@@ -36,6 +36,7 @@ struct ApplyArgs {
     double diag;          // (4 + m0) Wilson, m staggered, (m0 + 15/8) Brillouin
     const double* diag_v; // per-right-hand-side diagonal (device, Nv entries) or null: diag for all
     int* err;             // device error word (kernels with bounded waits record DIRAC_TIMEOUT) or null
+    int tc;               // site order of the grid (site_of): 0 lexicographic, else t-chunk
 };
 
 template <typename A> DEV_INLINE A diag_of(const ApplyArgs& a, int v)
@@ -213,6 +214,109 @@ DEV_INLINE void wilson_column(const ApplyArgs& a, long s3, int group, int t0, in
             wilson_reconstruct<3, SF>(w, acc[r]);
             wilson_reconstruct<3, SB>(hb[r], acc[r]);
             // backward t hop of slice t + 1
+            wilson_project<3, SB>(pc[r], h);
+            mat_dag_vec(U, h, hb[r]);
+            mat_dag_vec(U, h + 3, hb[r] + 3);
+            const A dg = diag_of<A>(a, v);
+#pragma unroll
+            for (int i = 0; i < 12; ++i) {
+                cx<A> o;
+                o.re = fma(mh, acc[r][i].re, dg * pc[r][i].re);
+                o.im = fma(mh, acc[r][i].im, dg * pc[r][i].im);
+                acc[r][i] = o;
+                pc[r][i] = pn[i];
+            }
+            if (v0 + r < a.Nv) store_spinor<T, 12>(a.out, a.g.vol, v0 + r, s, acc[r]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- Wilson, x-rows in a warp
+// wilson_column with the 32 lanes of a warp on 32 consecutive sites of the
+// (x, y, z) volume, i.e. on whole x-rows (Lx divides 32).  The x hops need no
+// memory access: lane x sends (1 + SF gamma_1) psi(x), the forward hop's
+// projection, to lane x - 1, and U_x(x)^+ (1 + SB gamma_1) psi(x), the
+// backward hop of site x + 1 built with its own link, to lane x + 1.  The t
+// hops are carried as in wilson_column; only the y and z hops load spinors.
+// Requires whole warps: every lane of the warp calls this with the same
+// group and t range.
+template <typename T, int R, bool DAG>
+DEV_INLINE void wilson_xrow(const ApplyArgs& a, long s3, int lane, int group, int t0, int t1)
+{
+    using A = typename Store<T>::A;
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int SB = -SF;
+    const long vol3 = a.g.stride[3];
+    const int Lt = a.g.L[3], Lx = a.g.L[0];
+    const int v0 = group * R;
+    long fwd[4], bwd[4];
+    int x[4];
+    site_offsets(a.g, s3, fwd, bwd, x);
+    const int lane_f = lane - x[0] + (x[0] + 1 == Lx ? 0 : x[0] + 1);   // site x + 1
+    const int lane_b = lane - x[0] + (x[0] == 0 ? Lx - 1 : x[0] - 1);   // site x - 1
+    cx<A> pc[R][12];   // psi(t)
+    cx<A> hb[R][6];    // U_t(t - 1)^+ (1 + SB gamma_4) psi(t - 1)
+    {
+        const long sp = s3 + vol3 * (t0 == 0 ? Lt - 1 : t0 - 1);
+        cx<A> U[9];
+        load_link<T>(a.links, a.g.vol, 3, sp, U);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int v = min(v0 + r, a.Nv - 1);
+            cx<A> p[12], h[6];
+            load_spinor<T, 12>(a.in, a.g.vol, v, sp, p);
+            wilson_project<3, SB>(p, h);
+            mat_dag_vec(U, h, hb[r]);
+            mat_dag_vec(U, h + 3, hb[r] + 3);
+            load_spinor<T, 12>(a.in, a.g.vol, v, s3 + vol3 * t0, pc[r]);
+        }
+    }
+    const A mh = (A)(-0.5);
+#pragma unroll 1
+    for (int t = t0; t < t1; ++t) {
+        const long s = s3 + vol3 * t;
+        const long sn = s3 + vol3 * (t + 1 == Lt ? 0 : t + 1);
+        cx<A> acc[R][12];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int i = 0; i < 12; ++i) acc[r][i] = cx<A>{A(0), A(0)};
+        {
+            cx<A> U[9];
+            load_link<T>(a.links, a.g.vol, 0, s, U);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                cx<A> h[6], w[6], q[6];
+                wilson_project<0, SF>(pc[r], h);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) q[i] = shfl_cx(h[i], lane_f);
+                mat_vec(U, q, w);
+                mat_vec(U, q + 3, w + 3);
+                wilson_reconstruct<0, SF>(w, acc[r]);
+                wilson_project<0, SB>(pc[r], h);
+                mat_dag_vec(U, h, w);
+                mat_dag_vec(U, h + 3, w + 3);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) q[i] = shfl_cx(w[i], lane_b);
+                wilson_reconstruct<0, SB>(q, acc[r]);
+            }
+        }
+        wilson_hop<T, R, 1, SF, false>(a, s + fwd[1], s, v0, acc);
+        wilson_hop<T, R, 1, SB, true>(a, s + bwd[1], s + bwd[1], v0, acc);
+        wilson_hop<T, R, 2, SF, false>(a, s + fwd[2], s, v0, acc);
+        wilson_hop<T, R, 2, SB, true>(a, s + bwd[2], s + bwd[2], v0, acc);
+        cx<A> U[9];
+        load_link<T>(a.links, a.g.vol, 3, s, U);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int v = min(v0 + r, a.Nv - 1);
+            cx<A> pn[12], h[6], w[6];
+            load_spinor<T, 12>(a.in, a.g.vol, v, sn, pn);
+            wilson_project<3, SF>(pn, h);
+            mat_vec(U, h, w);
+            mat_vec(U, h + 3, w + 3);
+            wilson_reconstruct<3, SF>(w, acc[r]);
+            wilson_reconstruct<3, SB>(hb[r], acc[r]);
             wilson_project<3, SB>(pc[r], h);
             mat_dag_vec(U, h, hb[r]);
             mat_dag_vec(U, h + 3, hb[r] + 3);
@@ -523,16 +627,16 @@ DEV_INLINE void bri_spin(const BriDirA<A>& m, const cx<A>* p, cx<A>* chi)
             t = cx<A>{m.a * d0.re, m.a * d0.im}; t = cfma2_conj(m.q00, u0, t); chi[6 + c] = cfma2_conj(m.q10, u1, t);
             t = cx<A>{m.a * d1.re, m.a * d1.im}; t = cfma2_conj(m.q01, u0, t); chi[9 + c] = cfma2_conj(m.q11, u1, t);
         }
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        cx<A> u0 = p[c], u1 = p[3 + c], d0 = p[6 + c], d1 = p[9 + c];
-        cx<A> t;
-        t = scale(m.a, u0); t = cfma(m.q00, d0, t); t = cfma(m.q01, d1, t); chi[c] = t;
-        t = scale(m.a, u1); t = cfma(m.q10, d0, t); t = cfma(m.q11, d1, t); chi[3 + c] = t;
-        t = scale(m.a, d0); t = cfma_conj(m.q00, u0, t); t = cfma_conj(m.q10, u1, t); chi[6 + c] = t;
-        t = scale(m.a, d1); t = cfma_conj(m.q01, u0, t); t = cfma_conj(m.q11, u1, t); chi[9 + c] = t;
+        for (int c = 0; c < 3; ++c) {
+            cx<A> u0 = p[c], u1 = p[3 + c], d0 = p[6 + c], d1 = p[9 + c];
+            cx<A> t;
+            t = scale(m.a, u0); t = cfma(m.q00, d0, t); t = cfma(m.q01, d1, t); chi[c] = t;
+            t = scale(m.a, u1); t = cfma(m.q10, d0, t); t = cfma(m.q11, d1, t); chi[3 + c] = t;
+            t = scale(m.a, d0); t = cfma_conj(m.q00, u0, t); t = cfma_conj(m.q10, u1, t); chi[6 + c] = t;
+            t = scale(m.a, d1); t = cfma_conj(m.q01, u0, t); t = cfma_conj(m.q11, u1, t); chi[9 + c] = t;
+        }
     }
 }
 

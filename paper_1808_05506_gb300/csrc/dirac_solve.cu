@@ -207,7 +207,7 @@ static dirac_status enqueue_iteration(dirac_handle* h, SolverWS* w, const double
 static dirac_status ensure_graph(dirac_handle* h, SolverWS* w, const double* diag_v)
 {
     if (w->gexec && w->g_cfg.R == h->cfg.R && w->g_cfg.block == h->cfg.block && w->g_cfg.variant == h->cfg.variant &&
-        w->g_links == h->links && w->g_diag == diag_v)
+        w->g_cfg.order == h->cfg.order && w->g_links == h->links && w->g_diag == diag_v)
         return DIRAC_OK;
     if (w->gexec) {
         cudaGraphExecDestroy(w->gexec);

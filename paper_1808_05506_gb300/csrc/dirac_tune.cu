@@ -1,7 +1,7 @@
 // Autotuner: the "best of breed" selection of Sec. 4 and Sec. 6 (build every
 // variant, time a few calls, keep the winner for this machine) applied to
-// the launch shape of the sweeps: right-hand sides per thread R and threads
-// per block.  Results can be kept in a plain-text cache file named by the
+// the launch shape of the sweeps: right-hand sides per thread R, threads
+// per block, launch variant and (variants 0 and 1) the site order.  Results can be kept in a plain-text cache file named by the
 // environment variable DIRAC_TUNE_CACHE, one line per
 // (operator, precision, lattice, Nv, device name).
 #include <algorithm>
@@ -31,7 +31,7 @@ static std::string tune_key(const dirac_handle* h)
     return buf;
 }
 
-static bool cache_lookup(const std::string& key, int* R, int* B, int* Pp, double* ms)
+static bool cache_lookup(const std::string& key, int* R, int* B, int* Pp, int* T, double* ms)
 {
     const char* path = getenv("DIRAC_TUNE_CACHE");
     if (!path || !*path) return false;
@@ -43,13 +43,14 @@ static bool cache_lookup(const std::string& key, int* R, int* B, int* Pp, double
     while (fgets(line, sizeof(line), f)) {
         const size_t kl = key.size();
         if (strncmp(line, key.c_str(), kl) == 0 && line[kl] == ' ') {
-            int r, b;
+            int r, b, tc;
             double t;
             int pp;
-            if (sscanf(line + kl, " R%d B%d P%d %lf", &r, &b, &pp, &t) == 4) {
+            if (sscanf(line + kl, " R%d B%d P%d T%d %lf", &r, &b, &pp, &tc, &t) == 5) {
                 *R = r;
                 *B = b;
                 *Pp = pp;
+                *T = tc;
                 *ms = t;
                 found = true;   // the last entry wins
             }
@@ -59,14 +60,14 @@ static bool cache_lookup(const std::string& key, int* R, int* B, int* Pp, double
     return found;
 }
 
-static void cache_store(const std::string& key, int R, int B, int Pp, double ms)
+static void cache_store(const std::string& key, int R, int B, int Pp, int T, double ms)
 {
     const char* path = getenv("DIRAC_TUNE_CACHE");
     if (!path || !*path) return;
     std::lock_guard<std::mutex> lk(g_cache_mu);
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s R%d B%d P%d %.6f\n", key.c_str(), R, B, Pp, ms);
+    fprintf(f, "%s R%d B%d P%d T%d %.6f\n", key.c_str(), R, B, Pp, T, ms);
     fclose(f);
 }
 
@@ -76,10 +77,11 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
     if (!h) return DIRAC_ERR_INVALID_ARG;
     if (!h->have_links) return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_autotune: call dirac_set_links first");
     const std::string key = tune_key(h);
-    int R = 0, B = 0, Pp = 0;
+    int R = 0, B = 0, Pp = 0, Tc = 0;
     double best = 0.0;
-    if (!force && cache_lookup(key, &R, &B, &Pp, &best) && apply_config_supported(h->op, h->prec, R, B, Pp, h->g)) {
-        h->cfg = LaunchCfg{R, B, Pp};
+    if (!force && cache_lookup(key, &R, &B, &Pp, &Tc, &best) &&
+        apply_config_supported(h->op, h->prec, R, B, Pp, h->g) && Tc >= 0 && Tc <= h->g.L[3]) {
+        h->cfg = LaunchCfg{R, B, Pp, Tc};
     } else {
         dirac_status st;
         if ((st = h->ensure_workspace())) return st;
@@ -95,13 +97,17 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
         }
         best = 1e30;
         LaunchCfg win = h->cfg;
-        const int variants[] = {V_DIRECT, V_GROUPS, V_TMARCH, V_PIPE3, V_TMA};
+        const int variants[] = {V_DIRECT, V_GROUPS, V_TMARCH, V_PIPE3, V_TMA, V_XROW};
         for (int r : Rs) {
             if (r > h->Nv && r != Rs.front()) continue;
             for (int b : blocks)
-            for (int pp : variants) {
+            for (int pp : variants)
+            for (int oi = 0; oi < 2; ++oi) {
                 if (!apply_config_supported(h->op, h->prec, r, b, pp, h->g)) continue;
-                LaunchCfg c{r, b, pp};
+                // site order: lexicographic, or t-chunks of 8 slices (variants 0 and 1)
+                const int tc = oi == 0 ? 0 : std::min(8, h->g.L[3]);
+                if (oi == 1 && pp != V_DIRECT && pp != V_GROUPS) continue;
+                LaunchCfg c{r, b, pp, tc};
                 std::vector<float> t;
                 cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream);
                 bool launched = true;
@@ -133,8 +139,8 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
                 const double med = t[t.size() / 2];
                 const char* tr = getenv("DIRAC_TRACE");
                 if (tr && *tr && *tr != '0')
-                    fprintf(stderr, "[dirac] autotune %s R=%d block=%d variant=%d: %.4f ms\n", key.c_str(), r, b,
-                            pp, med);
+                    fprintf(stderr, "[dirac] autotune %s R=%d block=%d variant=%d order=%d: %.4f ms\n", key.c_str(),
+                            r, b, pp, tc, med);
                 if (med < best) {
                     best = med;
                     win = c;
@@ -146,7 +152,7 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
         cudaEventDestroy(e1);
         if (st) return st;
         h->cfg = win;
-        cache_store(key, win.R, win.block, win.variant, best);
+        cache_store(key, win.R, win.block, win.variant, win.order, best);
     }
     if (R_out) *R_out = h->cfg.R;
     if (block_out) *block_out = h->cfg.block;

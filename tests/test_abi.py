@@ -147,13 +147,15 @@ def test_binding_calls_match_the_c_signatures(dg, monkeypatch):
     D.force(x, x, out=V.clone())
     D.set_kernel_config(2, 128, 3)
     D.kernel_config()
+    D.set_site_order(8)
+    D.site_order()
     D.autotune()
     D.solve(x.to(torch.complex128), x0=x.to(torch.complex128))
     D.solve_batched([x.to(torch.complex128)] * 2, [0.12, 0.121])
     D.close()
     for name in ("dirac_set_links", "dirac_apply", "dirac_apply_dagger", "dirac_force", "dirac_solve",
                  "dirac_set_kernel_config", "dirac_get_kernel_config", "dirac_autotune", "dirac_destroy",
-                 "dirac_solve_batched"):
+                 "dirac_solve_batched", "dirac_set_site_order", "dirac_get_site_order"):
         assert name in calls, name
 
 
@@ -166,3 +168,12 @@ def test_config_rule(dg):
     assert not dg.config_supported("staggered", "f32", 3, 32, 1)
     assert not dg.config_supported("brillouin", "f32", 2, 128, 1)
     assert not dg.config_supported("brillouin", "f32", 2, 128, 3)
+    # x-rows per warp: Lx divides 32 and whole warps over the (x, y, z) volume
+    assert dg.config_supported("wilson", "f32", 1, 192, 5, (32, 32, 32, 32))
+    assert dg.config_supported("wilson", "bf16", 2, 32, 5, (8, 4, 2, 3))
+    assert not dg.config_supported("wilson", "f32", 1, 64, 5, (24, 24, 24, 48))
+    assert not dg.config_supported("wilson", "f32", 1, 64, 5, (4, 6, 2, 4))
+    assert not dg.config_supported("wilson", "f32", 3, 64, 5, (32, 32, 32, 32))
+    assert not dg.config_supported("wilson", "f64", 1, 64, 5, (32, 32, 32, 32))
+    assert not dg.config_supported("wilson", "f32", 1, 256, 5, (32, 32, 32, 32))
+    assert not dg.config_supported("staggered", "f32", 1, 64, 5, (32, 32, 32, 32))

@@ -131,6 +131,24 @@ def test_wilson_tma_tiles(dg, prec):
             assert rel_l2(got, want) <= TOL[prec], (L, Nv, R, S, dagger)
 
 
+@pytest.mark.parametrize("prec", ["f32", "bf16", "f16"])
+def test_wilson_xrow_shapes(dg, prec):
+    """The warp-per-x-rows variant (x hops by lane exchange, t hops carried):
+    rows of 32, 16, 8 and 4 sites (one to eight rows per warp), t-extents
+    that leave a partial t-chunk, and Nv that leaves a partial group."""
+    for L, Nv in (((32, 2, 2, 3), 3), ((16, 2, 3, 5), 5), ((8, 4, 2, 10), 4), ((4, 4, 2, 3), 2)):
+        V, psi = inputs("wilson", L, Nv, "f32", 270)
+        Vr, pr = rounded_for_oracle(V, psi, prec)
+        for dagger in (False, True):
+            want = oracle.apply("wilson", Vr, pr, oracle.kappa_to_m0(0.121), dagger=dagger)
+            for R in (1, 2):
+                for block in (32, 96, 192):
+                    assert dg.config_supported("wilson", prec, R, block, 5, L)
+                    got = run(dg, "wilson", L, Nv, 0.121, prec, V, psi, dagger=dagger, cfg=(R, block, 5),
+                              internal=True)
+                    assert rel_l2(got, want) <= TOL[prec], (L, Nv, R, block, dagger)
+
+
 def test_autotune(dg, tmp_path, monkeypatch):
     """The tuner keeps a supported configuration that reproduces the sweep and
     writes / reuses its cache file."""
@@ -141,7 +159,7 @@ def test_autotune(dg, tmp_path, monkeypatch):
     D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
     R, B, variant, ms = D.autotune(force=True)
     assert (R, B, variant) == D.kernel_config() and ms > 0
-    assert "R%d B%d P%d" % (R, B, variant) in (tmp_path / "tune.txt").read_text()
+    assert "R%d B%d P%d T%d" % (R, B, variant, D.site_order()) in (tmp_path / "tune.txt").read_text()
     x = torch.from_numpy(psi.astype(np.complex64)).cuda()
     got = D.apply(x).cpu().numpy().astype(np.complex128)
     want = oracle.apply("wilson", V, psi, oracle.kappa_to_m0(0.12))
@@ -149,8 +167,35 @@ def test_autotune(dg, tmp_path, monkeypatch):
     D2 = dg.Dirac("wilson", L, Nv, 0.12, "f32")
     D2.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
     assert D2.autotune()[:3] == (R, B, variant)           # from the cache
+    assert D2.site_order() == D.site_order()
     D.close()
     D2.close()
+
+
+@pytest.mark.parametrize("op,mass", [("wilson", 0.125), ("staggered", 0.02), ("brillouin", 0.1)])
+def test_site_order_bit_identical(dg, op, mass):
+    """The site order only permutes independent per-site work: every order
+    gives the lexicographic result bit for bit (Nt = 5 leaves a partial
+    t-chunk for tchunk = 2 and 3)."""
+    L, Nv = (6, 4, 6, 5), 5
+    V, psi = inputs(op, L, Nv, "f32", 280)
+    D = dg.Dirac(op, L, Nv, mass, "f32")
+    D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
+    xi = D.pack(torch.from_numpy(psi.astype(np.complex64)).cuda())
+    for variant in (0, 1):
+        D.set_kernel_config(2, 64, variant)
+        D.set_site_order(0)
+        ref = D.apply(xi, out=D.new_internal(), dagger=True).clone()
+        for tc in (1, 2, 3, 5):
+            D.set_site_order(tc)
+            assert D.kernel_config() == (2, 64, variant) and D.site_order() == tc
+            got = D.apply(xi, out=D.new_internal(), dagger=True)
+            assert torch.equal(got, ref), (variant, tc)
+    with pytest.raises(dg.DiracError):
+        D.set_site_order(6)
+    with pytest.raises(dg.DiracError):
+        D.set_site_order(-1)
+    D.close()
 
 
 @pytest.mark.parametrize("op,mass", [("wilson", 0.13), ("staggered", 0.1), ("brillouin", 0.05)])
@@ -197,7 +242,7 @@ def test_wilson_full_size_sampled(dg):
     st = torch.from_numpy(sites).cuda()
     for R in (1, 2, 3, 4):
         for block in (32, 64, 128, 256):
-            for variant in (0, 1, 2, 3, 4):
+            for variant in dg.VARIANTS["wilson"]:
                 if not dg.config_supported("wilson", "f32", R, block, variant, L):
                     continue
                 D.set_kernel_config(R, block, variant)
