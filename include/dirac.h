@@ -141,6 +141,28 @@ DIRAC_API dirac_status dirac_unpack(dirac_handle* h, void* canonical_out, const 
  * Requires dirac_set_links first (else INVALID_ARG).  Asynchronous. */
 DIRAC_API dirac_status dirac_apply(dirac_handle* h, void* out, const void* in, dirac_layout layout);
 
+/* out = D in (dagger = 0) or D^+ in (dagger != 0) with out and in canonical
+ * fields in HOST memory (no counterpart in the paper, whose fields live in
+ * the memory of the node that sweeps them): the same result as copying in
+ * to the device, dirac_apply(..., DIRAC_CANONICAL) and copying out, with the
+ * copies overlapped with the work.  The lattice is cut into about 8 slabs of
+ * t-slices; the host-to-device copy of one slab, the pack / sweep / unpack
+ * of an earlier one and the device-to-host copy of a finished one run at
+ * the same time on two copy streams of the handle and the handle's stream.
+ *   out, in   host pointers (complex double for F64 handles, complex float
+ *             otherwise), Nx Ny Nz Nt * Nv * spin * 3 entries; page-locked
+ *             memory (cudaHostAlloc / cudaHostRegister) lets the copies
+ *             overlap, pageable memory works with copies that block the
+ *             calling thread; they must not overlap (INVALID_ARG), device
+ *             pointers are rejected (INVALID_ARG).
+ * Launch shape: the handle's kernel configuration when it is variant 0, 1, 2
+ * or 5 (the ones that can sweep a t-slab), else variant 1 with the same R.
+ * Holds two staging buffers per direction of one slab each (allocated on
+ * the first call, kept in the handle) and the handle's apply workspace.
+ * Requires dirac_set_links first.  Asynchronous: out is complete when the
+ * handle's stream has reached this point (dirac_sync). */
+DIRAC_API dirac_status dirac_apply_host(dirac_handle* h, void* out, const void* in, int dagger);
+
 /* out = D^+ in.  Staggered: D_S^+ = m - (hopping part of D_S) (the hopping
  * part is anti-hermitian, Sec. 3); Wilson, Brillouin: D^+ = gamma5 D gamma5.
  * Same contract as dirac_apply. */

@@ -67,6 +67,7 @@ SIGNATURES = {
     "dirac_set_kernel_config": (I, [P, I, I, I]),
     "dirac_get_kernel_config": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
     "dirac_set_site_order": (I, [P, I]),
+    "dirac_apply_host": (I, [P, P, P, I]),
     "dirac_get_site_order": (I, [P, ctypes.POINTER(I)]),
     "dirac_last_error": (ctypes.c_char_p, [P]),
     "dirac_solve": (I, [P, P, P, D, I, I, D, P, P]),
@@ -235,6 +236,24 @@ class Dirac:
         fn = lib().dirac_apply_dagger if dagger else lib().dirac_apply
         check(fn(self.h, _ptr(out), _ptr(x.contiguous() if layout == CANONICAL else x), layout),
               self.h, "dirac_apply_dagger" if dagger else "dirac_apply")
+        return out
+
+    def apply_host(self, x, out=None, dagger: bool = False, sync: bool = True):
+        """out = D x (or D^+ x) for canonical fields in host memory (CPU tensors; pinned
+        memory overlaps the copies with the sweep); see dirac_apply_host.  With sync the
+        call returns once out is written, else after enqueuing (then call sync())."""
+        torch = _torch()
+        if x.device.type != "cpu" or x.dtype != self.canon_dtype or tuple(x.shape) != self.canonical_shape:
+            raise ValueError(f"x must be a CPU {self.canon_dtype} tensor of shape {self.canonical_shape}")
+        x = x.contiguous()
+        if out is None:
+            out = torch.empty(self.canonical_shape, dtype=self.canon_dtype, pin_memory=x.is_pinned())
+        elif out.device.type != "cpu" or out.dtype != self.canon_dtype or not out.is_contiguous():
+            raise ValueError("out must be a contiguous CPU tensor of the canonical dtype")
+        self._sync_stream()
+        check(lib().dirac_apply_host(self.h, _ptr(out), _ptr(x), 1 if dagger else 0), self.h, "dirac_apply_host")
+        if sync:
+            self.sync()
         return out
 
     def apply_dagger(self, x, out=None, layout=None):

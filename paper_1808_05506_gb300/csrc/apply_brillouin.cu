@@ -19,8 +19,8 @@ __global__ void __launch_bounds__(256) k_brillouin(ApplyArgs a, int ngroups)
     const long b = blockIdx.x;
     const int group = (int)(b % ngroups);
     const long p = (b / ngroups) * blockDim.x + threadIdx.x;
-    if (p >= a.g.vol) return;
-    brillouin_site<T, R, DAG>(a, site_of(a.g, p, a.tc), group, c_bri_dirs);
+    if (p >= a.nsites) return;
+    brillouin_site<T, R, DAG>(a, slab_site(a, p), group, c_bri_dirs);
 }
 
 // V_GROUPS: blockDim = (sites, groups); block b covers a run of sites and a
@@ -32,8 +32,8 @@ __global__ void __launch_bounds__(192, 2) k_brillouin_groups(ApplyArgs a, int ng
     const long b = blockIdx.x;
     const int group = (int)(b % nchunks) * gy + threadIdx.y;
     const long p = (b / nchunks) * blockDim.x + threadIdx.x;
-    if (p >= a.g.vol || group >= ngroups) return;
-    brillouin_site<T, R, DAG>(a, site_of(a.g, p, a.tc), group, c_bri_dirs);
+    if (p >= a.nsites || group >= ngroups) return;
+    brillouin_site<T, R, DAG>(a, slab_site(a, p), group, c_bri_dirs);
 }
 
 template <typename T, int R>
@@ -43,12 +43,12 @@ static cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st
     const int ngroups = (a.Nv + R - 1) / R;
     if (c.variant == V_GROUPS) {
         const int gy = groups_per_block(block, ngroups);
-        const long nb = ((a.g.vol + block - 1) / block) * (long)((ngroups + gy - 1) / gy);
+        const long nb = ((a.nsites + block - 1) / block) * (long)((ngroups + gy - 1) / gy);
         if (dag) k_brillouin_groups<T, R, true><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
         else k_brillouin_groups<T, R, false><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
         return cudaGetLastError();
     }
-    const long nblk = ((a.g.vol + block - 1) / block) * (long)ngroups;
+    const long nblk = ((a.nsites + block - 1) / block) * (long)ngroups;
     if (dag) k_brillouin<T, R, true><<<(unsigned)nblk, block, 0, st>>>(a, ngroups);
     else k_brillouin<T, R, false><<<(unsigned)nblk, block, 0, st>>>(a, ngroups);
     return cudaGetLastError();

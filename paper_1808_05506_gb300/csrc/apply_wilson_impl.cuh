@@ -14,8 +14,8 @@ __global__ void __launch_bounds__(256) k_wilson(ApplyArgs a, int ngroups)
     const long b = blockIdx.x;
     const int group = (int)(b % ngroups);
     const long p = (b / ngroups) * blockDim.x + threadIdx.x;
-    if (p >= a.g.vol) return;
-    wilson_site<T, R, DAG>(a, site_of(a.g, p, a.tc), group);
+    if (p >= a.nsites) return;
+    wilson_site<T, R, DAG>(a, slab_site(a, p), group);
 }
 
 // V_TMARCH: blockDim = (sites, groups); a block owns a run of `block` site
@@ -31,9 +31,9 @@ __global__ void __launch_bounds__(192, 2) k_wilson_march(ApplyArgs a, int ngroup
     const int group = (int)(b % nchunks) * gy + threadIdx.y;
     b /= nchunks;
     const long s3 = (b % nruns) * blockDim.x + threadIdx.x;
-    const int t0 = (int)(b / nruns) * tc;
+    const int t0 = a.t0 + (int)(b / nruns) * tc;
     if (s3 >= vol3 || group >= ngroups) return;
-    wilson_column<T, R, DAG>(a, s3, group, t0, min(t0 + tc, a.g.L[3]));
+    wilson_column<T, R, DAG>(a, s3, group, t0, min(t0 + tc, a.t0 + a.nt));
 }
 
 // V_XROW: blockDim = (32, gy); warp y of block b takes right-hand-side group
@@ -48,9 +48,9 @@ __global__ void __launch_bounds__(192, 2) k_wilson_xrow(ApplyArgs a, int ngroups
     const int group = (int)(b % nchunks) * gy + threadIdx.y;
     b /= nchunks;
     const long s3 = (b % nruns) * 32 + threadIdx.x;
-    const int t0 = (int)(b / nruns) * tc;
+    const int t0 = a.t0 + (int)(b / nruns) * tc;
     if (group >= ngroups) return;   // a whole warp
-    wilson_xrow<T, R, DAG>(a, s3, threadIdx.x, group, t0, min(t0 + tc, a.g.L[3]));
+    wilson_xrow<T, R, DAG>(a, s3, threadIdx.x, group, t0, min(t0 + tc, a.t0 + a.nt));
 }
 
 // V_TMA: persistent CTAs; one producer warp streams the stages of each tile
@@ -205,8 +205,8 @@ __global__ void __launch_bounds__(192, 2) k_wilson_groups(ApplyArgs a, int ngrou
     const long b = blockIdx.x;
     const int group = (int)(b % nchunks) * gy + threadIdx.y;
     const long p = (b / nchunks) * blockDim.x + threadIdx.x;
-    if (p >= a.g.vol || group >= ngroups) return;
-    wilson_site<T, R, DAG>(a, site_of(a.g, p, a.tc), group);
+    if (p >= a.nsites || group >= ngroups) return;
+    wilson_site<T, R, DAG>(a, slab_site(a, p), group);
 }
 
 template <typename T, int R>
@@ -214,11 +214,11 @@ cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
 {
     const int block = c.block;
     const int ngroups = (a.Nv + R - 1) / R;
-    const long nblk = ((a.g.vol + block - 1) / block) * (long)ngroups;
+    const long nblk = ((a.nsites + block - 1) / block) * (long)ngroups;
     if constexpr (sizeof(T) != 8) {
     if (c.variant == V_GROUPS) {
         const int gy = groups_per_block(block, ngroups);
-        const long nb = ((a.g.vol + block - 1) / block) * (long)((ngroups + gy - 1) / gy);
+        const long nb = ((a.nsites + block - 1) / block) * (long)((ngroups + gy - 1) / gy);
         if (dag) k_wilson_groups<T, R, true><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
         else k_wilson_groups<T, R, false><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
         return cudaGetLastError();
@@ -227,8 +227,8 @@ cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
     if (c.variant == V_XROW) {
         // the host checked 32 % Lx == 0 and vol3 % 32 == 0: every warp is full
         const int gy = min(c.block / 32, ngroups);
-        const int tc = a.g.L[3] < 8 ? a.g.L[3] : 8;
-        const long nb = (a.g.stride[3] / 32) * (long)((ngroups + gy - 1) / gy) * (long)((a.g.L[3] + tc - 1) / tc);
+        const int tc = a.nt < 8 ? a.nt : 8;
+        const long nb = (a.g.stride[3] / 32) * (long)((ngroups + gy - 1) / gy) * (long)((a.nt + tc - 1) / tc);
         if (dag) k_wilson_xrow<T, R, true><<<(unsigned)nb, dim3(32, gy), 0, st>>>(a, ngroups, gy, tc);
         else k_wilson_xrow<T, R, false><<<(unsigned)nb, dim3(32, gy), 0, st>>>(a, ngroups, gy, tc);
         return cudaGetLastError();
@@ -236,9 +236,9 @@ cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
     if (c.variant == V_TMARCH) {
         const int gy = groups_per_block(block, ngroups);
         const long vol3 = a.g.stride[3];
-        const int tc = a.g.L[3] < 8 ? a.g.L[3] : 8;
+        const int tc = a.nt < 8 ? a.nt : 8;
         const long nb = ((vol3 + block - 1) / block) * (long)((ngroups + gy - 1) / gy) *
-                        (long)((a.g.L[3] + tc - 1) / tc);
+                        (long)((a.nt + tc - 1) / tc);
         if (dag) k_wilson_march<T, R, true><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy, tc);
         else k_wilson_march<T, R, false><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy, tc);
         return cudaGetLastError();

@@ -115,17 +115,25 @@ ApplyArgs dirac_handle::args(void* out, const void* in, int nv, double diag_valu
     a.diag_v = nullptr;
     a.err = dev_err;
     a.tc = 0;
+    a.t0 = 0;
+    a.nt = g.L[3];
+    a.nsites = g.vol;
     return a;
 }
 
 dirac_status dirac_handle::run_apply(bool dagger, void* out, const void* in, int nv,
                                      double diag_value, const void* link_ptr, int p, LaunchCfg c,
-                                     const double* diag_v)
+                                     const double* diag_v, int t0, int nt)
 {
     ApplyArgs a = args(out, in, nv, diag_value);
     a.links = link_ptr;
     a.diag_v = diag_v;
     a.err = dev_err;
+    if (nt > 0) {   // the slab of nt t-slices from t0 (variants 0, 1, 2 and 5)
+        a.t0 = t0;
+        a.nt = nt;
+        a.nsites = (long)nt * g.stride[3];
+    }
     a.tc = (c.variant == V_DIRECT || c.variant == V_GROUPS) ? c.order : 0;
     return cuda(launch_apply(op, p, dagger, a, c, stream), "apply kernel launch");
 }
@@ -237,6 +245,7 @@ dirac_handle::~dirac_handle()
     release(ws_in);
     release(ws_out);
     free_solver_workspace();
+    free_host_apply();
 }
 
 dirac_status dirac_destroy(dirac_handle* h)

@@ -527,13 +527,14 @@ struct Geom {
     long vol;
 };
 
-// Processing order of the sites.  With tc = 0 the p-th site is site p
-// (lexicographic).  With tc > 0 the (z, t) planes of Lx Ly sites are visited
-// in chunks of tc t-slices, and inside a chunk t runs faster than z, so a
-// site's t-neighbours are swept a few planes after it rather than a whole
-// (x, y, z) volume later; the last chunk may be shorter.  A bijection on
-// 0 <= p < vol.
-HD long site_of(const Geom& g, long p, int tc)
+// Processing order of the sites of a slab of nt consecutive t-slices.  With
+// tc = 0 the p-th site is site p of the slab (lexicographic).  With tc > 0
+// the (z, t) planes of Lx Ly sites are visited in chunks of tc t-slices, and
+// inside a chunk t runs faster than z, so a site's t-neighbours are swept a
+// few planes after it rather than a whole (x, y, z) volume later; the last
+// chunk may be shorter.  A bijection on 0 <= p < nt Lx Ly Lz (the offset of
+// the slab is added by the caller).
+HD long site_of(const Geom& g, long p, int tc, int nt)
 {
     if (tc <= 0) return p;
     const long P = g.stride[2];
@@ -542,7 +543,7 @@ HD long site_of(const Geom& g, long p, int tc)
     const int tb = (int)(q / chunk);
     const long r = q - tb * chunk;
     const int t0 = tb * tc;
-    const int n = (g.L[3] - t0 < tc) ? g.L[3] - t0 : tc;
+    const int n = (nt - t0 < tc) ? nt - t0 : tc;
     const int z = (int)(r / n), ti = (int)(r - (long)z * n);
     return w + P * (z + (long)g.L[2] * (t0 + ti));
 }

@@ -34,6 +34,9 @@ struct dirac_handle {
     size_t sw_bytes = 0;
     int sw_nv = 0;
 
+    // streams, events and staging buffers of dirac_apply_host (dirac_host_apply.cu)
+    void* hx = nullptr;
+
     std::string err;
 
     ~dirac_handle();
@@ -49,8 +52,10 @@ struct dirac_handle {
     dirac_status build_W64();
     dirac::ApplyArgs args(void* out, const void* in, int nv, double diag_value) const;
     dirac_status run_apply(bool dagger, void* out, const void* in, int nv, double diag_value,
-                           const void* link_ptr, int p, dirac::LaunchCfg c, const double* diag_v = nullptr);
+                           const void* link_ptr, int p, dirac::LaunchCfg c, const double* diag_v = nullptr,
+                           int t0 = 0, int nt = 0);
     void free_solver_workspace();
+    void free_host_apply();
 };
 
 bool dirac_check_device_ptr(const void* p);

@@ -71,11 +71,14 @@ cudaError_t launch_apply_brillouin(int prec, bool dagger, const ApplyArgs& a, La
 void brillouin_tables(BriDir dirs[80], int rep_dir81[40]);
 cudaError_t upload_brillouin_table(cudaStream_t st);
 
-// canonical (complex double if canon_f64 else complex float) <-> internal spinor
+// canonical (complex double if canon_f64 else complex float) <-> internal spinor;
+// canon holds the sites site0 .. site0 + nsites - 1 (nsites < 0: all sites)
 cudaError_t launch_pack_spinor(int prec, int nsc, const Geom& g, int Nv, const void* canon,
-                               bool canon_f64, void* internal, cudaStream_t st);
+                               bool canon_f64, void* internal, cudaStream_t st, long site0 = 0,
+                               long nsites = -1);
 cudaError_t launch_unpack_spinor(int prec, int nsc, const Geom& g, int Nv, const void* internal,
-                                 void* canon, bool canon_f64, cudaStream_t st);
+                                 void* canon, bool canon_f64, cudaStream_t st, long site0 = 0,
+                                 long nsites = -1);
 
 // column c of a canonical FP64 field with Nsrc right-hand sides <-> slot v of an
 // internal FP64 field

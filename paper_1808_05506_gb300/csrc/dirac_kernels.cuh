@@ -37,7 +37,17 @@ struct ApplyArgs {
     const double* diag_v; // per-right-hand-side diagonal (device, Nv entries) or null: diag for all
     int* err;             // device error word (kernels with bounded waits record DIRAC_TIMEOUT) or null
     int tc;               // site order of the grid (site_of): 0 lexicographic, else t-chunk
+    // the sweep covers the slab of nt t-slices starting at slice t0 (sites
+    // t0 Lx Ly Lz .. + nsites); the whole lattice: t0 = 0, nt = Nt
+    int t0, nt;
+    long nsites;
 };
+
+// site of the p-th work item of a sweep over the slab of a
+template <typename Args> HD long slab_site(const Args& a, long p)
+{
+    return (long)a.t0 * a.g.stride[3] + site_of(a.g, p, a.tc, a.nt);
+}
 
 template <typename A> DEV_INLINE A diag_of(const ApplyArgs& a, int v)
 {

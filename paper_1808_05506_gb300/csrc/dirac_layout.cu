@@ -55,13 +55,14 @@ __device__ __forceinline__ void canon_store(CT* dst, const cx<A>* p)
     }
 }
 
+// canon holds the sites site0 .. site0 + nsites - 1 (a t-slab, or the whole lattice)
 template <typename T, int NSC, typename CT>
-__global__ void k_pack(Geom g, int Nv, const CT* __restrict__ canon, void* internal)
+__global__ void k_pack(Geom g, int Nv, const CT* __restrict__ canon, void* internal, long site0, long nsites)
 {
     using A = typename Store<T>::A;
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;   // (site, v), v fastest
-    if (i >= g.vol * Nv) return;
-    const long s = i / Nv;
+    if (i >= nsites * Nv) return;
+    const long s = site0 + i / Nv;
     const int v = (int)(i % Nv);
     cx<A> p[NSC];
     canon_load<NSC, CT, A>(canon + (size_t)i * NSC * 2, p);
@@ -69,12 +70,12 @@ __global__ void k_pack(Geom g, int Nv, const CT* __restrict__ canon, void* inter
 }
 
 template <typename T, int NSC, typename CT>
-__global__ void k_unpack(Geom g, int Nv, const void* internal, CT* __restrict__ canon)
+__global__ void k_unpack(Geom g, int Nv, const void* internal, CT* __restrict__ canon, long site0, long nsites)
 {
     using A = typename Store<T>::A;
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.vol * Nv) return;
-    const long s = i / Nv;
+    if (i >= nsites * Nv) return;
+    const long s = site0 + i / Nv;
     const int v = (int)(i % Nv);
     cx<A> p[NSC];
     load_spinor<T, NSC>(internal, g.vol, v, s, p);
@@ -83,23 +84,23 @@ __global__ void k_unpack(Geom g, int Nv, const void* internal, CT* __restrict__ 
 
 template <typename T, int NSC>
 static cudaError_t pack_T(const Geom& g, int Nv, const void* canon, bool f64, void* internal,
-                          cudaStream_t st)
+                          cudaStream_t st, long site0, long nsites)
 {
-    const long n = g.vol * Nv;
+    const long n = nsites * Nv;
     const unsigned nb = (unsigned)((n + 255) / 256);
-    if (f64) k_pack<T, NSC, double><<<nb, 256, 0, st>>>(g, Nv, (const double*)canon, internal);
-    else k_pack<T, NSC, float><<<nb, 256, 0, st>>>(g, Nv, (const float*)canon, internal);
+    if (f64) k_pack<T, NSC, double><<<nb, 256, 0, st>>>(g, Nv, (const double*)canon, internal, site0, nsites);
+    else k_pack<T, NSC, float><<<nb, 256, 0, st>>>(g, Nv, (const float*)canon, internal, site0, nsites);
     return cudaGetLastError();
 }
 
 template <typename T, int NSC>
 static cudaError_t unpack_T(const Geom& g, int Nv, const void* internal, void* canon, bool f64,
-                            cudaStream_t st)
+                            cudaStream_t st, long site0, long nsites)
 {
-    const long n = g.vol * Nv;
+    const long n = nsites * Nv;
     const unsigned nb = (unsigned)((n + 255) / 256);
-    if (f64) k_unpack<T, NSC, double><<<nb, 256, 0, st>>>(g, Nv, internal, (double*)canon);
-    else k_unpack<T, NSC, float><<<nb, 256, 0, st>>>(g, Nv, internal, (float*)canon);
+    if (f64) k_unpack<T, NSC, double><<<nb, 256, 0, st>>>(g, Nv, internal, (double*)canon, site0, nsites);
+    else k_unpack<T, NSC, float><<<nb, 256, 0, st>>>(g, Nv, internal, (float*)canon, site0, nsites);
     return cudaGetLastError();
 }
 
@@ -114,17 +115,19 @@ static cudaError_t unpack_T(const Geom& g, int Nv, const void* internal, void* c
     }
 
 cudaError_t launch_pack_spinor(int prec, int nsc, const Geom& g, int Nv, const void* canon,
-                               bool canon_f64, void* internal, cudaStream_t st)
+                               bool canon_f64, void* internal, cudaStream_t st, long site0, long nsites)
 {
-    if (g.vol * Nv == 0) return cudaSuccess;
-    DISPATCH_PREC_NSC(pack_T, g, Nv, canon, canon_f64, internal, st)
+    if (nsites < 0) nsites = g.vol;
+    if (nsites * Nv == 0) return cudaSuccess;
+    DISPATCH_PREC_NSC(pack_T, g, Nv, canon, canon_f64, internal, st, site0, nsites)
 }
 
 cudaError_t launch_unpack_spinor(int prec, int nsc, const Geom& g, int Nv, const void* internal,
-                                 void* canon, bool canon_f64, cudaStream_t st)
+                                 void* canon, bool canon_f64, cudaStream_t st, long site0, long nsites)
 {
-    if (g.vol * Nv == 0) return cudaSuccess;
-    DISPATCH_PREC_NSC(unpack_T, g, Nv, internal, canon, canon_f64, st)
+    if (nsites < 0) nsites = g.vol;
+    if (nsites * Nv == 0) return cudaSuccess;
+    DISPATCH_PREC_NSC(unpack_T, g, Nv, internal, canon, canon_f64, st, site0, nsites)
 }
 
 // one column c of a canonical FP64 field with Nsrc right-hand sides <-> slot v

@@ -144,6 +144,7 @@ def test_binding_calls_match_the_c_signatures(dg, monkeypatch):
     D.unpack(torch.zeros(8, dtype=torch.uint8), out=x.clone())
     D.apply(x, out=x.clone())
     D.apply_dagger(x, out=x.clone())
+    D.apply_host(x, out=x.clone(), dagger=True, sync=False)
     D.force(x, x, out=V.clone())
     D.set_kernel_config(2, 128, 3)
     D.kernel_config()
@@ -155,7 +156,7 @@ def test_binding_calls_match_the_c_signatures(dg, monkeypatch):
     D.close()
     for name in ("dirac_set_links", "dirac_apply", "dirac_apply_dagger", "dirac_force", "dirac_solve",
                  "dirac_set_kernel_config", "dirac_get_kernel_config", "dirac_autotune", "dirac_destroy",
-                 "dirac_solve_batched", "dirac_set_site_order", "dirac_get_site_order"):
+                 "dirac_solve_batched", "dirac_set_site_order", "dirac_get_site_order", "dirac_apply_host"):
         assert name in calls, name
 
 

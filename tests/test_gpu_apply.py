@@ -149,6 +149,68 @@ def test_wilson_xrow_shapes(dg, prec):
                     assert rel_l2(got, want) <= TOL[prec], (L, Nv, R, block, dagger)
 
 
+@pytest.mark.parametrize("op,mass", [("wilson", 0.124), ("staggered", 0.05), ("brillouin", 0.2)])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_apply_host_matches_device_apply(dg, op, mass, prec):
+    """dirac_apply_host (host fields, slabs of t-slices streamed through the
+    device) gives the device apply bit for bit: one slice per slab (Nt = 2, 5),
+    two slices per slab with a one-slice last slab (Nt = 17), three with a
+    one-slice last slab (Nt = 34); pinned and pageable host memory, D and D^+."""
+    for L in ((4, 4, 2, 2), (4, 2, 4, 5), (2, 2, 4, 17), (2, 2, 2, 34)):
+        Nv = 3
+        V, psi = inputs(op, L, Nv, prec, 290)
+        D = dg.Dirac(op, L, Nv, mass, prec)
+        D.set_links(torch.from_numpy(V.astype(np.complex128 if prec == "f64" else np.complex64)).cuda())
+        D.set_kernel_config(2, 64, 0 if prec == "f64" else 1)
+        x = torch.from_numpy(psi.astype(np.complex128 if prec == "f64" else np.complex64))
+        for dagger in (False, True):
+            ref = D.apply(x.cuda(), dagger=dagger).cpu()
+            for pinned in (True, False):
+                xin = x.pin_memory() if pinned else x.clone()
+                got = D.apply_host(xin, dagger=dagger)
+                assert torch.equal(got, ref), (L, dagger, pinned)
+            want = oracle.apply(op, V, psi, m0_of(op, mass), dagger=dagger)
+            assert rel_l2(got.numpy().astype(np.complex128), want) <= TOL[prec]
+        D.close()
+
+
+@pytest.mark.parametrize("variant", [0, 2, 5, 3])
+def test_apply_host_launch_variants(dg, variant):
+    """The slab sweeps of the t-march (2) and x-row (5) Wilson variants, and a
+    configuration that cannot sweep a slab (3: replaced by variant 1)."""
+    L, Nv = (8, 4, 2, 10), 5
+    V, psi = inputs("wilson", L, Nv, "f32", 291)
+    D = dg.Dirac("wilson", L, Nv, 0.122, "f32")
+    D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
+    D.set_kernel_config(2, 64, variant)
+    x = torch.from_numpy(psi.astype(np.complex64)).pin_memory()
+    want = oracle.apply("wilson", V, psi, oracle.kappa_to_m0(0.122))
+    got = D.apply_host(x)
+    assert rel_l2(got.numpy().astype(np.complex128), want) <= TOL["f32"]
+    # repeated calls reuse the staging buffers and streams
+    got2 = D.apply_host(x, out=torch.empty_like(x).pin_memory())
+    assert torch.equal(got, got2)
+    D.close()
+
+
+def test_apply_host_rejects_device_memory(dg):
+    L, Nv = (4, 4, 4, 4), 2
+    D = dg.Dirac("wilson", L, Nv, 0.12, "f32")
+    x = torch.zeros(D.canonical_shape, dtype=torch.complex64)
+    with pytest.raises(dg.DiracError):
+        D.apply_host(x)                                   # no links yet
+    V, _ = inputs("wilson", L, Nv, "f32", 292)
+    D.set_links(torch.from_numpy(V.astype(np.complex64)))
+    xd = x.cuda()
+    st = dg.dirac_apply_host(D.h, dg._ptr(xd), dg._ptr(xd), 0)
+    assert st == dg.ERR_INVALID_ARG
+    st = dg.dirac_apply_host(D.h, dg._ptr(x), dg._ptr(x), 0)   # out overlaps in
+    assert st == dg.ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        D.apply_host(xd)
+    D.close()
+
+
 def test_autotune(dg, tmp_path, monkeypatch):
     """The tuner keeps a supported configuration that reproduces the sweep and
     writes / reuses its cache file."""
