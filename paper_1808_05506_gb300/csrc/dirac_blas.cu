@@ -6,7 +6,12 @@
 // Arithmetic is FP32 for FP32/BF16/FP16 storage and FP64 for FP64 storage;
 // every norm and dot product is accumulated in FP64: per-thread sums, warp
 // shuffles, one partial per block, then a second kernel that adds the
-// partials of each right-hand side in a fixed order (deterministic).
+// partials of each right-hand side in a fixed order (deterministic).  With
+// FP32 arithmetic a thread first sums KF consecutive terms of its stride in
+// FP32 and adds that sum to its FP64 accumulator (FP64 runs at a small
+// fraction of the FP32 rate on this GPU, and one FP64 operation per term
+// made the norms FP64-bound); each such FP32 sum of KF terms has a relative
+// error below KF * 2^-24, which does not grow with the field size.
 #include "dirac_blas.h"
 
 namespace dirac {
@@ -67,16 +72,43 @@ template <typename A> __device__ __forceinline__ double norm2c(cx<A> c)
     return (double)c.re * (double)c.re + (double)c.im * (double)c.im;
 }
 
+constexpr int KF = 16;   // terms per FP32 partial sum
+
+// FP64 accumulator fed by FP32 partial sums of KF terms (FP32 arithmetic), or
+// plain FP64 (FP64 arithmetic)
+template <typename A> struct Acc {
+    double s = 0.0;
+    A f = A(0);
+    int c = 0;
+    __device__ __forceinline__ void add(A v)
+    {
+        if constexpr (sizeof(A) == 8) {
+            s += v;
+        } else {
+            f += v;
+            if (++c == KF) {
+                s += (double)f;
+                f = A(0);
+                c = 0;
+            }
+        }
+    }
+    __device__ __forceinline__ double total() const { return sizeof(A) == 8 ? s : s + (double)f; }
+};
+
 // ---------------------------------------------------------------- norms
 template <typename T>
 __global__ void k_norm2(size_t n, const void* __restrict__ x, double* part)
 {
+    using A = typename Store<T>::A;
     const int v = blockIdx.y;
     const size_t base = (size_t)v * n;
-    double s = 0.0;
-    for (size_t i = (size_t)blockIdx.x * BT + threadIdx.x; i < n; i += (size_t)gridDim.x * BT)
-        s += norm2c(ld_one<T>(x, base + i));
-    block_partial(s, part, (size_t)v * gridDim.x + blockIdx.x);
+    Acc<A> s;
+    for (size_t i = (size_t)blockIdx.x * BT + threadIdx.x; i < n; i += (size_t)gridDim.x * BT) {
+        const cx<A> c = ld_one<T>(x, base + i);
+        s.add(fma(c.re, c.re, c.im * c.im));
+    }
+    block_partial(s.total(), part, (size_t)v * gridDim.x + blockIdx.x);
 }
 
 // re <x, y> and im <x, y> = sum conj(x) y
@@ -84,18 +116,19 @@ template <typename T>
 __global__ void k_dot(size_t n, const void* __restrict__ x, const void* __restrict__ y, double* part_re,
                       double* part_im)
 {
+    using A = typename Store<T>::A;
     const int v = blockIdx.y;
     const size_t base = (size_t)v * n;
-    double sr = 0.0, si = 0.0;
+    Acc<A> sr, si;
     for (size_t i = (size_t)blockIdx.x * BT + threadIdx.x; i < n; i += (size_t)gridDim.x * BT) {
-        auto a = ld_one<T>(x, base + i);
-        auto b = ld_one<T>(y, base + i);
-        sr += (double)a.re * b.re + (double)a.im * b.im;
-        si += (double)a.re * b.im - (double)a.im * b.re;
+        const cx<A> a = ld_one<T>(x, base + i);
+        const cx<A> b = ld_one<T>(y, base + i);
+        sr.add(fma(a.re, b.re, a.im * b.im));
+        si.add(fma(a.re, b.im, -(a.im * b.re)));
     }
-    block_partial(sr, part_re, (size_t)v * gridDim.x + blockIdx.x);
+    block_partial(sr.total(), part_re, (size_t)v * gridDim.x + blockIdx.x);
     __syncthreads();
-    block_partial(si, part_im, (size_t)v * gridDim.x + blockIdx.x);
+    block_partial(si.total(), part_im, (size_t)v * gridDim.x + blockIdx.x);
 }
 
 // ---------------------------------------------------------------- CGLS steps
@@ -108,7 +141,7 @@ __global__ void k_cgls_step(size_t n, const double* __restrict__ alpha, void* e,
     const int v = blockIdx.y;
     const size_t base = (size_t)v * n;
     const A a = (A)alpha[v];
-    double s = 0.0;
+    Acc<A> s;
     for (size_t i = (size_t)blockIdx.x * BT + threadIdx.x; i < n; i += (size_t)gridDim.x * BT) {
         cx<A> ev = ld_one<T>(e, base + i), pv = ld_one<T>(p, base + i);
         cx<A> rv = ld_one<T>(r, base + i), tv = ld_one<T>(t, base + i);
@@ -118,9 +151,9 @@ __global__ void k_cgls_step(size_t n, const double* __restrict__ alpha, void* e,
         rv.im = fma(-a, tv.im, rv.im);
         st_one<T>(e, base + i, ev);
         st_one<T>(r, base + i, rv);
-        s += norm2c(rv);
+        s.add(fma(rv.re, rv.re, rv.im * rv.im));
     }
-    block_partial(s, part, (size_t)v * gridDim.x + blockIdx.x);
+    block_partial(s.total(), part, (size_t)v * gridDim.x + blockIdx.x);
 }
 
 // p = s + beta_v p
@@ -139,6 +172,81 @@ __global__ void k_xpay(size_t n, const void* __restrict__ s, const double* __res
     }
 }
 
+// ---------------------------------------------------------------- 16-byte forms
+// The same three kernels on 16-byte elements (Store<T>::CPV complex numbers
+// each), for segments whose length n is a multiple of CPV; m = n / CPV.
+template <typename T>
+__global__ void k_norm2_v(size_t m, const void* __restrict__ x, double* part)
+{
+    using A = typename Store<T>::A;
+    constexpr int C = Store<T>::CPV;
+    const int v = blockIdx.y;
+    const size_t base = (size_t)v * m;
+    Acc<A> s;
+    for (size_t i = (size_t)blockIdx.x * BT + threadIdx.x; i < m; i += (size_t)gridDim.x * BT) {
+        cx<A> c[C];
+        ld_vec<T>(x, base + i, c);
+        A q = A(0);
+#pragma unroll
+        for (int j = 0; j < C; ++j) q = fma(c[j].re, c[j].re, fma(c[j].im, c[j].im, q));
+        s.add(q);
+    }
+    block_partial(s.total(), part, (size_t)v * gridDim.x + blockIdx.x);
+}
+
+template <typename T>
+__global__ void k_cgls_step_v(size_t m, const double* __restrict__ alpha, void* e, const void* __restrict__ p,
+                              void* r, const void* __restrict__ t, double* part)
+{
+    using A = typename Store<T>::A;
+    constexpr int C = Store<T>::CPV;
+    const int v = blockIdx.y;
+    const size_t base = (size_t)v * m;
+    const A a = (A)alpha[v];
+    Acc<A> s;
+    for (size_t i = (size_t)blockIdx.x * BT + threadIdx.x; i < m; i += (size_t)gridDim.x * BT) {
+        cx<A> ev[C], pv[C], rv[C], tv[C];
+        ld_vec<T>(e, base + i, ev);
+        ld_vec<T>(p, base + i, pv);
+        ld_vec<T>(r, base + i, rv);
+        ld_vec<T>(t, base + i, tv);
+        A q = A(0);
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            ev[j].re = fma(a, pv[j].re, ev[j].re);
+            ev[j].im = fma(a, pv[j].im, ev[j].im);
+            rv[j].re = fma(-a, tv[j].re, rv[j].re);
+            rv[j].im = fma(-a, tv[j].im, rv[j].im);
+            q = fma(rv[j].re, rv[j].re, fma(rv[j].im, rv[j].im, q));
+        }
+        st_vec<T>(e, base + i, ev);
+        st_vec<T>(r, base + i, rv);
+        s.add(q);
+    }
+    block_partial(s.total(), part, (size_t)v * gridDim.x + blockIdx.x);
+}
+
+template <typename T>
+__global__ void k_xpay_v(size_t m, const void* __restrict__ s, const double* __restrict__ beta, void* p)
+{
+    using A = typename Store<T>::A;
+    constexpr int C = Store<T>::CPV;
+    const int v = blockIdx.y;
+    const size_t base = (size_t)v * m;
+    const A b = (A)beta[v];
+    for (size_t i = (size_t)blockIdx.x * BT + threadIdx.x; i < m; i += (size_t)gridDim.x * BT) {
+        cx<A> sv[C], pv[C];
+        ld_vec<T>(s, base + i, sv);
+        ld_vec<T>(p, base + i, pv);
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            pv[j].re = fma(b, pv[j].re, sv[j].re);
+            pv[j].im = fma(b, pv[j].im, sv[j].im);
+        }
+        st_vec<T>(p, base + i, pv);
+    }
+}
+
 // dst = scale_v * src within one storage type, optional partial |dst|^2
 template <typename T>
 __global__ void k_scale_copy(size_t n, const void* __restrict__ src, const double* __restrict__ scale, void* dst,
@@ -147,15 +255,15 @@ __global__ void k_scale_copy(size_t n, const void* __restrict__ src, const doubl
     using A = typename Store<T>::A;
     const int v = blockIdx.y;
     const size_t base = (size_t)v * n;
-    const double c = scale ? scale[v] : 1.0;
-    double s = 0.0;
+    const A c = (A)(scale ? scale[v] : 1.0);
+    Acc<A> s;
     for (size_t i = (size_t)blockIdx.x * BT + threadIdx.x; i < n; i += (size_t)gridDim.x * BT) {
         auto x = ld_one<T>(src, base + i);
-        cx<A> y{(A)(c * (double)x.re), (A)(c * (double)x.im)};
+        cx<A> y{c * x.re, c * x.im};
         st_one<T>(dst, base + i, y);
-        s += norm2c(y);
+        s.add(fma(y.re, y.re, y.im * y.im));
     }
-    if (part) block_partial(s, part, (size_t)v * gridDim.x + blockIdx.x);
+    if (part) block_partial(s.total(), part, (size_t)v * gridDim.x + blockIdx.x);
 }
 
 // r64 = b64 - a64, partial |r|^2 (FP64 fields)
@@ -187,19 +295,21 @@ __global__ void k_convert(long vol, const void* __restrict__ src, const double* 
     using AD = typename Store<TD>::A;
     const int v = blockIdx.y;
     const double c = scale ? scale[v] : 1.0;
-    double s2 = 0.0;
+    Acc<AD> s2;
     for (long s = (long)blockIdx.x * BT + threadIdx.x; s < vol; s += (long)gridDim.x * BT) {
         cx<AS> a[NSC];
         cx<AD> b[NSC];
         load_spinor<TS, NSC>(src, vol, v, s, a);
+        AD q = AD(0);
 #pragma unroll
         for (int k = 0; k < NSC; ++k) {
             b[k] = cx<AD>{(AD)(c * (double)a[k].re), (AD)(c * (double)a[k].im)};
-            s2 += norm2c(b[k]);
+            q = fma(b[k].re, b[k].re, fma(b[k].im, b[k].im, q));
         }
+        s2.add(q);
         store_spinor<TD, NSC>(dst, vol, v, s, b);
     }
-    if (part) block_partial(s2, part, (size_t)v * gridDim.x + blockIdx.x);
+    if (part) block_partial(s2.total(), part, (size_t)v * gridDim.x + blockIdx.x);
 }
 
 // x64 += coef_v * e  (e in storage type T, x in FP64), site by site
@@ -236,11 +346,16 @@ __global__ void k_axpy_to64(long vol, const double* __restrict__ coef, const voi
 
 static dim3 grid_of(size_t n, int Nv) { return dim3((unsigned)blas_blocks(n), (unsigned)Nv); }
 
+// complex numbers per 16-byte element of a storage precision
+static int cpv_of(int prec) { return prec == P_F64 ? 1 : (prec == P_F32 ? 2 : 4); }
+
 cudaError_t blas_norm2(int prec, size_t n, int Nv, const void* x, double* part, double* out,
                        cudaStream_t st)
 {
-    dim3 g = grid_of(n, Nv);
-#define GO(T) k_norm2<T><<<g, BT, 0, st>>>(n, x, part)
+    const int C = cpv_of(prec);
+    const bool vec = n % C == 0;
+    dim3 g = grid_of(vec ? n / C : n, Nv);
+#define GO(T) (vec ? k_norm2_v<T><<<g, BT, 0, st>>>(n / C, x, part) : k_norm2<T><<<g, BT, 0, st>>>(n, x, part))
     PREC_SWITCH(prec, GO)
 #undef GO
     k_reduce_partials<<<Nv, BT, 0, st>>>(part, g.x, out, 0);
@@ -263,8 +378,11 @@ cudaError_t blas_dot(int prec, size_t n, int Nv, const void* x, const void* y, d
 cudaError_t blas_cgls_step(int prec, size_t n, int Nv, const double* alpha, void* e, const void* p, void* r,
                            const void* t, double* part, double* rr, cudaStream_t st)
 {
-    dim3 g = grid_of(n, Nv);
-#define GO(T) k_cgls_step<T><<<g, BT, 0, st>>>(n, alpha, e, p, r, t, part)
+    const int C = cpv_of(prec);
+    const bool vec = n % C == 0;
+    dim3 g = grid_of(vec ? n / C : n, Nv);
+#define GO(T) (vec ? k_cgls_step_v<T><<<g, BT, 0, st>>>(n / C, alpha, e, p, r, t, part) \
+               : k_cgls_step<T><<<g, BT, 0, st>>>(n, alpha, e, p, r, t, part))
     PREC_SWITCH(prec, GO)
 #undef GO
     k_reduce_partials<<<Nv, BT, 0, st>>>(part, g.x, rr, 0);
@@ -273,8 +391,10 @@ cudaError_t blas_cgls_step(int prec, size_t n, int Nv, const double* alpha, void
 
 cudaError_t blas_xpay(int prec, size_t n, int Nv, const void* s, const double* beta, void* p, cudaStream_t st)
 {
-    dim3 g = grid_of(n, Nv);
-#define GO(T) k_xpay<T><<<g, BT, 0, st>>>(n, s, beta, p)
+    const int C = cpv_of(prec);
+    const bool vec = n % C == 0;
+    dim3 g = grid_of(vec ? n / C : n, Nv);
+#define GO(T) (vec ? k_xpay_v<T><<<g, BT, 0, st>>>(n / C, s, beta, p) : k_xpay<T><<<g, BT, 0, st>>>(n, s, beta, p))
     PREC_SWITCH(prec, GO)
 #undef GO
     return cudaGetLastError();
