@@ -242,6 +242,44 @@ def solve_times(dg, torch, L=(24, 24, 24, 48), Nv=12, m0=0.05, precs=("f32", "bf
     return out
 
 
+def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=("f32", "bf16", "f16")):
+    """Wilson systems D(kappa_i) x_i = b_i on one gauge field, Nv_i ~ U{1..24},
+    kappa_i ~ U[0.120, 0.124], through dirac_solve_batched with `slots` resident
+    right-hand-side columns, each precision to a true FP64 residual of 1e-10:
+    the batched form of the mixed-vs-FP32 solve time (fewer systems than the
+    48 of the full configuration, so that the benchmark stays within minutes)."""
+    rng = np.random.default_rng(7)
+    nvs = [int(v) for v in rng.integers(1, 25, nsys)]
+    kap = [float(v) for v in rng.uniform(0.120, 0.124, nsys)]
+    V = synth.gauge_links(L, 3, "near_identity", 1005, eps=0.3)
+    bs = [torch.from_numpy(synth.spinor(L, nv, 4, 3, 2100 + i)).cuda() for i, nv in enumerate(nvs)]
+    out = {}
+    for prec in precs:
+        D = dg.Dirac("wilson", L, slots, 0.122, prec)
+        D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
+        D.autotune()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xs, res, _, st, status = D.solve_batched(bs, kap, tol=1e-10)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[prec] = {"seconds": dt, "status": int(status), "max_rel_residual": float(res.max()),
+                     "outer": st["outer_iterations"], "inner": st["inner_iterations"], "sweeps": st["sweeps"],
+                     "fp64_sweeps": st["fp64_sweeps"], "kernel": list(D.kernel_config())}
+        D.close()
+        del xs
+        torch.cuda.empty_cache()
+    if "f32" in out:
+        for p in precs:
+            if p != "f32":
+                out[p]["speedup_vs_f32"] = out["f32"]["seconds"] / out[p]["seconds"]
+    out["workload"] = "wilson_batched_solve_{}_{}sys_nv{}_{}slots".format("x".join(map(str, L)), nsys,
+                                                                        "-".join(map(str, nvs)), slots)
+    del bs
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_oracle_rate(w, inputs=None, seconds=15.0):
     s = OracleSample(w, inputs)
     n = s.calibrate(seconds)
@@ -427,6 +465,7 @@ def main():
         line["extra"] = extra
     if not args.no_solve and not args.no_extra:
         line["solve"] = solve_times(dg, torch)
+        line["batched_solve"] = batched_solve_times(dg, torch)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_rate(w, inputs=(V, psi))
     if rank == 0:
