@@ -135,6 +135,10 @@ dirac_status dirac_handle::run_apply(bool dagger, void* out, const void* in, int
         a.nsites = (long)nt * g.stride[3];
     }
     a.tc = (c.variant == V_DIRECT || c.variant == V_GROUPS) ? c.order : 0;
+    if (a.tc > 0) {
+        a.fdc = make_fdiv((uint32_t)(g.L[2] * a.tc));
+        a.fdt = make_fdiv((uint32_t)a.tc);
+    }
     return cuda(launch_apply(op, p, dagger, a, c, stream), "apply kernel launch");
 }
 
@@ -197,15 +201,7 @@ dirac_status dirac_create(dirac_handle** h, dirac_op op, int Nc, int Nx, int Ny,
     H->Nc = Nc;
     H->Nv = Nv;
     H->prec = (int)prec;
-    H->g.L[0] = Nx;
-    H->g.L[1] = Ny;
-    H->g.L[2] = Nz;
-    H->g.L[3] = Nt;
-    H->g.stride[0] = 1;
-    H->g.stride[1] = Nx;
-    H->g.stride[2] = (long)Nx * Ny;
-    H->g.stride[3] = (long)Nx * Ny * Nz;
-    H->g.vol = vol;
+    H->g = make_geom(Nx, Ny, Nz, Nt);
     H->mass = mass;
     H->diag = H->diag_of(mass);
     H->stream = (cudaStream_t)stream;

@@ -521,11 +521,60 @@ template <int N> DEV_INLINE void cp_async_wait()
 }
 
 // ---------------------------------------------------------------- geometry
+// Division by an invariant divisor as a multiply-high and a shift (Granlund
+// and Montgomery, "Division by invariant integers using multiplication",
+// PLDI 1994): for 0 <= n < 2^31 and 2 <= d < 2^31, with s = ceil(log2 d) and
+// M = floor(2^(31+s) / d) + 1 (< 2^32), d < M d - 2^(31+s) + d <= 2^s + d
+// gives floor(n / d) = floor(n M / 2^(31+s)).  Site indices are below 2^31.
+struct FDiv {
+    uint32_t d = 1, M = 0;
+    int sh = 0;   // s - 1
+};
+inline FDiv make_fdiv(uint32_t d)
+{
+    FDiv f;
+    f.d = d;
+    if (d <= 1) return f;
+    int s = 0;
+    while ((1ull << s) < d) ++s;
+    f.M = (uint32_t)((1ull << (31 + s)) / d + 1);
+    f.sh = s - 1;
+    return f;
+}
+HD uint32_t fdiv(const FDiv& f, uint32_t n)
+{
+    if (f.d == 1) return n;
+#if defined(__CUDA_ARCH__)
+    return __umulhi(n, f.M) >> f.sh;
+#else
+    return (uint32_t)(((uint64_t)n * f.M) >> 32) >> f.sh;
+#endif
+}
+
 struct Geom {
     int L[4];        // Nx, Ny, Nz, Nt
     long stride[4];  // 1, Nx, Nx Ny, Nx Ny Nz
     long vol;
+    FDiv fd[4];      // division by L[mu]
+    FDiv fdP;        // division by Nx Ny
 };
+
+inline Geom make_geom(int Nx, int Ny, int Nz, int Nt)
+{
+    Geom g;
+    g.L[0] = Nx;
+    g.L[1] = Ny;
+    g.L[2] = Nz;
+    g.L[3] = Nt;
+    g.stride[0] = 1;
+    g.stride[1] = Nx;
+    g.stride[2] = (long)Nx * Ny;
+    g.stride[3] = (long)Nx * Ny * Nz;
+    g.vol = g.stride[3] * Nt;
+    for (int mu = 0; mu < 4; ++mu) g.fd[mu] = make_fdiv((uint32_t)g.L[mu]);
+    g.fdP = make_fdiv((uint32_t)g.stride[2]);
+    return g;
+}
 
 // Processing order of the sites of a slab of nt consecutive t-slices.  With
 // tc = 0 the p-th site is site p of the slab (lexicographic).  With tc > 0
@@ -534,28 +583,33 @@ struct Geom {
 // few planes after it rather than a whole (x, y, z) volume later; the last
 // chunk may be shorter.  A bijection on 0 <= p < nt Lx Ly Lz (the offset of
 // the slab is added by the caller).
-HD long site_of(const Geom& g, long p, int tc, int nt)
+// fdc, fdt: division by Lz tc and by tc
+HD long site_of(const Geom& g, long p, int tc, int nt, const FDiv& fdc, const FDiv& fdt)
 {
     if (tc <= 0) return p;
-    const long P = g.stride[2];
-    const long q = p / P, w = p - q * P;
-    const long chunk = (long)g.L[2] * tc;
-    const int tb = (int)(q / chunk);
-    const long r = q - tb * chunk;
-    const int t0 = tb * tc;
+    const uint32_t P = (uint32_t)g.stride[2];
+    const uint32_t q = fdiv(g.fdP, (uint32_t)p), w = (uint32_t)p - q * P;
+    const uint32_t chunk = (uint32_t)g.L[2] * (uint32_t)tc;
+    const uint32_t tb = fdiv(fdc, q);
+    const uint32_t r = q - tb * chunk;
+    const int t0 = (int)tb * tc;
     const int n = (nt - t0 < tc) ? nt - t0 : tc;
-    const int z = (int)(r / n), ti = (int)(r - (long)z * n);
-    return w + P * (z + (long)g.L[2] * (t0 + ti));
+    uint32_t z;
+    if (n == tc) z = fdiv(fdt, r);
+    else z = r / (uint32_t)n;   // the shorter last chunk
+    const int ti = (int)(r - z * (uint32_t)n);
+    return (long)w + (long)P * ((long)z + (long)g.L[2] * (t0 + ti));
 }
 
 // neighbour offsets of site s: fwd[mu] = (s + mu) - s, bwd[mu] = (s - mu) - s (periodic)
 HD void site_offsets(const Geom& g, long s, long* fwd, long* bwd, int* x)
 {
-    long r = s;
+    uint32_t r = (uint32_t)s;
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
-        int c = (int)(r % g.L[mu]);
-        r /= g.L[mu];
+        const uint32_t q = fdiv(g.fd[mu], r);
+        const int c = (int)(r - q * (uint32_t)g.L[mu]);
+        r = q;
         x[mu] = c;
         fwd[mu] = (c == g.L[mu] - 1) ? -(long)(g.L[mu] - 1) * g.stride[mu] : g.stride[mu];
         bwd[mu] = (c == 0) ? (long)(g.L[mu] - 1) * g.stride[mu] : -g.stride[mu];

@@ -41,12 +41,13 @@ struct ApplyArgs {
     // t0 Lx Ly Lz .. + nsites); the whole lattice: t0 = 0, nt = Nt
     int t0, nt;
     long nsites;
+    FDiv fdc, fdt;        // division by Lz tc and by tc (site_of)
 };
 
 // site of the p-th work item of a sweep over the slab of a
 template <typename Args> HD long slab_site(const Args& a, long p)
 {
-    return (long)a.t0 * a.g.stride[3] + site_of(a.g, p, a.tc, a.nt);
+    return (long)a.t0 * a.g.stride[3] + site_of(a.g, p, a.tc, a.nt, a.fdc, a.fdt);
 }
 
 template <typename A> DEV_INLINE A diag_of(const ApplyArgs& a, int v)
