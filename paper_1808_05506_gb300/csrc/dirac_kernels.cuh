@@ -651,6 +651,38 @@ DEV_INLINE void bri_spin(const BriDirA<A>& m, const cx<A>* p, cx<A>* chi)
     }
 }
 
+// acc += M_d a + M_{-d} b for the pair of opposite directions d, -d, where
+// a = W_d psi(x + d), b = W_{-d} psi(x - d) (colour products done) and
+// M_{+-d} = lambda' +- G, G = [[0, rho Q], [rho Q^+, 0]]:
+// acc += lambda' (a + b) + G (a - b)
+template <typename A>
+DEV_INLINE void bri_pair_acc(const BriDirA<A>& m, const cx<A>* av, const cx<A>* bv, cx<A>* acc)
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        cx<A> su0 = av[c] + bv[c], su1 = av[3 + c] + bv[3 + c];
+        cx<A> sd0 = av[6 + c] + bv[6 + c], sd1 = av[9 + c] + bv[9 + c];
+        cx<A> tu0 = av[c] - bv[c], tu1 = av[3 + c] - bv[3 + c];
+        cx<A> td0 = av[6 + c] - bv[6 + c], td1 = av[9 + c] - bv[9 + c];
+        cx<A> o;
+        if constexpr (sizeof(A) == 4) {
+            o = caxpy2(m.a, su0, acc[c]); o = cfma2(m.q00, td0, o); acc[c] = cfma2(m.q01, td1, o);
+            o = caxpy2(m.a, su1, acc[3 + c]); o = cfma2(m.q10, td0, o); acc[3 + c] = cfma2(m.q11, td1, o);
+            o = caxpy2(m.a, sd0, acc[6 + c]); o = cfma2_conj(m.q00, tu0, o); acc[6 + c] = cfma2_conj(m.q10, tu1, o);
+            o = caxpy2(m.a, sd1, acc[9 + c]); o = cfma2_conj(m.q01, tu0, o); acc[9 + c] = cfma2_conj(m.q11, tu1, o);
+        } else {
+            o = acc[c] + scale(m.a, su0); o = cfma(m.q00, td0, o); acc[c] = cfma(m.q01, td1, o);
+            o = acc[3 + c] + scale(m.a, su1); o = cfma(m.q10, td0, o); acc[3 + c] = cfma(m.q11, td1, o);
+            o = acc[6 + c] + scale(m.a, sd0); o = cfma_conj(m.q00, tu0, o); acc[6 + c] = cfma_conj(m.q10, tu1, o);
+            o = acc[9 + c] + scale(m.a, sd1); o = cfma_conj(m.q01, tu0, o); acc[9 + c] = cfma_conj(m.q11, tu1, o);
+        }
+    }
+}
+
+// out = (m0 + 15/8) psi + sum over the 40 pairs (d, -d) of the stored
+// directions: the spin matrices of d and -d differ only in the sign of the
+// rho part, so both colour products are formed first and one spin matrix
+// application serves the pair
 template <typename T, int R, bool DAG>
 DEV_INLINE void brillouin_site(const ApplyArgs& a, long s, int group, const BriDir* dirs)
 {
@@ -664,31 +696,41 @@ DEV_INLINE void brillouin_site(const ApplyArgs& a, long s, int group, const BriD
     for (int r = 0; r < R; ++r)
 #pragma unroll
         for (int i = 0; i < 12; ++i) acc[r][i] = cx<A>{A(0), A(0)};
-#pragma unroll 2
+#pragma unroll 1
     for (int j = 0; j < 80; ++j) {
         const BriDir& D = dirs[j];
-        long nbr = s;
+        if (D.neg) continue;   // the stored directions; -d is handled with d
+        long np = s, nm = s;
 #pragma unroll
-        for (int mu = 0; mu < 4; ++mu) nbr += (D.d[mu] > 0) ? fwd[mu] : (D.d[mu] < 0 ? bwd[mu] : 0);
-        cx<A> W[9];
-        load_link<T>(a.links, a.g.vol, D.rep, D.neg ? nbr : s, W);
+        for (int mu = 0; mu < 4; ++mu) {
+            np += (D.d[mu] > 0) ? fwd[mu] : (D.d[mu] < 0 ? bwd[mu] : 0);
+            nm += (D.d[mu] > 0) ? bwd[mu] : (D.d[mu] < 0 ? fwd[mu] : 0);
+        }
+        cx<A> Wp[9], Wm[9];
+        load_link<T>(a.links, a.g.vol, D.rep, s, Wp);    // W_d(x)
+        load_link<T>(a.links, a.g.vol, D.rep, nm, Wm);   // W_{-d}(x) = W_d(x - d)^+
         const BriDirA<A> m = bri_coeffs<A, DAG>(D);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int v = min(v0 + r, a.Nv - 1);   // partial group: recompute, store guarded
-            cx<A> p[12], chi[12];
-            load_spinor<T, 12>(a.in, a.g.vol, v, nbr, p);
-            bri_spin(m, p, chi);
+            cx<A> p[12], av[12], bv[12];
+            load_spinor<T, 12>(a.in, a.g.vol, v, np, p);
 #pragma unroll
             for (int sp = 0; sp < 4; ++sp) {
-                if constexpr (sizeof(A) == 4) {
-                    if (D.neg) mat_dag_vec_acc2(W, chi + 3 * sp, acc[r] + 3 * sp);
-                    else mat_vec_acc2(W, chi + 3 * sp, acc[r] + 3 * sp);
-                } else {
-                    if (D.neg) mat_dag_vec_acc(W, chi + 3 * sp, acc[r] + 3 * sp);
-                    else mat_vec_acc(W, chi + 3 * sp, acc[r] + 3 * sp);
-                }
+#pragma unroll
+                for (int i = 0; i < 3; ++i) av[3 * sp + i] = cx<A>{A(0), A(0)};
+                if constexpr (sizeof(A) == 4) mat_vec_acc2(Wp, p + 3 * sp, av + 3 * sp);
+                else mat_vec_acc(Wp, p + 3 * sp, av + 3 * sp);
             }
+            load_spinor<T, 12>(a.in, a.g.vol, v, nm, p);
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) bv[3 * sp + i] = cx<A>{A(0), A(0)};
+                if constexpr (sizeof(A) == 4) mat_dag_vec_acc2(Wm, p + 3 * sp, bv + 3 * sp);
+                else mat_dag_vec_acc(Wm, p + 3 * sp, bv + 3 * sp);
+            }
+            bri_pair_acc(m, av, bv, acc[r]);
         }
     }
 #pragma unroll
