@@ -152,12 +152,16 @@ def time_kernel(torch, fn, steps, warmup):
     return t0.elapsed_time(t1), [a.elapsed_time(b) for a, b in ev]
 
 
-def sweep_rate(dg, torch, w, steps, warmup):
-    """Time one sweep workload on the internal layout; returns a dict of rates."""
+def sweep_rate(dg, torch, w, steps, warmup, kernel=None):
+    """Time one sweep workload on the internal layout; returns a dict of rates.
+    kernel = (R, block, variant): that launch shape instead of the autotuner."""
     V, psi = gen_inputs(w)
     D = dg.Dirac(w["op"], w["L"], w["Nv"], w["mass"], w["prec"])
     D.set_links(torch.from_numpy(V).cuda())
-    D.autotune()
+    if kernel:
+        D.set_kernel_config(*kernel)
+    else:
+        D.autotune()
     x = D.pack(torch.from_numpy(psi).cuda())
     y = D.new_internal()
     total, per = time_kernel(torch, lambda: D.apply(x, out=y), steps, warmup)
@@ -242,30 +246,50 @@ def solve_times(dg, torch, L=(24, 24, 24, 48), Nv=12, m0=0.05, precs=("f32", "bf
     return out
 
 
-def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=("f32", "bf16", "f16")):
+def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=("f32", "bf16", "f16"),
+                        rank=0, ws=1, dist=None):
     """Wilson systems D(kappa_i) x_i = b_i on one gauge field, Nv_i ~ U{1..24},
     kappa_i ~ U[0.120, 0.124], through dirac_solve_batched with `slots` resident
     right-hand-side columns, each precision to a true FP64 residual of 1e-10:
     the batched form of the mixed-vs-FP32 solve time (fewer systems than the
-    48 of the full configuration, so that the benchmark stays within minutes)."""
+    48 of the full configuration, so that the benchmark stays within minutes).
+    With N ranks the systems are shared out (sharding.assign_systems, 4 * N
+    systems in all: weak scaling) and each rank solves its own; the time is
+    the slowest rank's."""
+    from paper_1808_05506_gb300 import sharding
+    nsys = nsys * ws
     rng = np.random.default_rng(7)
     nvs = [int(v) for v in rng.integers(1, 25, nsys)]
     kap = [float(v) for v in rng.uniform(0.120, 0.124, nsys)]
     V = synth.gauge_links(L, 3, "near_identity", 1005, eps=0.3)
-    bs = [torch.from_numpy(synth.spinor(L, nv, 4, 3, 2100 + i)).cuda() for i, nv in enumerate(nvs)]
+
+    def make_b(i):
+        return torch.from_numpy(synth.spinor(L, nvs[i], 4, 3, 2100 + i)).cuda()
+
     out = {}
     for prec in precs:
         D = dg.Dirac("wilson", L, slots, 0.122, prec)
         D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
         D.autotune()
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
-        xs, res, _, st, status = D.solve_batched(bs, kap, tol=1e-10)
+        local, xs, status, stats, tot = sharding.solve_batched_sharded(
+            D.solve_batched, nvs, kap, make_b, rank, ws,
+            gather=(lambda o: [o]) if dist is None else None, tol=1e-10)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        out[prec] = {"seconds": dt, "status": int(status), "max_rel_residual": float(res.max()),
-                     "outer": st["outer_iterations"], "inner": st["inner_iterations"], "sweeps": st["sweeps"],
-                     "fp64_sweeps": st["fp64_sweeps"], "kernel": list(D.kernel_config())}
+        if dist:
+            tt = torch.tensor([dt], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dt = float(tt.item())
+        out[prec] = {"seconds": dt, "status": int(status),
+                     "max_rel_residual": max(s["residual_max"] for s in stats),
+                     "outer_max": max(s["outer_iterations"] for s in stats),
+                     "all_converged": all(s["converged"] for s in stats), "kernel": list(D.kernel_config()),
+                     "rank0_totals": {k: tot.get(k) for k in ("outer_iterations", "inner_iterations", "sweeps",
+                                                                "fp64_sweeps")}}
         D.close()
         del xs
         torch.cuda.empty_cache()
@@ -275,7 +299,7 @@ def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=(
                 out[p]["speedup_vs_f32"] = out["f32"]["seconds"] / out[p]["seconds"]
     out["workload"] = "wilson_batched_solve_{}_{}sys_nv{}_{}slots".format("x".join(map(str, L)), nsys,
                                                                         "-".join(map(str, nvs)), slots)
-    del bs
+    out["sharding"] = f"{ws} rank(s), systems per rank by assign_systems"
     torch.cuda.empty_cache()
     return out
 
@@ -462,10 +486,16 @@ def main():
         extra["brillouin_24x24x24x48_nv12_f32"] = sweep_rate(dg, torch, bw, 20, 3)
         extra["brillouin_24x24x24x48_nv12_bf16"] = sweep_rate(dg, torch, dict(bw, prec="bf16"), 20, 3)
         extra["wilson_32x32x32x32_nv12_bf16"] = sweep_rate(dg, torch, dict(WORKLOAD, prec="bf16"), 200, 5)
+        # the paper's own lattice (non-power-of-two extents) and the FP64 sweeps
+        extra["wilson_34x34x34x68_nv12_f32"] = sweep_rate(dg, torch, dict(WORKLOAD, L=(34, 34, 34, 68)), 50, 3)
+        extra["wilson_32x32x32x32_nv12_f64"] = sweep_rate(dg, torch, dict(WORKLOAD, prec="f64"), 20, 3)
+        extra["staggered_32x32x32x32_nv12_f64"] = sweep_rate(dg, torch, dict(sw, prec="f64"), 20, 3)
+        extra["brillouin_24x24x24x48_nv12_f64"] = sweep_rate(dg, torch, dict(bw, prec="f64"), 3, 1,
+                                                             kernel=(2, 128, 0))
         line["extra"] = extra
     if not args.no_solve and not args.no_extra:
         line["solve"] = solve_times(dg, torch)
-        line["batched_solve"] = batched_solve_times(dg, torch)
+        line["batched_solve"] = batched_solve_times(dg, torch, rank=rank, ws=ws, dist=dist)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_rate(w, inputs=(V, psi))
     if rank == 0:
