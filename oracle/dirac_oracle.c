@@ -519,16 +519,125 @@ int oracle_brillouin_W(int Nc, const int* L, const double* V, const long* sites,
     return 0;
 }
 
+/* M[b][a] = coef sum_{v,s,s'} psi_v(y+d)[s'][b] S[s][s'] conj(g_v(y)[s][a]) of one term */
+static void term_M(const ctx_t* c, const term_t* t, const cplx* py, const cplx* gy, cplx* M)
+{
+    int Nc = c->Nc, Nv = c->Nv;
+    for (int b = 0; b < Nc; ++b)
+        for (int a = 0; a < Nc; ++a) {
+            cplx acc = 0;
+            for (int v = 0; v < Nv; ++v)
+                for (int s = 0; s < c->Ns; ++s)
+                    for (int sp = 0; sp < c->Ns; ++sp) {
+                        cplx Sv = (t->spin < 0) ? (s == sp ? 1.0 : 0.0) : G[t->spin][s][sp];
+                        if (Sv == 0) continue;
+                        acc += py[((size_t)v * c->Ns + sp) * Nc + b] * Sv * conj(gy[((size_t)v * c->Ns + s) * Nc + a]);
+                    }
+            M[b * Nc + a] = t->coef * acc;
+        }
+}
+
+/* Brillouin: the terms couple through W_dir(y) = (1/k!) sum over the k! hop
+ * orderings of the path products H_1 ... H_k (Tab. tab:off-axis), with
+ * H = V_mu(z) for a +mu hop and V_mu(z - mu)^+ for a -mu hop.  The gradient
+ * with respect to W_dir(y) is the sum of M^+ over the terms through W_dir(y);
+ * for one ordering, Re tr(G^+ P1 H P2) gives P1^+ G P2^+ for H and, for a
+ * -mu hop, its adjoint P2 G^+ P1 for V_mu(z - mu); each weighted 1/k!. */
+static void brillouin_force(const ctx_t* c, const cplx* P, const cplx* Gv, cplx* Fo)
+{
+    int Nc = c->Nc;
+    size_t n2 = (size_t)Nc * Nc, blk = (size_t)c->Nv * c->Ns * Nc;
+    term_t T[MAX_TERMS];
+    cplx* W81 = malloc(sizeof(cplx) * 81 * n2);
+    cplx* G81 = malloc(sizeof(cplx) * 81 * n2);
+    cplx M[MAX_NC * MAX_NC];
+    for (long y = 0; y < c->vol; ++y) {
+        W81_site(c, y, W81);
+        int nt = rows_brillouin(c, y, W81, T);
+        memset(G81, 0, sizeof(cplx) * 81 * n2);
+        for (int t = 0; t < nt; ++t) {
+            if (!T[t].C) continue;
+            term_M(c, &T[t], P + blk * shift(c, y, T[t].d), Gv + blk * y, M);
+            cplx* Gd = G81 + (size_t)dir_index(T[t].d) * n2;
+            for (int a = 0; a < Nc; ++a)
+                for (int b = 0; b < Nc; ++b) Gd[a * Nc + b] += conj(M[b * Nc + a]);
+        }
+        for (int dir = 0; dir < 81; ++dir) {
+            int d[4] = {dir % 3 - 1, (dir / 3) % 3 - 1, (dir / 9) % 3 - 1, (dir / 27) % 3 - 1};
+            int axis[4], sign[4], k = 0;
+            for (int mu = 0; mu < 4; ++mu)
+                if (d[mu] != 0) {
+                    axis[k] = mu;
+                    sign[k] = d[mu];
+                    ++k;
+                }
+            if (k == 0) continue;
+            const cplx* Gd = G81 + (size_t)dir * n2;
+            double fact = 1;
+            for (int i = 2; i <= k; ++i) fact *= i;
+            int total = 1;
+            for (int i = 0; i < k; ++i) total *= k;
+            for (int code = 0; code < total; ++code) {
+                int cc = code, used = 0, ok = 1, ord[4];
+                for (int i = 0; i < k; ++i) {
+                    ord[i] = cc % k;
+                    cc /= k;
+                    if (used & (1 << ord[i])) ok = 0;
+                    used |= 1 << ord[i];
+                }
+                if (!ok) continue;
+                cplx H[4][MAX_NC * MAX_NC];
+                long z[5];
+                z[0] = y;
+                for (int i = 0; i < k; ++i) hop_link(c, z[i], axis[ord[i]], sign[ord[i]], H[i], &z[i + 1]);
+                for (int i = 0; i < k; ++i) {
+                    cplx P1[MAX_NC * MAX_NC], P2[MAX_NC * MAX_NC], tmp[MAX_NC * MAX_NC], X[MAX_NC * MAX_NC];
+                    for (int e = 0; e < Nc * Nc; ++e) P1[e] = P2[e] = 0;
+                    for (int a = 0; a < Nc; ++a) P1[a * Nc + a] = P2[a * Nc + a] = 1;
+                    for (int j = 0; j < i; ++j) {
+                        mat_mul(Nc, P1, 0, H[j], 0, tmp);
+                        memcpy(P1, tmp, sizeof(cplx) * n2);
+                    }
+                    for (int j = i + 1; j < k; ++j) {
+                        mat_mul(Nc, P2, 0, H[j], 0, tmp);
+                        memcpy(P2, tmp, sizeof(cplx) * n2);
+                    }
+                    const int mu = axis[ord[i]];
+                    if (sign[ord[i]] > 0) {
+                        mat_mul(Nc, P1, 1, Gd, 0, tmp);        /* P1^+ G */
+                        mat_mul(Nc, tmp, 0, P2, 1, X);         /* P1^+ G P2^+ */
+                        cplx* Fl = Fo + ((size_t)z[i] * 4 + mu) * n2;
+                        for (int e = 0; e < Nc * Nc; ++e) Fl[e] += X[e] / fact;
+                    } else {
+                        mat_mul(Nc, P2, 0, Gd, 1, tmp);        /* P2 G^+ */
+                        mat_mul(Nc, tmp, 0, P1, 0, X);         /* P2 G^+ P1 */
+                        cplx* Fl = Fo + ((size_t)z[i + 1] * 4 + mu) * n2;   /* V_mu(z_i - mu) */
+                        for (int e = 0; e < Nc * Nc; ++e) Fl[e] += X[e] / fact;
+                    }
+                }
+            }
+        }
+    }
+    free(W81);
+    free(G81);
+}
+
 /* Link gradient of L = Re <g, D psi> = Re sum_y g(y)^+ (D psi)(y), PyTorch's
- * convention F = dL/dRe V + i dL/dIm V, for the operators whose terms couple
- * through single links (staggered, Wilson).  A term coef (S (x) C) with C = V
- * contributes M^+ and one with C = V^+ contributes M, where
- * M[b][a] = coef sum_{v,s,s'} psi_v(y+d)[s'][b] S[s][s'] conj(g_v(y)[s][a]).
+ * convention F = dL/dRe V + i dL/dIm V.  Staggered, Wilson: a term
+ * coef (S (x) C) with C = V contributes M^+ and one with C = V^+ contributes
+ * M, with M of term_M.  Brillouin: through the paths of W (brillouin_force).
  * F is [site][mu][a][b]. */
 int oracle_force(int op, int Nc, const int* L, int Nv, double mass, const double* V,
                  const double* psi, const double* g, double* F)
 {
-    if (op == OP_BRILLOUIN || Nc < 1 || Nc > MAX_NC) return 1;
+    if (Nc < 1 || Nc > MAX_NC) return 1;
+    if (op == OP_BRILLOUIN) {
+        ctx_t cb;
+        set_ctx(&cb, op, Nc, L, Nv, mass, V, NULL);
+        memset(F, 0, sizeof(cplx) * cb.vol * 4 * Nc * Nc);
+        brillouin_force(&cb, (const cplx*)psi, (const cplx*)g, (cplx*)F);
+        return 0;
+    }
     ctx_t c;
     set_ctx(&c, op, Nc, L, Nv, mass, V, NULL);
     const cplx* P = (const cplx*)psi;

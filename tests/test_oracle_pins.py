@@ -395,6 +395,85 @@ def test_force_finite_differences(op):
         assert abs(fd - an) < 1e-8 * max(1.0, abs(an))
 
 
+@pytest.mark.parametrize("L", [(2, 3, 2, 3), (3, 3, 3, 3)])
+def test_brillouin_force_finite_differences(L):
+    """The Brillouin link gradient through the path products of W (Tab.
+    tab:off-axis): L is a polynomial of degree 4 in V, so the central
+    difference with eps = 1e-5 is exact to ~1e-10; extent 2 makes a path use
+    the same link twice."""
+    V = synth.gauge_links(L, 3, "haar", 140)
+    psi = _psi(L, "brillouin", 2, 141)
+    g = _psi(L, "brillouin", 2, 142)
+    m = 0.07
+    F = oracle.force("brillouin", V, psi, g, m)
+    rng = synth.rng(143, synth.STREAM_MISC)
+    eps = 1e-5
+    for _ in range(10):
+        idx = tuple(int(rng.integers(0, n)) for n in V.shape[:5])
+        dV = synth.complex_gaussian((3, 3), int(rng.integers(1 << 30)))
+        Vp = V.copy()
+        Vm = V.copy()
+        Vp[idx] += eps * dV
+        Vm[idx] -= eps * dV
+        fd = (_loss("brillouin", Vp, psi, g, m) - _loss("brillouin", Vm, psi, g, m)) / (2 * eps)
+        an = np.vdot(F[idx], dV).real
+        assert abs(fd - an) < 1e-7 * max(1.0, abs(an)), (idx, fd, an)
+
+
+def test_brillouin_force_unit_links_closed_form():
+    """At V = 1 every path product is 1, so the gradient of W_d(y),
+    G_d(y) = sum_{v,s} g_v(y)_s (M_d psi_v(y+d))_s^+ with the paper's spin
+    matrix M_d = rho_k (d . gamma) - lambda_k / 2 (Sec. 5, coefficients after
+    def_lap), reaches each link of each of the k! orderings with weight 1/k!.
+    A hop along mu that follows the subset S of the other hops of d sits at
+    y + sum(S) and occurs in |S|! (k-1-|S|)! orderings; a -mu hop acts through
+    V_mu at one site further back and receives the adjoint."""
+    from itertools import combinations, product
+    from math import factorial
+    L = (2, 2, 3, 2)
+    V = synth.gauge_links(L, 3, "unit", 0)
+    psi = _psi(L, "brillouin", 1, 144)
+    g = _psi(L, "brillouin", 1, 145)
+    F = oracle.force("brillouin", V, psi, g, 0.0)
+    rho = [0.0] + [r / 432.0 for r in GOLD["rho"]["values_times_432"]]
+    lam = [x / 64.0 for x in GOLD["lambda"]["values_times_64"]]
+    Nx, Ny, Nz, Nt = L
+    vol = Nx * Ny * Nz * Nt
+    G = dense.gammas()
+    ps = psi.reshape(vol, 1, 4, 3)
+    gs = g.reshape(vol, 1, 4, 3)
+
+    def site(x):
+        return x[0] + Nx * (x[1] + Ny * (x[2] + Nz * x[3]))
+
+    want = np.zeros((vol, 4, 3, 3), dtype=complex)
+    for y in range(vol):
+        xy = [y % Nx, (y // Nx) % Ny, (y // (Nx * Ny)) % Nz, y // (Nx * Ny * Nz)]
+        for d in product((-1, 0, 1), repeat=4):
+            k = sum(abs(c) for c in d)
+            if k == 0:
+                continue
+            M = rho[k] * sum(d[m] * G[m] for m in range(4)) - 0.5 * lam[k] * np.eye(4)
+            chi = np.einsum("st,vtb->vsb", M, ps[site([(xy[m] + d[m]) % L[m] for m in range(4)])])
+            Gd = np.einsum("vsa,vsb->ab", gs[y], chi.conj())
+            for mu in range(4):
+                if d[mu] == 0:
+                    continue
+                others = [m for m in range(4) if d[m] != 0 and m != mu]
+                for r in range(len(others) + 1):
+                    for sub in combinations(others, r):
+                        w = factorial(r) * factorial(k - 1 - r) / factorial(k)
+                        z = list(xy)
+                        for m in sub:
+                            z[m] = (z[m] + d[m]) % L[m]
+                        if d[mu] > 0:
+                            want[site(z), mu] += w * Gd
+                        else:
+                            z[mu] = (z[mu] - 1) % L[mu]
+                            want[site(z), mu] += w * Gd.conj().T
+    assert np.abs(F.reshape(vol, 4, 3, 3) - want).max() < 1e-12
+
+
 def test_force_closed_forms():
     """Closed forms of the link gradient, derived from Sec. 3 / def_wils:
     staggered F_mu(x) = 1/2 eta_mu(x) sum_v [g_v(x) psi_v(x+mu)^+ - psi_v(x) g_v(x+mu)^+]
