@@ -175,10 +175,16 @@ DIRAC_API dirac_status dirac_apply_dagger(dirac_handle* h, void* out, const void
  * Staggered (Sec. 3):  F_mu(x) = 1/2 eta_mu(x) sum_v [g_v(x) psi_v(x+mu)^+ - psi_v(x) g_v(x+mu)^+]
  * Wilson (def_wils):   F_mu(x) = -1/2 sum_v,s [(1-gamma_mu) g_v(x)]_s psi_v(x+mu)_s^+
  *                                -1/2 sum_v,s psi_v(x)_s [(1+gamma_mu) g_v(x+mu)]_s^+
+ * Brillouin (Sec. 5, Tab. tab:off-axis): through the transporters W, which
+ *   are rebuilt from V in FP64 here (not kept from the forward pass):
+ *   G_dir(y) = sum_v,s g_v(y)_s (M_dir psi_v(y+dir))_s^+ is passed down the
+ *   recursion W_dir(x) = (1/k) sum_a H_a(x) W_{dir-a}(x+a) to the links.
+ *   Holds two FP64 scratch fields of 81 * 9 complex per site (11.7 KB per
+ *   site each) during the call.
  *   F        device, canonical link layout [s][mu][a][b], complex double for
  *            F64 handles and complex float otherwise; written once per link
  *   psi, g   device spinor fields in `layout`
- * UNSUPPORTED for Brillouin (its links W are composite).  Asynchronous. */
+ * Asynchronous. */
 DIRAC_API dirac_status dirac_force(dirac_handle* h, void* F, const void* psi, const void* g,
                                    dirac_layout layout);
 

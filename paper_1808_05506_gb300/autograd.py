@@ -1,8 +1,9 @@
-"""Differentiable out = D(V) psi for the staggered and Wilson operators.
+"""Differentiable out = D(V) psi for the staggered, Wilson and Brillouin operators.
 
 forward:  out = D psi (dirac_apply)
 backward: dL/dpsi = D^+ g (dirac_apply_dagger) and dL/dV = the link force
-          (dirac_force), both hand-written kernels of the library, with
+          (dirac_force; for Brillouin through the transporters W, which the
+          backward pass rebuilds from V), both hand-written kernels of the library, with
           PyTorch's convention for real losses of complex tensors
           (grad = dL/dRe + i dL/dIm), so that for L = Re <g, D psi> the
           gradients are exactly D^+ g and F.
@@ -39,7 +40,5 @@ class DiracApply(torch.autograd.Function):
 
 
 def dirac_apply(D: Dirac, psi: torch.Tensor, V: torch.Tensor) -> torch.Tensor:
-    """out = D(V) psi, differentiable in psi and V (staggered and Wilson handles)."""
-    if D.op == "brillouin" and V.requires_grad:
-        raise NotImplementedError("the Brillouin link gradient is not built")
+    """out = D(V) psi, differentiable in psi and V."""
     return DiracApply.apply(psi, V, D)

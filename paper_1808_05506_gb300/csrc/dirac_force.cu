@@ -12,7 +12,8 @@
 //   staggered (Sec. 3; eta_mu(x + mu) = eta_mu(x)):
 //     F_mu(x) = 1/2 eta_mu(x) sum_v [g_v(x) psi_v(x+mu)^+ - psi_v(x) g_v(x+mu)^+]
 // One thread owns one link (x, mu), gathers both hops that touch it and
-// writes it once (no atomics).
+// writes it once (no atomics).  The Brillouin gradient, through the composite
+// transporters W, is in dirac_force_brillouin.cu.
 #include "dirac_handle.h"
 #include "dirac_kernels.cuh"
 
@@ -131,8 +132,6 @@ extern "C" DIRAC_API dirac_status dirac_force(dirac_handle* h, void* F, const vo
     if (!h) return DIRAC_ERR_INVALID_ARG;
     if (!F || !psi || !g || F == psi || F == g)
         return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_force: NULL or aliased pointers");
-    if (h->op == OP_BRILLOUIN)
-        return h->fail(DIRAC_ERR_UNSUPPORTED, "dirac_force: the Brillouin link gradient is not built");
     if (layout != DIRAC_CANONICAL && layout != DIRAC_INTERNAL)
         return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_force: unknown layout");
     if (!dirac_check_device_ptr(F) || !dirac_check_device_ptr(psi) || !dirac_check_device_ptr(g))
@@ -145,6 +144,21 @@ extern "C" DIRAC_API dirac_status dirac_force(dirac_handle* h, void* F, const vo
         if ((st = dirac_pack(h, h->ws_out, g))) return st;
         pi = h->ws_in;
         gi = h->ws_out;
+    }
+    if (h->op == OP_BRILLOUIN) {
+        // the transporters are rebuilt from V in FP64 (not kept from the forward pass)
+        void *w81 = nullptr, *g81 = nullptr;
+        const size_t fb = (size_t)h->g.vol * 81 * 9 * 16;
+        if ((st = h->alloc(&w81, fb, "Brillouin force scratch"))) return st;
+        if ((st = h->alloc(&g81, fb, "Brillouin force scratch"))) {
+            h->release(w81);
+            return st;
+        }
+        st = h->cuda(launch_force_brillouin(h->prec, h->g, h->Nv, pi, gi, h->links64, w81, g81, F, h->stream),
+                     "Brillouin force kernels");
+        h->release_after_sync(w81);
+        h->release_after_sync(g81);
+        return st;
     }
     return h->cuda(launch_force(h->op, h->prec, h->g, h->Nv, pi, gi, F, h->stream), "force kernel launch");
 }

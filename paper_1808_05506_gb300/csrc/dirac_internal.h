@@ -95,9 +95,13 @@ cudaError_t launch_convert_links(int prec, const Geom& g, int nmat, const void* 
                                  cudaStream_t st);
 // Tab. tab:off-axis: FP64 links V64 [4][9][s] -> FP64 W64 [40][9][s]; tmp81 holds
 // 81 * 9 * vol complex doubles.
+cudaError_t launch_build_W81(const Geom& g, const void* V64, void* tmp81, cudaStream_t st);
 cudaError_t launch_build_W(const Geom& g, const void* V64, void* tmp81, void* W64, cudaStream_t st);
 
 // link gradient of Re <g, D psi> (staggered, Wilson); F canonical link layout
+// Brillouin link gradient: W81, G81 are FP64 scratch fields of 81 * 9 * vol complex
+cudaError_t launch_force_brillouin(int prec, const Geom& g, int Nv, const void* psi, const void* gv,
+                                   const void* V64, void* W81, void* G81, void* F, cudaStream_t st);
 cudaError_t launch_force(int op, int prec, const Geom& g, int Nv, const void* psi, const void* gv, void* F,
                          cudaStream_t st);
 

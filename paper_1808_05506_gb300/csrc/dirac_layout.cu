@@ -317,7 +317,8 @@ __global__ void k_wbuild_store(Geom g, RepList R, const double2* __restrict__ tm
     for (int e = 0; e < 9; ++e) W64[((size_t)r * 9 + e) * g.vol + s] = tmp[((size_t)R.code[r] * 9 + e) * g.vol + s];
 }
 
-cudaError_t launch_build_W(const Geom& g, const void* V64, void* tmp81, void* W64, cudaStream_t st)
+// all 80 directions of W (FP64, [dir81][9][site]; the centre code 40 is not written)
+cudaError_t launch_build_W81(const Geom& g, const void* V64, void* tmp81, cudaStream_t st)
 {
     double2* tmp = (double2*)tmp81;
     unsigned nb = (unsigned)((g.vol + 255) / 256);
@@ -338,6 +339,14 @@ cudaError_t launch_build_W(const Geom& g, const void* V64, void* tmp81, void* W6
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
+}
+
+cudaError_t launch_build_W(const Geom& g, const void* V64, void* tmp81, void* W64, cudaStream_t st)
+{
+    double2* tmp = (double2*)tmp81;
+    cudaError_t e = launch_build_W81(g, V64, tmp81, st);
+    if (e != cudaSuccess) return e;
     BriDir dirs[80];
     int reps[40];
     brillouin_tables(dirs, reps);
