@@ -139,6 +139,10 @@ def _ptr(t) -> ctypes.c_void_p:
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _is_device(t) -> bool:
+    return bool(t.is_cuda)
+
+
 class Dirac:
     """One operator on one lattice, bound to a handle of the C library.
 
@@ -196,6 +200,43 @@ class Dirac:
         torch = _torch()
         return torch.empty(self.canonical_shape, dtype=self.canon_dtype, device=self.device)
 
+    # -- argument checks: the C ABI takes bare pointers and cannot see a
+    # tensor's size or type, so every tensor is checked here before its
+    # pointer is passed (a wrong dtype or size would make a kernel read or
+    # write past the end of the buffer)
+    def _n_canonical(self) -> int:
+        n = 1
+        for d in self.canonical_shape:
+            n *= d
+        return n
+
+    def _canon_in(self, t, what="field", device=True):
+        """A canonical input: converted to this handle's complex dtype."""
+        torch = _torch()
+        if not isinstance(t, torch.Tensor) or not t.is_complex():
+            raise TypeError(f"{what} must be a complex tensor")
+        if device and not _is_device(t):
+            raise ValueError(f"{what} must be a CUDA tensor")
+        if t.numel() != self._n_canonical():
+            raise ValueError(f"{what} has {t.numel()} entries, the canonical field {self.canonical_shape} "
+                             f"has {self._n_canonical()}")
+        return t.to(self.canon_dtype).contiguous()
+
+    def _canon_out(self, t, what="out"):
+        if t.dtype != self.canon_dtype or not _is_device(t) or not t.is_contiguous() \
+                or t.numel() != self._n_canonical():
+            raise ValueError(f"{what} must be a contiguous CUDA {self.canon_dtype} tensor with "
+                             f"{self._n_canonical()} entries")
+        return t
+
+    def _internal(self, t, what="internal field"):
+        torch = _torch()
+        if t.dtype != torch.uint8 or not _is_device(t) or not t.is_contiguous() \
+                or t.numel() < self.field_bytes(INTERNAL):
+            raise ValueError(f"{what} must be a contiguous CUDA uint8 buffer of at least "
+                             f"{self.field_bytes(INTERNAL)} bytes (new_internal)")
+        return t
+
     def _sync_stream(self):
         check(lib().dirac_set_stream(self.h, _stream_ptr(self._stream)), self.h, "dirac_set_stream")
 
@@ -203,10 +244,14 @@ class Dirac:
     def set_links(self, V):
         """V: canonical links (Nt, Nz, Ny, Nx, 4, 3, 3), complex128/complex64, host or device."""
         torch = _torch()
-        V = V.contiguous()
-        prec = F64 if V.dtype == torch.complex128 else F32
         if V.dtype not in (torch.complex128, torch.complex64):
             raise TypeError("links must be complex128 or complex64")
+        Nx, Ny, Nz, Nt = self.L
+        if V.numel() != Nx * Ny * Nz * Nt * 4 * self.Nc * self.Nc:
+            raise ValueError(f"links must have {Nx * Ny * Nz * Nt * 4 * self.Nc * self.Nc} entries "
+                             "(Nt, Nz, Ny, Nx, 4, 3, 3)")
+        V = V.contiguous()
+        prec = F64 if V.dtype == torch.complex128 else F32
         self._sync_stream()
         check(lib().dirac_set_links(self.h, _ptr(V), prec, 1 if V.is_cuda else 0), self.h, "dirac_set_links")
 
@@ -215,13 +260,15 @@ class Dirac:
         self.mass = float(mass)
 
     def pack(self, canonical, out=None):
-        out = self.new_internal() if out is None else out
+        canonical = self._canon_in(canonical, "canonical")
+        out = self.new_internal() if out is None else self._internal(out, "out")
         self._sync_stream()
-        check(lib().dirac_pack(self.h, _ptr(out), _ptr(canonical.contiguous())), self.h, "dirac_pack")
+        check(lib().dirac_pack(self.h, _ptr(out), _ptr(canonical)), self.h, "dirac_pack")
         return out
 
     def unpack(self, internal, out=None):
-        out = self.new_canonical() if out is None else out
+        internal = self._internal(internal)
+        out = self.new_canonical() if out is None else self._canon_out(out)
         self._sync_stream()
         check(lib().dirac_unpack(self.h, _ptr(out), _ptr(internal)), self.h, "dirac_unpack")
         return out
@@ -230,11 +277,15 @@ class Dirac:
         """out = D x (or D^+ x).  x canonical (complex tensor) or internal (uint8 buffer)."""
         if layout is None:
             layout = INTERNAL if x.dtype == _torch().uint8 else CANONICAL
-        if out is None:
-            out = self.new_internal() if layout == INTERNAL else self.new_canonical()
+        if layout == INTERNAL:
+            x = self._internal(x, "x")
+            out = self.new_internal() if out is None else self._internal(out, "out")
+        else:
+            x = self._canon_in(x, "x")
+            out = self.new_canonical() if out is None else self._canon_out(out)
         self._sync_stream()
         fn = lib().dirac_apply_dagger if dagger else lib().dirac_apply
-        check(fn(self.h, _ptr(out), _ptr(x.contiguous() if layout == CANONICAL else x), layout),
+        check(fn(self.h, _ptr(out), _ptr(x), layout),
               self.h, "dirac_apply_dagger" if dagger else "dirac_apply")
         return out
 
@@ -267,8 +318,8 @@ class Dirac:
         torch = _torch()
         if inner_tol is None:
             inner_tol = {"f64": 1e-10, "f32": 1e-5, "f16": 2e-3, "bf16": 1e-2}[self.prec]
-        b = b.to(torch.complex128).contiguous()
-        x = torch.zeros_like(b) if x0 is None else x0.to(torch.complex128).contiguous().clone()
+        b = self._canon_in(b, "b").to(torch.complex128)
+        x = torch.zeros_like(b) if x0 is None else self._canon_in(x0, "x0").to(torch.complex128).clone()
         res = np.zeros(self.Nv, dtype=np.float64)
         st = SolveStats()
         self._sync_stream()
@@ -289,7 +340,15 @@ class Dirac:
         if inner_tol is None:
             inner_tol = {"f64": 1e-10, "f32": 1e-5, "f16": 2e-3, "bf16": 1e-2}[self.prec]
         nsys = len(bs)
+        Nx, Ny, Nz, Nt = self.L
+        for i, b in enumerate(bs):
+            if not b.is_complex() or not _is_device(b) or b.dim() != 7 or tuple(b.shape[:4]) != (Nt, Nz, Ny, Nx) \
+                    or tuple(b.shape[5:]) != self.spin_shape[1:] or b.shape[4] < 1:
+                raise ValueError(f"b[{i}] must be a complex CUDA tensor (Nt, Nz, Ny, Nx, Nv_i) + "
+                                 f"{self.spin_shape[1:]}")
         bs = [b.to(torch.complex128).contiguous() for b in bs]
+        if x0s is not None and [tuple(x.shape) for x in x0s] != [tuple(b.shape) for b in bs]:
+            raise ValueError("x0s must have the shapes of bs")
         xs = [torch.zeros_like(b) for b in bs] if x0s is None else \
             [x.to(torch.complex128).contiguous().clone() for x in x0s]
         nv = (ctypes.c_int * nsys)(*[int(b.shape[4]) for b in bs])
@@ -313,11 +372,15 @@ class Dirac:
         """Link gradient of Re <g, D psi>: canonical links shape, complex128 (f64) / complex64."""
         torch = _torch()
         Nx, Ny, Nz, Nt = self.L
+        psi = self._canon_in(psi, "psi")
+        g = self._canon_in(g, "g")
+        nl = Nx * Ny * Nz * Nt * 4 * self.Nc * self.Nc
         if out is None:
             out = torch.empty((Nt, Nz, Ny, Nx, 4, 3, 3), dtype=self.canon_dtype, device=self.device)
+        elif out.dtype != self.canon_dtype or not _is_device(out) or not out.is_contiguous() or out.numel() != nl:
+            raise ValueError(f"out must be a contiguous CUDA {self.canon_dtype} tensor with {nl} entries")
         self._sync_stream()
-        check(lib().dirac_force(self.h, _ptr(out), _ptr(psi.contiguous()), _ptr(g.contiguous()), CANONICAL),
-              self.h, "dirac_force")
+        check(lib().dirac_force(self.h, _ptr(out), _ptr(psi), _ptr(g), CANONICAL), self.h, "dirac_force")
         return out
 
     def set_kernel_config(self, R: int, block: int, variant: int = 0):

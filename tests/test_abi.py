@@ -127,6 +127,7 @@ def test_binding_calls_match_the_c_signatures(dg, monkeypatch):
             return FakeFn(name)
 
     monkeypatch.setattr(dg, "_lib", FakeLib())
+    monkeypatch.setattr(dg, "_is_device", lambda t: True)   # CPU tensors stand in for device ones
     monkeypatch.setattr(dg, "_stream_ptr", lambda stream=None: ctypes.c_void_p(0))
     monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
     D = dg.Dirac.__new__(dg.Dirac)
@@ -142,6 +143,7 @@ def test_binding_calls_match_the_c_signatures(dg, monkeypatch):
     D.field_bytes()
     D.pack(x, out=torch.zeros(8, dtype=torch.uint8))
     D.unpack(torch.zeros(8, dtype=torch.uint8), out=x.clone())
+    D.apply(torch.zeros(8, dtype=torch.uint8), out=torch.zeros(8, dtype=torch.uint8))
     D.apply(x, out=x.clone())
     D.apply_dagger(x, out=x.clone())
     D.apply_host(x, out=x.clone(), dagger=True, sync=False)
@@ -178,3 +180,48 @@ def test_config_rule(dg):
     assert not dg.config_supported("wilson", "f64", 1, 64, 5, (32, 32, 32, 32))
     assert not dg.config_supported("wilson", "f32", 1, 256, 5, (32, 32, 32, 32))
     assert not dg.config_supported("staggered", "f32", 1, 64, 5, (32, 32, 32, 32))
+
+
+def test_binding_rejects_mismatched_tensors(dg, monkeypatch):
+    """The C ABI takes bare pointers, so the binding checks every tensor's type
+    and size before passing it (a complex64 field handed to an FP64 handle
+    would be read as twice its size); no C entry point is reached."""
+    import torch
+
+    class NoLib:
+        def __getattr__(self, name):
+            if name == "dirac_field_bytes":
+                def fb(h, layout, out):
+                    out._obj.value = 4096
+                    return dg.OK
+                return fb
+            raise AssertionError(f"{name} must not be called")
+
+    monkeypatch.setattr(dg, "_lib", NoLib())
+    monkeypatch.setattr(dg, "_is_device", lambda t: True)
+    D = dg.Dirac.__new__(dg.Dirac)
+    D.op, D.L, D.Nv, D.mass, D.prec, D.Nc = "wilson", (4, 4, 4, 4), 2, 0.12, "f64", 3
+    D.device = torch.device("cpu")
+    D._stream = None
+    D.h = ctypes.c_void_p(1)
+    D.canon_dtype = torch.complex128
+    good = torch.zeros(D.canonical_shape, dtype=torch.complex128)
+    with pytest.raises(ValueError):
+        D.pack(torch.zeros(10, dtype=torch.complex64))                      # wrong size
+    with pytest.raises(TypeError):
+        D.pack(torch.zeros(D.canonical_shape, dtype=torch.float64))         # not complex
+    with pytest.raises(ValueError):
+        D.unpack(torch.zeros(100, dtype=torch.uint8))                       # internal buffer too small
+    with pytest.raises(ValueError):
+        D.unpack(torch.zeros(4096, dtype=torch.uint8), out=good.to(torch.complex64))   # out of the wrong type
+    with pytest.raises(ValueError):
+        D.apply(good, out=torch.zeros(5, dtype=torch.complex128))
+    with pytest.raises(ValueError):
+        D.force(good, good[..., :1, :, :])
+    with pytest.raises(ValueError):
+        D.set_links(torch.zeros((4, 4, 4, 4, 4, 3), dtype=torch.complex128))
+    with pytest.raises(ValueError):
+        D.solve_batched([torch.zeros((4, 4, 4, 4, 2, 4), dtype=torch.complex128)], [0.12])
+    monkeypatch.setattr(dg, "_is_device", lambda t: False)
+    with pytest.raises(ValueError):
+        D.pack(good)                                                        # host tensor
