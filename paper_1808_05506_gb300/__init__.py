@@ -210,8 +210,8 @@ class Dirac:
             n *= d
         return n
 
-    def _canon_in(self, t, what="field", device=True):
-        """A canonical input: converted to this handle's complex dtype."""
+    def _canon_in(self, t, what="field", device=True, dtype=None):
+        """A canonical input: converted to `dtype` (default: this handle's complex dtype)."""
         torch = _torch()
         if not isinstance(t, torch.Tensor) or not t.is_complex():
             raise TypeError(f"{what} must be a complex tensor")
@@ -220,7 +220,7 @@ class Dirac:
         if t.numel() != self._n_canonical():
             raise ValueError(f"{what} has {t.numel()} entries, the canonical field {self.canonical_shape} "
                              f"has {self._n_canonical()}")
-        return t.to(self.canon_dtype).contiguous()
+        return t.to(self.canon_dtype if dtype is None else dtype).contiguous()
 
     def _canon_out(self, t, what="out"):
         if t.dtype != self.canon_dtype or not _is_device(t) or not t.is_contiguous() \
@@ -318,8 +318,8 @@ class Dirac:
         torch = _torch()
         if inner_tol is None:
             inner_tol = {"f64": 1e-10, "f32": 1e-5, "f16": 2e-3, "bf16": 1e-2}[self.prec]
-        b = self._canon_in(b, "b").to(torch.complex128)
-        x = torch.zeros_like(b) if x0 is None else self._canon_in(x0, "x0").to(torch.complex128).clone()
+        b = self._canon_in(b, "b", dtype=torch.complex128)
+        x = torch.zeros_like(b) if x0 is None else self._canon_in(x0, "x0", dtype=torch.complex128).clone()
         res = np.zeros(self.Nv, dtype=np.float64)
         st = SolveStats()
         self._sync_stream()
@@ -342,7 +342,8 @@ class Dirac:
         nsys = len(bs)
         Nx, Ny, Nz, Nt = self.L
         for i, b in enumerate(bs):
-            if not b.is_complex() or not _is_device(b) or b.dim() != 7 or tuple(b.shape[:4]) != (Nt, Nz, Ny, Nx) \
+            if not b.is_complex() or not _is_device(b) or b.dim() != 4 + len(self.spin_shape) \
+                    or tuple(b.shape[:4]) != (Nt, Nz, Ny, Nx) \
                     or tuple(b.shape[5:]) != self.spin_shape[1:] or b.shape[4] < 1:
                 raise ValueError(f"b[{i}] must be a complex CUDA tensor (Nt, Nz, Ny, Nx, Nv_i) + "
                                  f"{self.spin_shape[1:]}")

@@ -225,3 +225,29 @@ def test_binding_rejects_mismatched_tensors(dg, monkeypatch):
     monkeypatch.setattr(dg, "_is_device", lambda t: False)
     with pytest.raises(ValueError):
         D.pack(good)                                                        # host tensor
+
+
+def test_binding_accepts_staggered_solve_shapes(dg, monkeypatch):
+    """Staggered right-hand sides have no spin index: (Nt, Nz, Ny, Nx, Nv_i, 3)."""
+    import torch
+    seen = []
+
+    class RecLib:
+        def __getattr__(self, name):
+            def f(*a):
+                seen.append(name)
+                return dg.OK
+            return f
+
+    monkeypatch.setattr(dg, "_lib", RecLib())
+    monkeypatch.setattr(dg, "_is_device", lambda t: True)
+    D = dg.Dirac.__new__(dg.Dirac)
+    D.op, D.L, D.Nv, D.mass, D.prec, D.Nc = "staggered", (4, 4, 4, 4), 4, 0.1, "f32", 3
+    D.device = torch.device("cpu")
+    D._stream = None
+    D.h = ctypes.c_void_p(1)
+    D.canon_dtype = torch.complex64
+    D.solve_batched([torch.zeros((4, 4, 4, 4, 3, 3), dtype=torch.complex128)], [0.1])
+    assert "dirac_solve_batched" in seen
+    with pytest.raises(ValueError):
+        D.solve_batched([torch.zeros((4, 4, 4, 4, 3, 4, 3), dtype=torch.complex128)], [0.1])

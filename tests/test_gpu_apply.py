@@ -341,8 +341,10 @@ def test_error_paths(dg):
     with pytest.raises(dg.DiracError):               # aliasing
         D.apply(x, out=x)
     xh = torch.zeros_like(x, device="cpu")
-    with pytest.raises(dg.DiracError):               # host pointer
+    with pytest.raises(ValueError):                  # host tensor: stopped by the binding
         D.apply(xh, out=torch.zeros_like(xh))
+    # the C entry point rejects host pointers by itself
+    assert dg.dirac_apply(D.h, dg._ptr(torch.zeros_like(xh)), dg._ptr(xh), dg.CANONICAL) == dg.ERR_INVALID_ARG
     with pytest.raises(dg.DiracError) as e:
         D.set_kernel_config(5, 128)
     assert e.value.status == dg.ERR_UNSUPPORTED
