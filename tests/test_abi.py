@@ -241,6 +241,7 @@ def test_binding_accepts_staggered_solve_shapes(dg, monkeypatch):
 
     monkeypatch.setattr(dg, "_lib", RecLib())
     monkeypatch.setattr(dg, "_is_device", lambda t: True)
+    monkeypatch.setattr(dg, "_stream_ptr", lambda stream=None: ctypes.c_void_p(0))
     D = dg.Dirac.__new__(dg.Dirac)
     D.op, D.L, D.Nv, D.mass, D.prec, D.Nc = "staggered", (4, 4, 4, 4), 4, 0.1, "f32", 3
     D.device = torch.device("cpu")
