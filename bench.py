@@ -263,8 +263,12 @@ def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=(
     kap = [float(v) for v in rng.uniform(0.120, 0.124, nsys)]
     V = synth.gauge_links(L, 3, "near_identity", 1005, eps=0.3)
 
+    # this rank's right-hand sides, generated before any timing
+    local_b = {i: torch.from_numpy(synth.spinor(L, nvs[i], 4, 3, 2100 + i)).cuda()
+               for i in sharding.assign_systems(nvs, ws)[rank]}
+
     def make_b(i):
-        return torch.from_numpy(synth.spinor(L, nvs[i], 4, 3, 2100 + i)).cuda()
+        return local_b[i]
 
     out = {}
     for prec in precs:
@@ -300,6 +304,7 @@ def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=(
     out["workload"] = "wilson_batched_solve_{}_{}sys_nv{}_{}slots".format("x".join(map(str, L)), nsys,
                                                                         "-".join(map(str, nvs)), slots)
     out["sharding"] = f"{ws} rank(s), systems per rank by assign_systems"
+    del local_b
     torch.cuda.empty_cache()
     return out
 
