@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(256) k_wilson_pipe(ApplyArgs a, int ngroups)
 
 // V_GROUPS: blockDim = (sites, groups); block b covers a run of sites and a
 // chunk of gy right-hand-side groups
-template <typename T, int R, bool DAG>
+template <typename T, int R, bool DAG, bool FAST>
 __global__ void __launch_bounds__(192, 2) k_wilson_groups(ApplyArgs a, int ngroups, int gy)
 {
     const int nchunks = (ngroups + gy - 1) / gy;
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(192, 2) k_wilson_groups(ApplyArgs a, int ngrou
     const int group = (int)(b % nchunks) * gy + threadIdx.y;
     const long p = (b / nchunks) * blockDim.x + threadIdx.x;
     if (p >= a.nsites || group >= ngroups) return;
-    wilson_site<T, R, DAG>(a, slab_site(a, p), group);
+    wilson_site<T, R, DAG, FAST>(a, slab_site(a, p), group);
 }
 
 template <typename T, int R>
@@ -219,8 +219,14 @@ cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
     if (c.variant == V_GROUPS) {
         const int gy = groups_per_block(block, ngroups);
         const long nb = ((a.nsites + block - 1) / block) * (long)((ngroups + gy - 1) / gy);
-        if (dag) k_wilson_groups<T, R, true><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
-        else k_wilson_groups<T, R, false><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+        // whole groups of R right-hand sides and one diagonal: the specialised body
+        if (a.Nv % R == 0 && a.diag_v == nullptr) {
+            if (dag) k_wilson_groups<T, R, true, true><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+            else k_wilson_groups<T, R, false, true><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+        } else {
+            if (dag) k_wilson_groups<T, R, true, false><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+            else k_wilson_groups<T, R, false, false><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+        }
         return cudaGetLastError();
     }
     if constexpr (R <= 2) {

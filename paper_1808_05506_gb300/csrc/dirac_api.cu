@@ -113,6 +113,8 @@ ApplyArgs dirac_handle::args(void* out, const void* in, int nv, double diag_valu
     a.links = links;
     a.diag = diag_value;
     a.diag_v = nullptr;
+    a.diagf = (float)diag_value;
+    a.diag_vf = nullptr;
     a.err = dev_err;
     a.tc = 0;
     a.t0 = 0;
@@ -123,11 +125,12 @@ ApplyArgs dirac_handle::args(void* out, const void* in, int nv, double diag_valu
 
 dirac_status dirac_handle::run_apply(bool dagger, void* out, const void* in, int nv,
                                      double diag_value, const void* link_ptr, int p, LaunchCfg c,
-                                     const double* diag_v, int t0, int nt)
+                                     const double* diag_v, int t0, int nt, const float* diag_vf)
 {
     ApplyArgs a = args(out, in, nv, diag_value);
     a.links = link_ptr;
     a.diag_v = diag_v;
+    a.diag_vf = diag_vf;
     a.err = dev_err;
     if (nt > 0) {   // the slab of nt t-slices from t0 (variants 0, 1, 2 and 5)
         a.t0 = t0;

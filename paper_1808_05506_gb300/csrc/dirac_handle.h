@@ -53,7 +53,7 @@ struct dirac_handle {
     dirac::ApplyArgs args(void* out, const void* in, int nv, double diag_value) const;
     dirac_status run_apply(bool dagger, void* out, const void* in, int nv, double diag_value,
                            const void* link_ptr, int p, dirac::LaunchCfg c, const double* diag_v = nullptr,
-                           int t0 = 0, int nt = 0);
+                           int t0 = 0, int nt = 0, const float* diag_vf = nullptr);
     void free_solver_workspace();
     void free_host_apply();
 };

@@ -35,6 +35,8 @@ struct ApplyArgs {
     const void* links;    // internal link layout (V_mu or the 40 stored W)
     double diag;          // (4 + m0) Wilson, m staggered, (m0 + 15/8) Brillouin
     const double* diag_v; // per-right-hand-side diagonal (device, Nv entries) or null: diag for all
+    float diagf;          // the same in FP32, for the FP32-arithmetic sweeps (no FP64
+    const float* diag_vf; // conversion inside them)
     int* err;             // device error word (kernels with bounded waits record DIRAC_TIMEOUT) or null
     int tc;               // site order of the grid (site_of): 0 lexicographic, else t-chunk
     // the sweep covers the slab of nt t-slices starting at slice t0 (sites
@@ -52,7 +54,8 @@ template <typename Args> HD long slab_site(const Args& a, long p)
 
 template <typename A> DEV_INLINE A diag_of(const ApplyArgs& a, int v)
 {
-    return a.diag_v ? (A)a.diag_v[v] : (A)a.diag;
+    if constexpr (sizeof(A) == 4) return a.diag_vf ? a.diag_vf[v] : a.diagf;
+    else return a.diag_v ? a.diag_v[v] : a.diag;
 }
 
 // ---------------------------------------------------------------- Wilson
@@ -94,7 +97,8 @@ HD void wilson_reconstruct(const cx<A>* w, cx<A>* acc)
 
 // one hop: acc_r += (1 + S gamma_MU) U psi_r(nbr),  U = V_MU(lsite) or its adjoint (BACK);
 // NA: the loads bypass L1 (data this SM will not read again soon)
-template <typename T, int R, int MU, int S, bool BACK, bool NA = false>
+// FULL: every group holds R right-hand sides (Nv % R == 0), no clamping
+template <typename T, int R, int MU, int S, bool BACK, bool NA = false, bool FULL = false>
 DEV_INLINE void wilson_hop(const ApplyArgs& a, long nbr, long lsite, int v0,
                            cx<typename Store<T>::A> (&acc)[R][12])
 {
@@ -106,7 +110,7 @@ DEV_INLINE void wilson_hop(const ApplyArgs& a, long nbr, long lsite, int v0,
         // a partial last group recomputes the last right-hand side instead of
         // branching, so that the loads of all R right-hand sides can be issued
         // together; only the stores are guarded
-        const int v = min(v0 + r, a.Nv - 1);
+        const int v = FULL ? v0 + r : min(v0 + r, a.Nv - 1);
         cx<A> p[12], h[6], w[6];
         load_spinor_p<T, 12, NA>(a.in, a.g.vol, v, nbr, p);
         wilson_project<MU, S>(p, h);
@@ -116,9 +120,12 @@ DEV_INLINE void wilson_hop(const ApplyArgs& a, long nbr, long lsite, int v0,
     }
 }
 
-template <typename T, int R, bool DAG>
+// FAST: whole groups (Nv % R == 0) and one diagonal for all right-hand sides
+// (no per-column diagonal): no clamping, no branch on the diagonal
+template <typename T, int R, bool DAG, bool FAST = false>
 DEV_INLINE void wilson_site(const ApplyArgs& a, long s, int group)
 {
+    constexpr bool FULL = FAST;
     using A = typename Store<T>::A;
     long fwd[4], bwd[4];
     int x[4];
@@ -132,19 +139,21 @@ DEV_INLINE void wilson_site(const ApplyArgs& a, long s, int group)
     // forward hop carries (1 - gamma), backward (1 + gamma); the adjoint swaps them
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
-    wilson_hop<T, R, 0, SF, false>(a, s + fwd[0], s, v0, acc);
-    wilson_hop<T, R, 0, SB, true>(a, s + bwd[0], s + bwd[0], v0, acc);
-    wilson_hop<T, R, 1, SF, false>(a, s + fwd[1], s, v0, acc);
-    wilson_hop<T, R, 1, SB, true>(a, s + bwd[1], s + bwd[1], v0, acc);
-    wilson_hop<T, R, 2, SF, false>(a, s + fwd[2], s, v0, acc);
-    wilson_hop<T, R, 2, SB, true>(a, s + bwd[2], s + bwd[2], v0, acc);
-    wilson_hop<T, R, 3, SF, false>(a, s + fwd[3], s, v0, acc);
-    wilson_hop<T, R, 3, SB, true>(a, s + bwd[3], s + bwd[3], v0, acc);
+    wilson_hop<T, R, 0, SF, false, false, FULL>(a, s + fwd[0], s, v0, acc);
+    wilson_hop<T, R, 0, SB, true, false, FULL>(a, s + bwd[0], s + bwd[0], v0, acc);
+    wilson_hop<T, R, 1, SF, false, false, FULL>(a, s + fwd[1], s, v0, acc);
+    wilson_hop<T, R, 1, SB, true, false, FULL>(a, s + bwd[1], s + bwd[1], v0, acc);
+    wilson_hop<T, R, 2, SF, false, false, FULL>(a, s + fwd[2], s, v0, acc);
+    wilson_hop<T, R, 2, SB, true, false, FULL>(a, s + bwd[2], s + bwd[2], v0, acc);
+    wilson_hop<T, R, 3, SF, false, false, FULL>(a, s + fwd[3], s, v0, acc);
+    wilson_hop<T, R, 3, SB, true, false, FULL>(a, s + bwd[3], s + bwd[3], v0, acc);
     const A mh = (A)(-0.5);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int v = min(v0 + r, a.Nv - 1);
-        const A dg = diag_of<A>(a, v);
+        const int v = FULL ? v0 + r : min(v0 + r, a.Nv - 1);
+        A dg;
+        if constexpr (FAST) dg = (sizeof(A) == 4) ? (A)a.diagf : (A)a.diag;
+        else dg = diag_of<A>(a, v);
         cx<A> p[12];
         load_spinor<T, 12>(a.in, a.g.vol, v, s, p);
 #pragma unroll
@@ -154,7 +163,7 @@ DEV_INLINE void wilson_site(const ApplyArgs& a, long s, int group)
             o.im = fma(mh, acc[r][i].im, dg * p[i].im);
             p[i] = o;
         }
-        if (v0 + r < a.Nv) store_spinor<T, 12>(a.out, a.g.vol, v0 + r, s, p);
+        if (FULL || v0 + r < a.Nv) store_spinor<T, 12>(a.out, a.g.vol, v0 + r, s, p);
     }
 }
 
@@ -532,7 +541,8 @@ DEV_INLINE void wilson_site_pipe(const ApplyArgs& a, long s, int group, char* sm
 }
 
 // ---------------------------------------------------------------- staggered
-template <typename T, int R, bool DAG>
+// FAST as in wilson_site
+template <typename T, int R, bool DAG, bool FAST = false>
 DEV_INLINE void staggered_site(const ApplyArgs& a, long s, int group)
 {
     using A = typename Store<T>::A;
@@ -555,7 +565,7 @@ DEV_INLINE void staggered_site(const ApplyArgs& a, long s, int group)
         load_link<T>(a.links, a.g.vol, mu, s + bwd[mu], Ub);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int v = min(v0 + r, a.Nv - 1);   // partial group: recompute, store guarded
+            const int v = FAST ? v0 + r : min(v0 + r, a.Nv - 1);   // partial group: recompute, store guarded
             cx<A> pf[3], pb[3], w[3] = {}, wb[3] = {};
             load_spinor<T, 3>(a.in, a.g.vol, v, s + fwd[mu], pf);
             load_spinor<T, 3>(a.in, a.g.vol, v, s + bwd[mu], pb);
@@ -572,8 +582,10 @@ DEV_INLINE void staggered_site(const ApplyArgs& a, long s, int group)
     const A hf = DAG ? A(-0.5) : A(0.5);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int v = min(v0 + r, a.Nv - 1);
-        const A dg = diag_of<A>(a, v);
+        const int v = FAST ? v0 + r : min(v0 + r, a.Nv - 1);
+        A dg;
+        if constexpr (FAST) dg = (sizeof(A) == 4) ? (A)a.diagf : (A)a.diag;
+        else dg = diag_of<A>(a, v);
         cx<A> p[3];
         load_spinor<T, 3>(a.in, a.g.vol, v, s, p);
 #pragma unroll
@@ -583,7 +595,7 @@ DEV_INLINE void staggered_site(const ApplyArgs& a, long s, int group)
             o.im = fma(hf, acc[r][c].im, dg * p[c].im);
             p[c] = o;
         }
-        if (v0 + r < a.Nv) store_spinor<T, 3>(a.out, a.g.vol, v0 + r, s, p);
+        if (FAST || v0 + r < a.Nv) store_spinor<T, 3>(a.out, a.g.vol, v0 + r, s, p);
     }
 }
 

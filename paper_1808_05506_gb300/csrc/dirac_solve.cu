@@ -106,6 +106,7 @@ struct SolverWS {
     double* scal = nullptr;                                   // per-rhs scalar slots
     int* iflags = nullptr;                                    // active[W], breakdown, nactive
     double *bb, *rr64, *scale, *coef, *rr0, *rr, *gamma, *gnew, *delta, *alpha, *beta, *diag_v, *itol2;
+    float* diag_vf;                                           // diag_v in FP32 for the FP32-arithmetic sweeps
     cudaStream_t cs = nullptr;          // private stream: graphs cannot be captured on the legacy stream
     cudaEvent_t ev = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -163,12 +164,14 @@ static dirac_status ensure_solver_ws(dirac_handle* h, SolverWS** out)
     if ((st = h->alloc(&pp, 2 * blas_partials(n, h->Nv) * sizeof(double), "solver partials"))) return st;
     w->part = (double*)pp;
     const int nslots = 12;
-    if ((st = h->alloc(&pp, ((size_t)nslots * h->Nv + 1) * sizeof(double), "solver scalars"))) return st;
+    if ((st = h->alloc(&pp, ((size_t)nslots * h->Nv + 1 + ((size_t)h->Nv + 1) / 2) * sizeof(double), "solver scalars")))
+        return st;
     w->scal = (double*)pp;
     double** slots[] = {&w->bb, &w->rr64, &w->scale, &w->coef, &w->rr0, &w->rr,
                         &w->gamma, &w->gnew, &w->delta, &w->alpha, &w->beta, &w->diag_v};
     for (int i = 0; i < nslots; ++i) *slots[i] = w->scal + (size_t)i * h->Nv;
     w->itol2 = w->scal + (size_t)nslots * h->Nv;
+    w->diag_vf = reinterpret_cast<float*>(w->scal + (size_t)nslots * h->Nv + 1);
     if ((st = h->alloc(&pp, ((size_t)h->Nv + 2) * sizeof(int), "solver flags"))) return st;
     w->iflags = (int*)pp;
     if ((st = h->cuda(cudaStreamCreateWithFlags(&w->cs, cudaStreamNonBlocking), "solver stream"))) return st;
@@ -191,12 +194,13 @@ static dirac_status enqueue_iteration(dirac_handle* h, SolverWS* w, const double
     int* nactive = w->iflags + W + 1;
     const unsigned sb = (unsigned)((W + 127) / 128);
     dirac_status st;
-    if ((st = h->run_apply(false, w->t, w->p, W, h->diag, h->links, P, h->cfg, diag_v))) return st;
+    const float* dvf = diag_v ? w->diag_vf : nullptr;
+    if ((st = h->run_apply(false, w->t, w->p, W, h->diag, h->links, P, h->cfg, diag_v, 0, 0, dvf))) return st;
     if ((st = h->cuda(blas_norm2(P, n, W, w->t, w->part, w->delta, S), "solve: |t|"))) return st;
     k_cgls_alpha<<<sb, 128, 0, S>>>(W, w->gamma, w->delta, active, w->alpha, breakdown);
     if ((st = h->cuda(blas_cgls_step(P, n, W, w->alpha, w->e, w->p, w->r, w->t, w->part, w->rr, S), "solve: step")))
         return st;
-    if ((st = h->run_apply(true, w->s, w->r, W, h->diag, h->links, P, h->cfg, diag_v))) return st;
+    if ((st = h->run_apply(true, w->s, w->r, W, h->diag, h->links, P, h->cfg, diag_v, 0, 0, dvf))) return st;
     if ((st = h->cuda(blas_norm2(P, n, W, w->s, w->part, w->gnew, S), "solve: |s|"))) return st;
     k_cgls_beta<<<sb, 128, 0, S>>>(W, w->gnew, w->gamma, active, w->beta);
     if ((st = h->cuda(blas_xpay(P, n, W, w->s, w->beta, w->p, S), "solve: p = s + beta p"))) return st;
@@ -250,7 +254,9 @@ static dirac_status inner_cgls(dirac_handle* h, SolverWS* w, const double* diag_
     if ((st = h->cuda(cudaMemsetAsync(w->iflags + W, 0, 2 * sizeof(int), S), "solve: memset"))) return st;
     if ((st = h->cuda(cudaMemsetAsync(w->e, 0, n * W * cbytes(P), S), "solve: e = 0"))) return st;
     // s = D^+ r, p = s, gamma = |s|^2
-    if ((st = h->run_apply(true, w->s, w->r, W, h->diag, h->links, P, h->cfg, diag_v))) return st;
+    if ((st = h->run_apply(true, w->s, w->r, W, h->diag, h->links, P, h->cfg, diag_v, 0, 0,
+                           diag_v ? w->diag_vf : nullptr)))
+        return st;
     S_->sweeps++;
     if ((st = h->cuda(blas_scale_copy(P, n, W, w->s, nullptr, w->p, w->part, w->gamma, S), "solve: p = s")))
         return st;
@@ -490,6 +496,7 @@ extern "C" DIRAC_API dirac_status dirac_solve_batched(dirac_handle* h, int nsys,
     }
     std::vector<int> slot_sys(W, -1), slot_col(W, -1), slot_outer(W, 0);
     std::vector<double> diag(W, h->diag), bb(W, 0.0), rr64, res_col(col_base[nsys], 0.0);
+    std::vector<float> diagf(W);
     std::vector<int> outer_sys(nsys, 0), conv_col(col_base[nsys], 0);
     dirac_solve_stats S_ = {};
     CK(cudaMemsetAsync(w->b64, 0, n * W * 16, S), "batched: clear b");
@@ -531,6 +538,8 @@ extern "C" DIRAC_API dirac_status dirac_solve_batched(dirac_handle* h, int nsys,
         if (!occupied) break;
         if (admitted) {
             CK(cudaMemcpyAsync(w->diag_v, diag.data(), W * sizeof(double), cudaMemcpyHostToDevice, S), "copy");
+            diagf.assign(diag.begin(), diag.end());
+            CK(cudaMemcpyAsync(w->diag_vf, diagf.data(), W * sizeof(float), cudaMemcpyHostToDevice, S), "copy");
             CK(blas_norm2(P_F64, n, W, w->b64, w->part, w->bb, S), "batched: |b|");
             CK(cudaMemcpyAsync(bb.data(), w->bb, W * sizeof(double), cudaMemcpyDeviceToHost, S), "copy");
         }
