@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(256) k_wilson_pipe(ApplyArgs a, int ngroups)
 
 // V_GROUPS: blockDim = (sites, groups); block b covers a run of sites and a
 // chunk of gy right-hand-side groups
-template <typename T, int R, bool DAG, bool FAST>
+template <typename T, int R, bool DAG, int MODE>
 __global__ void __launch_bounds__(192, 2) k_wilson_groups(ApplyArgs a, int ngroups, int gy)
 {
     const int nchunks = (ngroups + gy - 1) / gy;
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(192, 2) k_wilson_groups(ApplyArgs a, int ngrou
     const int group = (int)(b % nchunks) * gy + threadIdx.y;
     const long p = (b / nchunks) * blockDim.x + threadIdx.x;
     if (p >= a.nsites || group >= ngroups) return;
-    wilson_site<T, R, DAG, FAST>(a, slab_site(a, p), group);
+    wilson_site<T, R, DAG, MODE>(a, slab_site(a, p), group);
 }
 
 template <typename T, int R>
@@ -219,14 +219,17 @@ cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
     if (c.variant == V_GROUPS) {
         const int gy = groups_per_block(block, ngroups);
         const long nb = ((a.nsites + block - 1) / block) * (long)((ngroups + gy - 1) / gy);
-        // whole groups of R right-hand sides and one diagonal: the specialised body
-        if (a.Nv % R == 0 && a.diag_v == nullptr) {
-            if (dag) k_wilson_groups<T, R, true, true><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
-            else k_wilson_groups<T, R, false, true><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
-        } else {
-            if (dag) k_wilson_groups<T, R, true, false><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
-            else k_wilson_groups<T, R, false, false><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
-        }
+        // whole groups of R right-hand sides: the specialised bodies
+        const bool dv = sizeof(T) == 8 ? a.diag_v != nullptr : a.diag_vf != nullptr;
+        const int mode = (a.Nv % R != 0 || (a.diag_v != nullptr && !dv)) ? 0 : (dv ? 2 : 1);
+        auto launch = [&](auto m) {
+            constexpr int M = decltype(m)::value;
+            if (dag) k_wilson_groups<T, R, true, M><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+            else k_wilson_groups<T, R, false, M><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+        };
+        if (mode == 1) launch(std::integral_constant<int, 1>{});
+        else if (mode == 2) launch(std::integral_constant<int, 2>{});
+        else launch(std::integral_constant<int, 0>{});
         return cudaGetLastError();
     }
     if constexpr (R <= 2) {

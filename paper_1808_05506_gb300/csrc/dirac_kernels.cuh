@@ -54,7 +54,7 @@ template <typename Args> HD long slab_site(const Args& a, long p)
 
 template <typename A> DEV_INLINE A diag_of(const ApplyArgs& a, int v)
 {
-    if constexpr (sizeof(A) == 4) return a.diag_vf ? a.diag_vf[v] : a.diagf;
+    if constexpr (sizeof(A) == 4) return a.diag_vf ? a.diag_vf[v] : (a.diag_v ? (A)a.diag_v[v] : a.diagf);
     else return a.diag_v ? a.diag_v[v] : a.diag;
 }
 
@@ -120,12 +120,23 @@ DEV_INLINE void wilson_hop(const ApplyArgs& a, long nbr, long lsite, int v0,
     }
 }
 
-// FAST: whole groups (Nv % R == 0) and one diagonal for all right-hand sides
-// (no per-column diagonal): no clamping, no branch on the diagonal
-template <typename T, int R, bool DAG, bool FAST = false>
+// MODE 0: general.  MODE 1: whole groups (Nv % R == 0) and one diagonal for
+// all right-hand sides; MODE 2: whole groups and a per-column diagonal.
+// Modes 1 and 2 need no clamping and no branch on the diagonal.
+template <typename A> DEV_INLINE A diag_mode(const ApplyArgs& a, int v, int mode)
+{
+    if (mode == 1) return sizeof(A) == 4 ? (A)a.diagf : (A)a.diag;
+    if (mode == 2) {
+        if constexpr (sizeof(A) == 4) return a.diag_vf[v];
+        else return a.diag_v[v];
+    }
+    return diag_of<A>(a, v);
+}
+
+template <typename T, int R, bool DAG, int MODE = 0>
 DEV_INLINE void wilson_site(const ApplyArgs& a, long s, int group)
 {
-    constexpr bool FULL = FAST;
+    constexpr bool FULL = MODE != 0;
     using A = typename Store<T>::A;
     long fwd[4], bwd[4];
     int x[4];
@@ -151,9 +162,7 @@ DEV_INLINE void wilson_site(const ApplyArgs& a, long s, int group)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int v = FULL ? v0 + r : min(v0 + r, a.Nv - 1);
-        A dg;
-        if constexpr (FAST) dg = (sizeof(A) == 4) ? (A)a.diagf : (A)a.diag;
-        else dg = diag_of<A>(a, v);
+        const A dg = diag_mode<A>(a, v, MODE);
         cx<A> p[12];
         load_spinor<T, 12>(a.in, a.g.vol, v, s, p);
 #pragma unroll
@@ -541,10 +550,11 @@ DEV_INLINE void wilson_site_pipe(const ApplyArgs& a, long s, int group, char* sm
 }
 
 // ---------------------------------------------------------------- staggered
-// FAST as in wilson_site
-template <typename T, int R, bool DAG, bool FAST = false>
+// MODE as in wilson_site
+template <typename T, int R, bool DAG, int MODE = 0>
 DEV_INLINE void staggered_site(const ApplyArgs& a, long s, int group)
 {
+    constexpr bool FAST = MODE != 0;
     using A = typename Store<T>::A;
     long fwd[4], bwd[4];
     int x[4];
@@ -583,9 +593,7 @@ DEV_INLINE void staggered_site(const ApplyArgs& a, long s, int group)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int v = FAST ? v0 + r : min(v0 + r, a.Nv - 1);
-        A dg;
-        if constexpr (FAST) dg = (sizeof(A) == 4) ? (A)a.diagf : (A)a.diag;
-        else dg = diag_of<A>(a, v);
+        const A dg = diag_mode<A>(a, v, MODE);
         cx<A> p[3];
         load_spinor<T, 3>(a.in, a.g.vol, v, s, p);
 #pragma unroll

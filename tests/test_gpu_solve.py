@@ -184,7 +184,9 @@ def test_solve_batched_c5_full(dg):
     nv_list = [int(v) for v in rng.integers(1, 25, 48)]
     kappas = [float(k) for k in rng.uniform(0.120, 0.124, 48)]
     V = synth.round_to(synth.gauge_links(L, 3, "near_identity", 1005), "f32")
-    D = dg.Dirac("wilson", L, 96, kappas[0], "bf16")
+    # 64 resident slots (solver: 3 FP64 + 5 BF16 fields of 64 columns, ~110 GB)
+    # and waves of at most 96 columns (their FP64 b and x, ~77 GB)
+    D = dg.Dirac("wilson", L, 64, kappas[0], "bf16")
     D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
     D.autotune()
     t0 = time.perf_counter()
@@ -192,7 +194,7 @@ def test_solve_batched_c5_full(dg):
     while i < 48:
         wave = []
         cols = 0
-        while i < 48 and cols + nv_list[i] <= 160:
+        while i < 48 and cols + nv_list[i] <= 96:
             wave.append(i)
             cols += nv_list[i]
             i += 1
