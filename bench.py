@@ -42,7 +42,6 @@ PAPER_CONTEXT = {"wilson_sp_knl_gflops": 345, "staggered_sp_knl_gflops": 475,
 KERNEL_SOURCES = ["paper_1808_05506_gb300/csrc/dirac_kernels.cuh",
                   "paper_1808_05506_gb300/csrc/dirac_common.cuh",
                   "paper_1808_05506_gb300/csrc/apply_wilson_impl.cuh",
-                  "paper_1808_05506_gb300/csrc/wilson_tma.cuh",
                   "paper_1808_05506_gb300/csrc/apply_wilson_f32.cu",
                   "paper_1808_05506_gb300/csrc/apply_wilson.cu"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "wilson_apply_traffic.json")
@@ -469,7 +468,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
                      "peak_kind": f"{peak_kind} copy bandwidth",
-                     "kernel": "k_{}{}<{},R={}>".format(op, {0: "", 1: "_groups", 2: "_march", 3: "_pipe", 4: "_tma", 5: "_xrow"}[cfg[2]],
+                     "kernel": "k_{}{}<{},R={}>".format(op, {0: "", 1: "_groups", 2: "_march", 3: "_pipe", 5: "_xrow"}[cfg[2]],
                                                       w["prec"], cfg[0]),
                      "algorithmic_bytes_per_launch": bytes_step},
         "clocks": clk.summary(),

@@ -289,12 +289,7 @@ DIRAC_API dirac_status dirac_apply_static(dirac_handle* h, void* out, const void
  *               to 8 consecutive t-slices of its (x, y, z) site, reading each
  *               spinor and t-link along t once (the t hops are carried from
  *               one slice to the next in registers);
- *            4: (Wilson, FP32/BF16/FP16, R = 1 or 2) tiles of `block` sites made
- *               of complete x-rows, each tile's neighbour rows and tiles
- *               streamed into shared memory by bulk copies (one producer warp,
- *               a ring of mbarrier-guarded buffers) for 2 * R right-hand sides
- *               at a time; block must be a multiple of Lx and of 32, <= 128,
- *               with Ly divisible by block / Lx and Lx divisible by 4;
+ *            4: not used;
  *            3: (Wilson) variant 0 with a three-stage cp.async pipeline that
  *               keeps the next two hops in flight in shared memory; needs
  *               3 * block * (R * spinor bytes + link bytes) <= 227 KB;
@@ -334,9 +329,10 @@ DIRAC_API dirac_status dirac_get_site_order(const dirac_handle* h, int* tchunk);
 DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int* R, int* block, int* variant, double* ms);
 
 /* Wait for the handle's stream and report kernel-side failures: returns
- * DIRAC_TIMEOUT (and clears the record) if a kernel's bounded wait for its
- * staged operands ran out since the last call, else DIRAC_OK or the CUDA
- * error of the stream. */
+ * DIRAC_TIMEOUT (and clears the record) if a kernel recorded that a bounded
+ * device-side wait ran out since the last call (none of the current sweeps
+ * waits on other threads' data), else DIRAC_OK or the CUDA error of the
+ * stream. */
 DIRAC_API dirac_status dirac_sync(dirac_handle* h);
 
 /* One-line description of the last error on h (or of the last failed

@@ -386,8 +386,8 @@ class Dirac:
 
     def set_kernel_config(self, R: int, block: int, variant: int = 0):
         """Launch shape: R right-hand sides per thread, block, variant (0 direct,
-        1 groups in block, 2 Wilson t-march, 3 pipelined Wilson, 4 bulk-copy
-        Wilson, 5 Wilson x-rows per warp); see dirac_set_kernel_config."""
+        1 groups in block, 2 Wilson t-march, 3 pipelined Wilson, 5 Wilson x-rows
+        per warp); see dirac_set_kernel_config."""
         check(lib().dirac_set_kernel_config(self.h, R, block, variant), self.h, "dirac_set_kernel_config")
 
     def set_site_order(self, tchunk: int):
@@ -419,22 +419,16 @@ class Dirac:
         return R.value, B.value, Pp.value
 
 
-VARIANTS = {"staggered": (0, 1), "wilson": (0, 1, 2, 3, 4, 5), "brillouin": (0, 1)}
+VARIANTS = {"staggered": (0, 1), "wilson": (0, 1, 2, 3, 5), "brillouin": (0, 1)}
 
 
 def config_supported(op: str, prec: str, R: int, block: int, variant: int, L=None) -> bool:
     """The rule dirac_set_kernel_config applies (without a handle); L = (Nx, Ny, Nz, Nt)
-    is needed for variants 4 and 5."""
+    is needed for variant 5."""
     if block < 32 or block > 256 or block % 32:
         return False
     if variant == 4:
-        if op != "wilson" or prec == "f64" or R not in (1, 2) or L is None or block > 128:
-            return False
-        Lx, Ly = L[0], L[1]
-        if block % Lx or Lx % 4 or Ly % (block // Lx):
-            return False
-        k, lb, nst = (6, 8, 3) if prec == "f32" else (3, 4, 4)
-        return 256 + 128 + nst * (2 * R * k * block * 16 + 9 * block * lb) <= 227 * 1024
+        return False   # not used
     if variant == 5:
         if op != "wilson" or prec == "f64" or not 1 <= R <= 2 or block > 192 or L is None:
             return False

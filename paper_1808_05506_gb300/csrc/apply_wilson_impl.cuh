@@ -3,7 +3,9 @@
 #pragma once
 
 #include "dirac_internal.h"
-#include "wilson_tma.cuh"
+#include <type_traits>
+
+#include "dirac_kernels.cuh"
 
 namespace dirac {
 
@@ -51,137 +53,6 @@ __global__ void __launch_bounds__(192, 2) k_wilson_xrow(ApplyArgs a, int ngroups
     const int t0 = a.t0 + (int)(b / nruns) * tc;
     if (group >= ngroups) return;   // a whole warp
     wilson_xrow<T, R, DAG>(a, s3, threadIdx.x, group, t0, min(t0 + tc, a.t0 + a.nt));
-}
-
-// V_TMA: persistent CTAs; one producer warp streams the stages of each tile
-// with bulk copies, G * S consumer threads compute from shared memory
-constexpr int kTimeoutCode = 7;   // DIRAC_TIMEOUT
-
-template <typename T> struct TmaStages { static constexpr int value = sizeof(T) >= 4 ? 3 : 4; };
-
-template <typename T, int R, int G, bool DAG>
-__global__ void __launch_bounds__(G * 128 + 32, 1) k_wilson_tma(TmaArgs ta, const __grid_constant__ CUtensorMap mspin,
-                                                                 const __grid_constant__ CUtensorMap mlink)
-{
-    constexpr int RB = R * G;
-    constexpr int NST = TmaStages<T>::value;
-    using Lay = TmaLayout<T, RB>;
-    using A = typename Store<T>::A;
-    extern __shared__ __align__(16) char smem[];
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
-    uint64_t* empty = full + NST;
-    // stage buffers start on a 128-byte boundary (tensor-copy destinations)
-    char* bufs = smem + 256 + ((128u - (smem_u32(smem) & 127u)) & 127u);
-    const size_t sb = Lay::stage_bytes(ta.S);
-    const int ncons = ta.S * G;
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        for (int b = 0; b < NST; ++b) {
-            mbar_init(&full[b], 1);
-            mbar_init(&empty[b], ncons / 32);
-        }
-        mbar_fence_init();
-    }
-    __syncthreads();
-    const Geom& g = ta.a.g;
-    if (tid >= ncons) {
-        // producer: lane 0 of the last warp
-        if ((tid & 31) != 0) return;
-        unsigned long seq = 0;
-        bool ok = true;
-        for (long tile = blockIdx.x; tile < ta.ntiles && ok; tile += gridDim.x) {
-            const TmaTile Tt = tma_tile(g, ta.ny, tile);
-            for (int q = 0; q < ta.rounds && ok; ++q)
-                for (int d = 0; d < TMA_STAGES_PER_ROUND; ++d) {
-                    const int b = (int)(seq % NST);
-                    const unsigned long u = seq / NST;
-                    if (u > 0 && !mbar_wait(&empty[b], (unsigned)((u - 1) & 1))) {
-                        ok = false;
-                        break;
-                    }
-                    tma_issue_stage<T, RB>(ta, &mspin, &mlink, Tt, q, d, bufs + b * sb, &full[b]);
-                    ++seq;
-                }
-        }
-        if (!ok) {
-            if (ta.err) atomicExch(ta.err, kTimeoutCode);
-            // let the copies already issued land before the CTA can exit
-            const unsigned long first = seq > (unsigned long)NST ? seq - NST : 0;
-            for (unsigned long s2 = first; s2 < seq; ++s2) mbar_wait(&full[s2 % NST], (unsigned)((s2 / NST) & 1));
-        }
-        return;
-    }
-    const int i = tid % ta.S, sub = tid / ta.S;
-    const int j = i / g.L[0], x = i % g.L[0];
-    unsigned long seq = 0;
-    for (long tile = blockIdx.x; tile < ta.ntiles; tile += gridDim.x) {
-        const TmaTile Tt = tma_tile(g, ta.ny, tile);
-        const long site = tma_row_site(g, Tt, j, 0) + x;
-        // rows whose y neighbour lies across the periodic boundary (outside the box)
-        const long gs_up = (Tt.y0 + ta.ny == g.L[1] && j == ta.ny - 1) ? tma_row_site(g, Tt, j, 1) + x : -1;
-        const long gs_dn = (Tt.y0 == 0 && j == 0) ? tma_row_site(g, Tt, j, 2) + x : -1;
-        for (int q = 0; q < ta.rounds; ++q) {
-            cx<A> acc[R][12];
-            for (int d = 0; d < TMA_STAGES_PER_ROUND; ++d, ++seq) {
-                const int b = (int)(seq % NST);
-                if (!mbar_wait(&full[b], (unsigned)((seq / NST) & 1))) {
-                    if (ta.err) atomicExch(ta.err, kTimeoutCode);
-                    return;
-                }
-                tma_consume_stage<T, R, RB, DAG>(ta, d, bufs + b * sb, i, sub, q, acc,
-                                                 d == 1 ? gs_up : (d == 2 ? gs_dn : -1));
-                __syncwarp();
-                if ((tid & 31) == 0) mbar_arrive(&empty[b]);
-            }
-            const A mh = (A)(-0.5);
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int v = q * RB + sub * R + r;
-                if (v < ta.a.Nv) {
-                    cx<A> o[12];
-#pragma unroll
-                    for (int c = 0; c < 12; ++c) o[c] = cx<A>{mh * acc[r][c].re, mh * acc[r][c].im};
-                    store_spinor<T, 12>(ta.a.out, g.vol, v, site, o);
-                }
-            }
-        }
-    }
-}
-
-// the tile of the TMA variant for sites-per-tile S: ny = S / Lx complete rows
-
-
-
-
-template <typename T, int R>
-cudaError_t go_tma(bool dag, const ApplyArgs& a, int S, cudaStream_t st)
-{
-    constexpr int G = 2;
-    int ny = 0;
-    if (!wilson_tma_geometry(a.g, S, &ny)) return cudaErrorInvalidValue;
-    const int prec0 = sizeof(T) == 4 ? P_F32 : P_BF16;
-    CUtensorMap mspin, mlink;
-    const int P = R * G * SpinorLayout<T, 12>::K;
-    if (!wilson_tma_maps(a, prec0, P, ny, &mspin, &mlink)) return cudaErrorInvalidValue;
-    TmaArgs ta;
-    ta.a = a;
-    ta.P = P;
-    ta.ny = ny;
-    ta.S = S;
-    ta.ntiles = a.g.vol / S;
-    ta.rounds = (a.Nv + R * G - 1) / (R * G);
-    ta.err = a.err;
-    const int prec = sizeof(T) == 4 ? P_F32 : P_BF16;
-    const size_t smem = wilson_tma_smem(prec, R, S);
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const long grid = ta.ntiles < nsm ? ta.ntiles : nsm;
-    auto kern = dag ? k_wilson_tma<T, R, G, true> : k_wilson_tma<T, R, G, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<(unsigned)grid, G * S + 32, smem, st>>>(ta, mspin, mlink);
-    return cudaGetLastError();
 }
 
 // pipelined variant: the loads of later hops are in flight in shared memory
@@ -275,16 +146,6 @@ cudaError_t wilson_go_T(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t 
         if (c.variant != V_DIRECT) return cudaErrorInvalidValue;
     }
 
-    if (c.variant == V_TMA) {
-        if constexpr (sizeof(T) == 8) return cudaErrorInvalidValue;
-        else {
-            switch (c.R) {
-            case 1: return go_tma<T, 1>(dag, a, c.block, st);
-            case 2: return go_tma<T, 2>(dag, a, c.block, st);
-            default: return cudaErrorInvalidValue;
-            }
-        }
-    }
     switch (c.R) {
     case 1: return go<T, 1>(dag, a, c, st);
     case 2: return go<T, 2>(dag, a, c, st);

@@ -73,7 +73,7 @@ void dirac_handle::release(void*& p)
 
 size_t dirac_handle::field_bytes_internal(int nv) const
 {
-    return (size_t)g.vol * nv * nsc_of(op) * cbytes(prec);
+    return nblk_of((size_t)g.vol) * 32 * nv * nsc_of(op) * cbytes(prec);   // whole blocks of 32 sites
 }
 
 size_t dirac_handle::field_bytes_canonical(int nv) const
@@ -241,6 +241,7 @@ dirac_handle::~dirac_handle()
     release(links);
     release(links64);
     release(W64);
+    release(links64b);
     release(ws_in);
     release(ws_out);
     free_solver_workspace();
@@ -309,8 +310,9 @@ dirac_status dirac_set_links(dirac_handle* h, const void* V, dirac_prec V_prec, 
     h->release_after_sync(dV);
     if (st) return st;
     h->release(h->W64);
+    h->release(h->links64b);
     const int nmat = (h->op == OP_BRILLOUIN) ? 40 : 4;
-    if (!h->links && (st = h->alloc(&h->links, (size_t)h->g.vol * 9 * nmat * cbytes(h->prec), "links")))
+    if (!h->links && (st = h->alloc(&h->links, nblk_of((size_t)h->g.vol) * 32 * 9 * nmat * cbytes(h->prec), "links")))
         return st;
     if (h->op == OP_BRILLOUIN) {
         if ((st = h->build_W64())) return st;
@@ -324,6 +326,29 @@ dirac_status dirac_set_links(dirac_handle* h, const void* V, dirac_prec V_prec, 
     st = h->cuda(cudaStreamSynchronize(h->stream), "dirac_set_links");
     if (st) return st;
     h->have_links = true;
+    return DIRAC_OK;
+}
+
+// the operator's links in FP64 and in the sweeps' blocked layout (the FP64 copies
+// links64 / W64 are [m][9][site], the layout the W build and the force read)
+dirac_status dirac_handle::ensure_links64b(const void** out)
+{
+    if (prec == P_F64) {
+        *out = links;
+        return DIRAC_OK;
+    }
+    if (!links64b) {
+        dirac_status st;
+        const int nmat = (op == OP_BRILLOUIN) ? 40 : 4;
+        if (op == OP_BRILLOUIN && (st = build_W64())) return st;
+        if ((st = alloc(&links64b, nblk_of((size_t)g.vol) * 32 * 9 * nmat * 16, "FP64 links (blocked)"))) return st;
+        if ((st = cuda(launch_convert_links(P_F64, g, nmat, op == OP_BRILLOUIN ? W64 : links64, links64b, stream),
+                       "FP64 links (blocked)"))) {
+            release(links64b);
+            return st;
+        }
+    }
+    *out = links64b;
     return DIRAC_OK;
 }
 
@@ -474,11 +499,6 @@ namespace dirac {
 bool apply_config_supported(int op, int prec, int R, int block, int variant, const Geom& g)
 {
     if (block < 32 || block > 256 || block % 32) return false;
-    if (variant == V_TMA) {
-        int ny = 0;
-        return op == OP_WILSON && prec != P_F64 && (R == 1 || R == 2) && wilson_tma_geometry(g, block, &ny) &&
-               wilson_tma_smem(prec, R, block) <= 227 * 1024;
-    }
     if (variant == V_XROW)
         return op == OP_WILSON && prec != P_F64 && R >= 1 && R <= 2 && block <= 192 && 32 % g.L[0] == 0 &&
                g.stride[3] % 32 == 0;

@@ -281,13 +281,27 @@ template <typename T, int NSC> struct SpinorLayout {
     static constexpr int K = NSC / CPV;
 };
 
+// Internal layout of the spinor and link fields: the sites go in blocks of
+// 32 (what one warp reads), and inside a block the planes follow each other:
+// element (plane q, site s) of a field with Q planes of one right-hand side
+// (or one link set) sits at ((p * nblk + s / 32) * Q + q) * 32 + s % 32,
+// p = right-hand side (or link direction), nblk = ceil(vol / 32).  A warp on
+// 32 aligned sites reads 32 consecutive elements per plane, and the planes of
+// one site lie at fixed offsets (32 elements apart), so one address serves a
+// whole spinor or link.  The sites s >= vol of the last block are padding.
+HD size_t nblk_of(size_t vol) { return (vol + 31) >> 5; }
+HD size_t blk_index(size_t vol, int Q, int p, int q, long s)
+{
+    return (((size_t)p * nblk_of(vol) + ((size_t)s >> 5)) * Q + q) * 32 + ((size_t)s & 31);
+}
+
 template <typename T, int NSC>
 DEV_INLINE void load_spinor(const void* base, size_t vol, int v, long s, cx<typename Store<T>::A>* out)
 {
     using L = SpinorLayout<T, NSC>;
 #pragma unroll
     for (int k = 0; k < L::K; ++k) {
-        size_t idx = ((size_t)v * L::K + k) * vol + (size_t)s;
+        size_t idx = blk_index(vol, L::K, v, k, s);
         if constexpr (L::CPV == 1) out[k] = ld_one<T>(base, idx);
         else ld_vec<T>(base, idx, out + k * L::CPV);
     }
@@ -299,7 +313,7 @@ DEV_INLINE void store_spinor(void* base, size_t vol, int v, long s, const cx<typ
     using L = SpinorLayout<T, NSC>;
 #pragma unroll
     for (int k = 0; k < L::K; ++k) {
-        size_t idx = ((size_t)v * L::K + k) * vol + (size_t)s;
+        size_t idx = blk_index(vol, L::K, v, k, s);
         if constexpr (L::CPV == 1) st_one<T>(base, idx, in[k]);
         else st_vec<T>(base, idx, in + k * L::CPV);
     }
@@ -343,7 +357,7 @@ DEV_INLINE void load_spinor_p(const void* base, size_t vol, int v, long s, cx<ty
     using L = SpinorLayout<T, NSC>;
 #pragma unroll
     for (int k = 0; k < L::K; ++k) {
-        size_t idx = ((size_t)v * L::K + k) * vol + (size_t)s;
+        size_t idx = blk_index(vol, L::K, v, k, s);
         if constexpr (L::CPV == 1) out[k] = ld_one_p<T, NA>(base, idx);
         else ld_vec_p<T, NA>(base, idx, out + k * L::CPV);
     }
@@ -352,7 +366,7 @@ template <typename T, bool NA>
 DEV_INLINE void load_link_p(const void* base, size_t vol, int m, long s, cx<typename Store<T>::A>* U)
 {
 #pragma unroll
-    for (int e = 0; e < 9; ++e) U[e] = ld_one_p<T, NA>(base, ((size_t)m * 9 + e) * vol + (size_t)s);
+    for (int e = 0; e < 9; ++e) U[e] = ld_one_p<T, NA>(base, blk_index(vol, 9, m, e, s));
 }
 
 // 3x3 link m at site s
@@ -360,7 +374,7 @@ template <typename T>
 DEV_INLINE void load_link(const void* base, size_t vol, int m, long s, cx<typename Store<T>::A>* U)
 {
 #pragma unroll
-    for (int e = 0; e < 9; ++e) U[e] = ld_one<T>(base, ((size_t)m * 9 + e) * vol + (size_t)s);
+    for (int e = 0; e < 9; ++e) U[e] = ld_one<T>(base, blk_index(vol, 9, m, e, s));
 }
 
 // ---- packed FP32 pairs: one fma.rn.f32x2 does the (re, im) halves of a

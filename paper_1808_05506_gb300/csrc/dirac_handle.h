@@ -22,6 +22,8 @@ struct dirac_handle {
     void* links = nullptr;    // storage-precision links [m][9][site] (m = mu, or 40 stored W)
     void* links64 = nullptr;  // FP64 V_mu [4][9][site]
     void* W64 = nullptr;      // FP64 W [40][9][site] (Brillouin; kept for F64 handles, lazy otherwise)
+    void* links64b = nullptr; // FP64 links of the operator (V or W) in the blocked layout of the
+                              // sweeps, for the solver's FP64 residual (lazy; F64 handles use links)
     bool have_links = false;
     int* dev_err = nullptr;   // device error word written by kernels whose bounded waits run out
 
@@ -50,6 +52,7 @@ struct dirac_handle {
     double diag_of(double mass) const;
     dirac_status ensure_workspace();
     dirac_status build_W64();
+    dirac_status ensure_links64b(const void** out);
     dirac::ApplyArgs args(void* out, const void* in, int nv, double diag_value) const;
     dirac_status run_apply(bool dagger, void* out, const void* in, int nv, double diag_value,
                            const void* link_ptr, int p, dirac::LaunchCfg c, const double* diag_v = nullptr,

@@ -28,8 +28,7 @@ enum Variant {
     V_TMARCH = 2,   // Wilson: V_GROUPS over (x, y, z) site columns, each thread walking up to
                     // 8 consecutive t-slices with the t hops carried in registers
     V_PIPE3 = 3,    // Wilson: V_DIRECT with a 3-stage cp.async pipeline in shared memory
-    V_TMA = 4,      // Wilson (FP32/BF16/FP16): tiles of complete x-rows streamed by bulk copies
-                    // (one producer warp, mbarrier ring); `block` = sites per tile
+    // 4 is not used (a variant with bulk-copied tiles, retired with the blocked layout)
     V_XROW = 5      // Wilson (FP32/BF16/FP16), Lx dividing 32: a warp holds 32 consecutive sites
                     // of the (x, y, z) volume (whole x-rows) and walks up to 8 t-slices; x hops
                     // by warp shuffles, t hops carried in registers; `block` = threads
@@ -52,10 +51,6 @@ inline int groups_per_block(int block, int ngroups)
 
 bool apply_config_supported(int op, int prec, int R, int block, int variant, const Geom& g);
 size_t wilson_pipe_smem(int prec, int R, int block, int stages);
-bool wilson_tma_geometry(const Geom& g, int S, int* ny);
-// tensor maps (CUtensorMap) of the spinor and link arrays for the TMA sweep
-bool wilson_tma_maps(const ApplyArgs& a, int prec, int P, int ny, void* mspin, void* mlink);
-size_t wilson_tma_smem(int prec, int R, int S);
 
 // out = D in (or D^+ in) on internal-layout fields
 cudaError_t launch_apply(int op, int prec, bool dagger, const ApplyArgs& a, LaunchCfg cfg,

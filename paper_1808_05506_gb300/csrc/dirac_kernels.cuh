@@ -388,7 +388,7 @@ DEV_INLINE void wilson_issue(const ApplyArgs& a, int h, long nbr, long lsite, in
         if (v0 + r < a.Nv) {
 #pragma unroll
             for (int k = 0; k < P::K; ++k) {
-                const size_t gi = ((size_t)(v0 + r) * P::K + k) * a.g.vol + (size_t)nbr;
+                const size_t gi = blk_index(a.g.vol, P::K, v0 + r, k, nbr);
                 cp_async<16>(stage + ((size_t)(r * P::K + k) * nthr + tid) * 16,
                              static_cast<const char*>(a.in) + gi * 16);
             }
@@ -400,7 +400,7 @@ DEV_INLINE void wilson_issue(const ApplyArgs& a, int h, long nbr, long lsite, in
 #pragma unroll
         for (int e = 0; e < 9; ++e)
             cp_async<P::LB>(lb + ((size_t)e * nthr + tid) * P::LB,
-                            static_cast<const char*>(a.links) + (((size_t)mu * 9 + e) * a.g.vol + (size_t)lsite) * P::LB);
+                            static_cast<const char*>(a.links) + blk_index(a.g.vol, 9, mu, e, lsite) * P::LB);
     }
     cp_async_commit();
 }

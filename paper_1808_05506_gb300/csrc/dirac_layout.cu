@@ -200,14 +200,17 @@ cudaError_t launch_links_to_f64(const Geom& g, const void* canon, bool canon_f64
     return cudaGetLastError();
 }
 
+// FP64 links [m][e][site] -> storage-precision links in the blocked layout
 template <typename T>
-__global__ void k_convert_links(long n, const double2* __restrict__ src, void* dst)
+__global__ void k_convert_links(long vol, long n, const double2* __restrict__ src, void* dst)
 {
-    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;   // (m, e, site), site fastest
     if (i >= n) return;
+    const long s = i % vol;
+    const long me = i / vol;
     double2 v = src[i];
     using A = typename Store<T>::A;
-    st_one<T>(dst, (size_t)i, cx<A>{(A)v.x, (A)v.y});
+    st_one<T>(dst, blk_index((size_t)vol, 9, (int)(me / 9), (int)(me % 9), s), cx<A>{(A)v.x, (A)v.y});
 }
 
 cudaError_t launch_convert_links(int prec, const Geom& g, int nmat, const void* src64, void* dst,
@@ -217,10 +220,10 @@ cudaError_t launch_convert_links(int prec, const Geom& g, int nmat, const void* 
     const unsigned nb = (unsigned)((n + 255) / 256);
     const double2* s = (const double2*)src64;
     switch (prec) {
-    case P_F64: k_convert_links<double><<<nb, 256, 0, st>>>(n, s, dst); break;
-    case P_F32: k_convert_links<float><<<nb, 256, 0, st>>>(n, s, dst); break;
-    case P_BF16: k_convert_links<__nv_bfloat16><<<nb, 256, 0, st>>>(n, s, dst); break;
-    case P_F16: k_convert_links<__half><<<nb, 256, 0, st>>>(n, s, dst); break;
+    case P_F64: k_convert_links<double><<<nb, 256, 0, st>>>(g.vol, n, s, dst); break;
+    case P_F32: k_convert_links<float><<<nb, 256, 0, st>>>(g.vol, n, s, dst); break;
+    case P_BF16: k_convert_links<__nv_bfloat16><<<nb, 256, 0, st>>>(g.vol, n, s, dst); break;
+    case P_F16: k_convert_links<__half><<<nb, 256, 0, st>>>(g.vol, n, s, dst); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -151,7 +151,7 @@ static dirac_status ensure_solver_ws(dirac_handle* h, SolverWS** out)
     h->sw = w;
     w->W = h->Nv;
     w->prec = h->prec;
-    const size_t n = (size_t)nsc_of(h->op) * h->g.vol;
+    const size_t n = (size_t)nsc_of(h->op) * nblk_of((size_t)h->g.vol) * 32;
     const size_t f64 = n * h->Nv * 16, fp = n * h->Nv * cbytes(h->prec);
     dirac_status st;
     if ((st = h->alloc(&w->b64, f64, "solver b"))) return st;
@@ -160,6 +160,13 @@ static dirac_status ensure_solver_ws(dirac_handle* h, SolverWS** out)
     void** inner[] = {&w->e, &w->r, &w->s, &w->p, &w->t};
     for (void** q : inner)
         if ((st = h->alloc(q, fp, "solver inner field"))) return st;
+    // the padding sites of the last block of 32 stay zero (the vector kernels
+    // run over whole blocks; the sweeps and packs write only real sites)
+    void** fields64[] = {&w->b64, &w->x64, &w->r64};
+    for (void** q : fields64)
+        if ((st = h->cuda(cudaMemset(*q, 0, f64), "solver field clear"))) return st;
+    for (void** q : inner)
+        if ((st = h->cuda(cudaMemset(*q, 0, fp), "solver field clear"))) return st;
     void* pp = nullptr;
     if ((st = h->alloc(&pp, 2 * blas_partials(n, h->Nv) * sizeof(double), "solver partials"))) return st;
     w->part = (double*)pp;
@@ -187,7 +194,7 @@ static dirac_status ensure_solver_ws(dirac_handle* h, SolverWS** out)
 static dirac_status enqueue_iteration(dirac_handle* h, SolverWS* w, const double* diag_v)
 {
     const int W = w->W, P = w->prec;
-    const size_t n = (size_t)nsc_of(h->op) * h->g.vol;
+    const size_t n = (size_t)nsc_of(h->op) * nblk_of((size_t)h->g.vol) * 32;
     cudaStream_t S = h->stream;
     int* active = w->iflags;
     int* breakdown = w->iflags + W;
@@ -244,7 +251,7 @@ static dirac_status inner_cgls(dirac_handle* h, SolverWS* w, const double* diag_
                                dirac_solve_stats* S_, bool* breakdown_out)
 {
     const int W = w->W, P = w->prec;
-    const size_t n = (size_t)nsc_of(h->op) * h->g.vol;
+    const size_t n = (size_t)nsc_of(h->op) * nblk_of((size_t)h->g.vol) * 32;
     cudaStream_t S = h->stream;
     dirac_status st;
     *breakdown_out = false;
@@ -305,7 +312,7 @@ static dirac_status refine_step(dirac_handle* h, SolverWS* w, const double* diag
                                 dirac_solve_stats* S_)
 {
     const int W = w->W, P = w->prec;
-    const size_t n = (size_t)nsc_of(h->op) * h->g.vol;
+    const size_t n = (size_t)nsc_of(h->op) * nblk_of((size_t)h->g.vol) * 32;
     cudaStream_t S = h->stream;
     dirac_status st;
     std::vector<double> scale(W), coef(W);
@@ -334,11 +341,12 @@ static dirac_status fp64_residual(dirac_handle* h, SolverWS* w, const double* di
                                   dirac_solve_stats* S_)
 {
     const int W = w->W;
-    const size_t n = (size_t)nsc_of(h->op) * h->g.vol;
+    const size_t n = (size_t)nsc_of(h->op) * nblk_of((size_t)h->g.vol) * 32;
     cudaStream_t S = h->stream;
-    const void* L64 = (h->op == OP_BRILLOUIN) ? h->W64 : h->links64;
-    const LaunchCfg cfg64 = default_config(h->op, P_F64, W);
+    const void* L64 = nullptr;
     dirac_status st;
+    if ((st = h->ensure_links64b(&L64))) return st;
+    const LaunchCfg cfg64 = default_config(h->op, P_F64, W);
     if ((st = h->run_apply(false, w->r64, w->x64, W, h->diag, L64, P_F64, cfg64, diag_v))) return st;
     S_->fp64_sweeps++;
     if ((st = h->cuda(blas_residual64(n, W, w->b64, w->r64, w->r64, w->part, w->rr64, S), "solve: residual")))
@@ -396,7 +404,7 @@ extern "C" DIRAC_API dirac_status dirac_solve(dirac_handle* h, void* x, const vo
     if ((st = ensure_solver_ws(h, &w))) return st;
     OnPrivateStream guard(h, w);
     const int Nv = h->Nv, nsc = nsc_of(h->op);
-    const size_t n = (size_t)nsc * h->g.vol;
+    const size_t n = (size_t)nsc * nblk_of((size_t)h->g.vol) * 32;
     cudaStream_t S = h->stream;
 
 #define CK(call, what)                               \
@@ -479,7 +487,7 @@ extern "C" DIRAC_API dirac_status dirac_solve_batched(dirac_handle* h, int nsys,
     if ((st = ensure_solver_ws(h, &w))) return st;
     OnPrivateStream guard(h, w);
     const int W = w->W, nsc = nsc_of(h->op);
-    const size_t n = (size_t)nsc * h->g.vol;
+    const size_t n = (size_t)nsc * nblk_of((size_t)h->g.vol) * 32;
     cudaStream_t S = h->stream;
 
 #define CK(call, what)                               \

@@ -97,7 +97,7 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
         }
         best = 1e30;
         LaunchCfg win = h->cfg;
-        const int variants[] = {V_DIRECT, V_GROUPS, V_TMARCH, V_PIPE3, V_TMA, V_XROW};
+        const int variants[] = {V_DIRECT, V_GROUPS, V_TMARCH, V_PIPE3, V_XROW};
         for (int r : Rs) {
             if (r > h->Nv && r != Rs.front()) continue;
             for (int b : blocks)
@@ -131,7 +131,7 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
                 if (!launched) continue;
                 int kerr = 0;
                 cudaMemcpy(&kerr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
-                if (kerr) {   // a bounded wait ran out in this variant: never pick it
+                if (kerr) {   // a kernel recorded a failure in this variant: never pick it
                     cudaMemset(h->dev_err, 0, sizeof(int));
                     continue;
                 }

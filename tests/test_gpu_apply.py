@@ -118,20 +118,6 @@ def test_low_precision_storage(dg, op, mass, prec):
 
 
 @pytest.mark.parametrize("prec", ["f32", "bf16", "f16"])
-def test_wilson_tma_tiles(dg, prec):
-    """The bulk-copy variant over tile shapes: whole planes, partial planes
-    whose y+1 / y-1 stages wrap around, Nv that leaves a partial round."""
-    for L, Nv, R, S in (((8, 16, 2, 4), 3, 1, 32), ((8, 12, 4, 2), 5, 2, 32), ((32, 8, 4, 4), 7, 2, 128),
-                        ((16, 8, 2, 6), 4, 1, 64), ((24, 8, 4, 4), 6, 2, 96)):
-        V, psi = inputs("wilson", L, Nv, "f32", 260)
-        for dagger in (False, True):
-            got = run(dg, "wilson", L, Nv, 0.124, prec, V, psi, dagger=dagger, cfg=(R, S, 4), internal=True)
-            Vr, pr = rounded_for_oracle(V, psi, prec)
-            want = oracle.apply("wilson", Vr, pr, oracle.kappa_to_m0(0.124), dagger=dagger)
-            assert rel_l2(got, want) <= TOL[prec], (L, Nv, R, S, dagger)
-
-
-@pytest.mark.parametrize("prec", ["f32", "bf16", "f16"])
 def test_wilson_xrow_shapes(dg, prec):
     """The warp-per-x-rows variant (x hops by lane exchange, t hops carried):
     rows of 32, 16, 8 and 4 sites (one to eight rows per warp), t-extents
@@ -247,11 +233,12 @@ def test_site_order_bit_identical(dg, op, mass):
     for variant in (0, 1):
         D.set_kernel_config(2, 64, variant)
         D.set_site_order(0)
-        ref = D.apply(xi, out=D.new_internal(), dagger=True).clone()
+        # zeroed outputs: the padding sites of the last block of 32 are never written
+        ref = D.apply(xi, out=D.new_internal().zero_(), dagger=True).clone()
         for tc in (1, 2, 3, 5):
             D.set_site_order(tc)
             assert D.kernel_config() == (2, 64, variant) and D.site_order() == tc
-            got = D.apply(xi, out=D.new_internal(), dagger=True)
+            got = D.apply(xi, out=D.new_internal().zero_(), dagger=True)
             assert torch.equal(got, ref), (variant, tc)
     with pytest.raises(dg.DiracError):
         D.set_site_order(6)
