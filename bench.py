@@ -2,7 +2,7 @@
 
 Default workload (one step = one sweep): Wilson D_W, 32^4 periodic lattice,
 Nc = 3, Nv = 12, FP32, kappa = 0.125, links exp(0.3 i H), Gaussian source,
-internal site-fastest layout, inputs resident in HBM.  Each step reads and
+internal blocked layout, inputs resident in HBM.  Each step reads and
 writes 2.7 GB, far more than the 129 MB L2, so no flush is needed between
 steps.  The JSON line reports model Gflop/s (1368 flop per site and
 right-hand side), the HBM roofline of the kernel, the end-to-end rate through
@@ -459,7 +459,7 @@ def main():
         "vs_baseline": None, "dtype": "f32" if w["prec"] != "f64" else "f64", "data": "synthetic",
         "config": {"workload": workload, "op": op, "storage": w["prec"], "lattice": list(w["L"]),
                    "Nc": 3, "Nv": w["Nv"], "kappa": w["mass"], "links": "exp(0.3 i H), H traceless Gaussian",
-                   "source": "complex Gaussian N(0,1)", "layout": "internal site-fastest SoA",
+                   "source": "complex Gaussian N(0,1)", "layout": "internal blocked SoA (blocks of 32 sites)",
                    "l2": "no flush: each step streams {:.2f} GB > 129 MB L2".format(bytes_step / 1e9),
                    "kernel": {"rhs_per_thread": cfg[0], "block": cfg[1], "variant": cfg[2],
                               "site_order_tchunk": site_order},

@@ -28,13 +28,13 @@
  *           staggered          [s][v][colour]        == the paper's suv(Nc,Nv,...)
  *   Canonical spinors are complex double for DIRAC_F64 handles and complex
  *   float for every other precision.
- * Internal layout (site-fastest structure of arrays, in the storage
- * precision; allocate with dirac_field_bytes, convert with dirac_pack /
- * dirac_unpack):
- *   spinor  [v][k][s] with k over 16-byte elements of one right-hand side
- *           (Wilson/Brillouin: 12 complex per site split into elements of
- *           2 complex (F32), 1 (F64) or 4 (BF16/F16); staggered: 3 elements
- *           of one complex each).
+ * Internal layout (blocked structure of arrays, in the storage precision;
+ * allocate with dirac_field_bytes, convert with dirac_pack / dirac_unpack):
+ *   spinor  [v][s/32][k][s%32] with k over the elements of one right-hand
+ *           side (Wilson/Brillouin: 12 complex per site split into 16-byte
+ *           elements of 2 complex (F32), 1 (F64) or 4 (BF16/F16); staggered:
+ *           3 elements of one complex each); the sites go in blocks of 32,
+ *           the last block padded, so a field holds ceil(vol / 32) * 32 sites.
  *
  * Pointers: unless a function says otherwise, spinor and field pointers are
  * DEVICE pointers owned by the caller, 16-byte aligned (else

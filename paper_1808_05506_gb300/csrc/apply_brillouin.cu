@@ -1,5 +1,5 @@
 // Brillouin D_B and D_B^+ sweeps (Sec. 5, Eqs. def_bril, def_der, def_lap at
-// c_SW = 0) on the internal site-fastest layout.  One thread owns one site
+// c_SW = 0) on the internal blocked layout.  One thread owns one site
 // and R right-hand sides and walks the 80 off-centre directions; each stored
 // link W (Tab. tab:off-axis) is loaded once per thread and applied to its R
 // spinors from registers.  The direction table sits in constant memory, read

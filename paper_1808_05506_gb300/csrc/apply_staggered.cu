@@ -1,5 +1,5 @@
 // Staggered D_S and D_S^+ sweeps (Sec. 3, plus a mass term) on the
-// internal site-fastest layout.  One thread owns one site and R right-hand
+// internal blocked layout.  One thread owns one site and R right-hand
 // sides: every link is loaded once per thread and applied to its R spinors
 // from registers, and every output element is written once.  Consecutive
 // blocks cover the right-hand-side groups of the same sites, so the other

@@ -1,16 +1,17 @@
 // Shared device-side building blocks of the Dirac kernels: storage types,
-// the internal site-fastest layouts, complex arithmetic, lattice geometry and
-// the chiral-basis spin projectors.
+// the internal blocked layouts, complex arithmetic, lattice geometry and the
+// chiral-basis spin projectors.
 //
-// Internal layouts (all site-fastest structure-of-arrays, one "element" is a
-// 4- to 16-byte vector so that a warp reading 32 consecutive sites issues one
-// coalesced load per element):
-//   spinor   [v][k][site]   k = 0..K-1 element of right-hand side v at a site;
-//                           Wilson/Brillouin: 12 complex (spin-major, colour-
-//                           minor) split into K = 12/CPV elements of CPV
-//                           complex each; staggered: 3 complex, K = 3, CPV = 1.
-//   links    [m][e][site]   m = mu (0..3) for V_mu, or one of the 40 stored
-//                           Brillouin directions; e = row*3 + col (9 complex).
+// Internal layouts (blocked structure-of-arrays, one "element" is a 4- to
+// 16-byte vector so that a warp reading 32 aligned sites issues one
+// coalesced load per element; blk_index gives the position):
+//   spinor   [v][site/32][k][site%32]   k = 0..K-1 element of right-hand side
+//                           v at a site; Wilson/Brillouin: 12 complex (spin-
+//                           major, colour-minor) split into K = 12/CPV
+//                           elements of CPV complex each; staggered: 3
+//                           complex, K = 3, CPV = 1.
+//   links    [m][site/32][e][site%32]   m = mu (0..3) for V_mu, or one of the
+//                           40 stored Brillouin directions; e = row*3 + col.
 // Site index s = x + Nx (y + Ny (z + Nz t)).
 #pragma once
 

@@ -1,4 +1,4 @@
-// Layout conversion (canonical <-> internal site-fastest layout) and the
+// Layout conversion (canonical <-> internal blocked layout) and the
 // Brillouin off-axis link build of Tab. tab:off-axis.
 #include "dirac_internal.h"
 
