@@ -132,6 +132,29 @@ def test_solve_batched_queue(dg, op, masses, prec):
         k += nv_list[i]
 
 
+@pytest.mark.parametrize("op,mass", [("wilson", 0.121), ("staggered", 0.1), ("brillouin", 0.08)])
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_solve_ragged_volume(dg, op, mass, prec):
+    """A volume that is not a multiple of 32 (3 x 4 x 2 x 5 = 120 sites): the
+    last block of the internal layout has 8 padding sites, which the solver's
+    vector kernels must see as zeros.  Single and batched solves."""
+    L = (3, 4, 2, 5)
+    V = links_for(prec, synth.gauge_links(L, 3, "near_identity", 410))
+    b = synth.spinor(L, 3, NS[op], 3, 411)
+    D = dg.Dirac(op, L, 3, mass, prec)
+    D.set_links(torch.from_numpy(V.astype(np.complex64 if prec != "f64" else np.complex128)).cuda())
+    x, res, st, status = D.solve(torch.from_numpy(b).cuda(), tol=1e-10, max_outer=40, max_inner=3000)
+    D.close()
+    assert status == dg.OK, (res, st)
+    true_res = oracle_residual(op, V, x.cpu().numpy(), b, m0_of(op, mass))
+    assert true_res.max() <= 1e-10, true_res
+    V, bs, xs, res, sys_stats, tot, status = _batched_case(dg, op, L, [2, 1, 3], [mass, mass * 1.01, mass * 0.99],
+                                                          prec, 4, 412)
+    assert status == dg.OK, (sys_stats, tot)
+    for b, x, m in zip(bs, xs, [mass, mass * 1.01, mass * 0.99]):
+        assert oracle_residual(op, V, x, b, m0_of(op, m)).max() <= 1e-10
+
+
 def test_solve_batched_matches_single(dg):
     """A batch of one system equals dirac_solve on it (same iterates up to the
     tolerance)."""
