@@ -246,7 +246,7 @@ def solve_times(dg, torch, L=(24, 24, 24, 48), Nv=12, m0=0.05, precs=("f32", "bf
 
 
 def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=("f32", "bf16", "f16"),
-                        rank=0, ws=1, dist=None):
+                        rank=0, ws=1, dist=None, precond=1):
     """Wilson systems D(kappa_i) x_i = b_i on one gauge field, Nv_i ~ U{1..24},
     kappa_i ~ U[0.120, 0.124], through dirac_solve_batched with `slots` resident
     right-hand-side columns, each precision to a true FP64 residual of 1e-10:
@@ -254,7 +254,8 @@ def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=(
     48 of the full configuration, so that the benchmark stays within minutes).
     With N ranks the systems are shared out (sharding.assign_systems, 4 * N
     systems in all: weak scaling) and each rank solves its own; the time is
-    the slowest rank's."""
+    the slowest rank's.  precond: 1 even-odd inner solves (the library's
+    default), 0 whole-lattice ones."""
     from paper_1808_05506_gb300 import sharding
     nsys = nsys * ws
     rng = np.random.default_rng(7)
@@ -272,6 +273,7 @@ def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=(
     out = {}
     for prec in precs:
         D = dg.Dirac("wilson", L, slots, 0.122, prec)
+        D.set_preconditioner(precond)
         D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
         D.autotune()
         torch.cuda.synchronize()
@@ -292,7 +294,7 @@ def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=(
                      "outer_max": max(s["outer_iterations"] for s in stats),
                      "all_converged": all(s["converged"] for s in stats), "kernel": list(D.kernel_config()),
                      "rank0_totals": {k: tot.get(k) for k in ("outer_iterations", "inner_iterations", "sweeps",
-                                                                "fp64_sweeps")}}
+                                                                "fp64_sweeps", "even_odd")}}
         D.close()
         del xs
         torch.cuda.empty_cache()
@@ -303,6 +305,8 @@ def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=(
     out["workload"] = "wilson_batched_solve_{}_{}sys_nv{}_{}slots".format("x".join(map(str, L)), nsys,
                                                                         "-".join(map(str, nvs)), slots)
     out["sharding"] = f"{ws} rank(s), systems per rank by assign_systems"
+    out["inner_solver"] = ("even-odd: CGLS on the Schur complement of the odd sites" if precond
+                           else "whole lattice: CGLS on D")
     del local_b
     torch.cuda.empty_cache()
     return out

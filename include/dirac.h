@@ -192,8 +192,10 @@ DIRAC_API dirac_status dirac_force(dirac_handle* h, void* F, const void* psi, co
 typedef struct {
     int outer_iterations;   /* refinement steps (inner solves) taken */
     int inner_iterations;   /* inner CGLS iterations summed over the refinement steps */
-    int sweeps;             /* storage-precision applications of D or D^+ */
+    int sweeps;             /* storage-precision applications of D or D^+ (with even-odd
+                               inner solves, each pair of half-lattice sweeps counts one) */
     int fp64_sweeps;        /* FP64 applications of D (outer residuals) */
+    int even_odd;           /* 1 if the inner solves took the even-odd Schur complement */
     double residual_max;    /* max over right-hand sides of |b - D x| / |b|, FP64 */
     double seconds;         /* host wall time of the call */
 } dirac_solve_stats;
@@ -206,6 +208,9 @@ typedef struct {
  * the residual of D e = r_hat) with fields in the handle's storage precision
  * and FP32 arithmetic (FP64 for DIRAC_F64 handles), to |r_hat - D e| <=
  * inner_tol |r_hat| or max_inner iterations, then updates x += |r| e in FP64.
+ * With even-odd preconditioning (dirac_set_preconditioner; on by default where
+ * it applies) the inner solve runs on the Schur complement of the odd sites
+ * instead (see there); the outer loop and its FP64 residual are the same.
  *   x            canonical FP64 device field; on entry the starting guess
  *                (resume = call again with the previous result)
  *   b            canonical FP64 device field, not aliasing x
@@ -274,6 +279,25 @@ DIRAC_API dirac_status dirac_solve_batched(dirac_handle* h, int nsys, const int*
  *     host threads) race on it: serialise them.
  * Requires dirac_set_links first.  Asynchronous on the handle's stream. */
 DIRAC_API dirac_status dirac_apply_static(dirac_handle* h, void* out, const void* in, int dagger);
+
+/* Preconditioning of the inner solves of dirac_solve and dirac_solve_batched
+ * (Sec. 4 names the even-odd decomposition as the next step of tuning).
+ *   mode 1 (default): even-odd where it applies -- Wilson and staggered
+ *          operators, every lattice extent even, and a nonzero diagonal
+ *          (4 + m0, or the staggered mass m) for every system.  With D = a + H
+ *          and H linking only sites of opposite parity, the inner solve of
+ *          D e = r takes the Schur complement S = a - H_oe H_eo / a on the odd
+ *          sites, S e_o = r_o - H_oe r_e / a (CGLS for Wilson; CG for
+ *          staggered, where S = m + H_eo^+ H_eo / m is hermitian and
+ *          definite), then e_e = (r_e - H_eo e_o) / a.  Its fields hold half
+ *          the sites; one application of S costs two half-lattice sweeps.
+ *   mode 0: the inner solve on the whole lattice (CGLS on D).
+ * Elsewhere (Brillouin: its 2- and 4-hop terms link sites of equal parity; an
+ * odd extent; a zero mass) mode 1 falls back to mode 0.  The stats field
+ * even_odd reports which one ran.  Errors: DIRAC_ERR_INVALID_ARG for another
+ * mode. */
+DIRAC_API dirac_status dirac_set_preconditioner(dirac_handle* h, int mode);
+DIRAC_API dirac_status dirac_get_preconditioner(const dirac_handle* h, int* mode);
 
 /* Kernel configuration (the launch shape of the sweeps):
  *   R        right-hand sides per thread (1..4 for Wilson and Brillouin; 1, 2, 4

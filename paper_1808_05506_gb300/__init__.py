@@ -69,6 +69,8 @@ SIGNATURES = {
     "dirac_set_site_order": (I, [P, I]),
     "dirac_apply_host": (I, [P, P, P, I]),
     "dirac_get_site_order": (I, [P, ctypes.POINTER(I)]),
+    "dirac_set_preconditioner": (I, [P, I]),
+    "dirac_get_preconditioner": (I, [P, ctypes.POINTER(I)]),
     "dirac_last_error": (ctypes.c_char_p, [P]),
     "dirac_solve": (I, [P, P, P, D, I, I, D, P, P]),
     "dirac_force": (I, [P, P, P, P, I]),
@@ -88,7 +90,7 @@ class SystemStats(ctypes.Structure):
 class SolveStats(ctypes.Structure):
     """dirac_solve_stats of include/dirac.h."""
     _fields_ = [("outer_iterations", ctypes.c_int), ("inner_iterations", ctypes.c_int),
-                ("sweeps", ctypes.c_int), ("fp64_sweeps", ctypes.c_int),
+                ("sweeps", ctypes.c_int), ("fp64_sweeps", ctypes.c_int), ("even_odd", ctypes.c_int),
                 ("residual_max", ctypes.c_double), ("seconds", ctypes.c_double)]
 
     def as_dict(self):
@@ -397,6 +399,16 @@ class Dirac:
     def site_order(self) -> int:
         t = I()
         check(lib().dirac_get_site_order(self.h, ctypes.byref(t)), self.h, "dirac_get_site_order")
+        return t.value
+
+    def set_preconditioner(self, mode: int):
+        """Inner solves: 1 even-odd Schur complement where it applies, 0 whole lattice;
+        see dirac_set_preconditioner."""
+        check(lib().dirac_set_preconditioner(self.h, mode), self.h, "dirac_set_preconditioner")
+
+    def preconditioner(self) -> int:
+        t = I()
+        check(lib().dirac_get_preconditioner(self.h, ctypes.byref(t)), self.h, "dirac_get_preconditioner")
         return t.value
 
     def autotune(self, force: bool = False):

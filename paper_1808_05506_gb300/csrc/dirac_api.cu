@@ -464,6 +464,22 @@ dirac_status dirac_get_site_order(const dirac_handle* h, int* tchunk)
     return DIRAC_OK;
 }
 
+dirac_status dirac_set_preconditioner(dirac_handle* h, int mode)
+{
+    if (!h) return DIRAC_ERR_INVALID_ARG;
+    if (mode != 0 && mode != 1)
+        return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_set_preconditioner: mode %d is not 0 or 1", mode);
+    h->precond = mode;
+    return DIRAC_OK;
+}
+
+dirac_status dirac_get_preconditioner(const dirac_handle* h, int* mode)
+{
+    if (!h || !mode) return DIRAC_ERR_INVALID_ARG;
+    *mode = h->precond;
+    return DIRAC_OK;
+}
+
 dirac_status dirac_get_kernel_config(const dirac_handle* h, int* R, int* block, int* variant)
 {
     if (!h || !R || !block || !variant) return DIRAC_ERR_INVALID_ARG;

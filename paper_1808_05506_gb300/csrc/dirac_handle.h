@@ -18,6 +18,8 @@ struct dirac_handle {
     cudaStream_t stream = nullptr;
     int device = 0;
     dirac::LaunchCfg cfg{1, 128, dirac::V_DIRECT};
+    int precond = 1;          // inner solves: 1 even-odd where it applies, 0 whole lattice
+    dirac::LaunchCfg eo_cfg{0, 0, 0, 0};   // launch shape of the even-odd sweeps (R = 0: not tuned)
 
     void* links = nullptr;    // storage-precision links [m][9][site] (m = mu, or 40 stored W)
     void* links64 = nullptr;  // FP64 V_mu [4][9][site]

@@ -25,6 +25,15 @@
 // diagonal (the mass of its system).  A queue admits the columns of the
 // systems into free slots and writes each column back as soon as it
 // converges.
+// Even-odd inner solves (Wilson and staggered, every extent even, nonzero
+// diagonal; dirac_eo.cuh): r_hat is split into its even and odd half fields,
+// the inner iteration runs on the Schur complement S = a - H_oe H_eo / a of
+// the odd sites (CGLS for Wilson; plain CG for staggered, whose S = m +
+// H_eo^+ H_eo / m is hermitian and definite), and the even half follows as
+// e_e = (r_e - H_eo e_o) / a.  The residual of D e = r_hat is then the Schur
+// residual on the odd sites (zero on the even ones), so the stopping test and
+// the FP64 outer loop are unchanged.  Each application of S is two
+// half-lattice sweeps.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -34,6 +43,7 @@
 #include <vector>
 
 #include "dirac_blas.h"
+#include "dirac_eo.cuh"
 #include "dirac_handle.h"
 
 using namespace dirac;
@@ -68,6 +78,22 @@ __global__ void k_cgls_alpha(int Nv, const double* gamma, const double* delta, c
     alpha[v] = a;
 }
 
+// the same for CG on a hermitian definite operator of either sign: delta =
+// <p, S p> may be negative, only zero or non-finite values are a breakdown
+__global__ void k_cg_alpha(int Nv, const double* gamma, const double* delta, const int* active, double* alpha,
+                           int* breakdown)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= Nv) return;
+    double a = 0.0;
+    if (active[v]) {
+        const double d = delta[v];
+        if (d == 0.0 || !isfinite(d) || !isfinite(gamma[v])) *breakdown = 1;
+        else a = gamma[v] / d;
+    }
+    alpha[v] = a;
+}
+
 // beta = gamma' / gamma for active ones (else 0); gamma <- gamma'
 __global__ void k_cgls_beta(int Nv, const double* gnew, double* gamma, const int* active, double* beta)
 {
@@ -97,21 +123,36 @@ __global__ void k_cgls_mask(int Nv, const double* rr, const double* rr0, const d
     if (threadIdx.x == 0) *nactive = cnt;
 }
 
+// coefficient sets (alpha_v, beta_v) of the even-odd sweeps out = alpha in2 + beta H in
+enum { EO_HOP = 0,   // (0, 1): H_eo p
+       EO_S = 1,     // (a, -1/a): S p = a p - H_oe (H_eo p) / a
+       EO_RHS = 2,   // (1, -1/a): r_o - H_oe r_e / a
+       EO_REC = 3,   // (1/a, -1/a): e_e = (r_e - H_eo e_o) / a
+       EO_NSETS = 4 };
+
 struct SolverWS {
     int W = 0;
     int prec = 0;
+    bool eo = false;                                          // even-odd inner solve (half fields)
+    bool cg = false;                                          // CG on the hermitian Schur complement
     void *b64 = nullptr, *x64 = nullptr, *r64 = nullptr;     // FP64 internal fields
-    void *e = nullptr, *r = nullptr, *s = nullptr, *p = nullptr, *t = nullptr;   // storage precision
+    // storage precision: whole-lattice fields, or odd half fields when eo
+    void *e = nullptr, *r = nullptr, *s = nullptr, *p = nullptr, *t = nullptr;
+    void *tmp = nullptr, *re = nullptr, *ro = nullptr;        // eo: even scratch, r_hat halves
+    size_t n = 0;                                             // complex numbers per rhs of the inner fields
     double* part = nullptr;                                   // reduction partials
     double* scal = nullptr;                                   // per-rhs scalar slots
     int* iflags = nullptr;                                    // active[W], breakdown, nactive
-    double *bb, *rr64, *scale, *coef, *rr0, *rr, *gamma, *gnew, *delta, *alpha, *beta, *diag_v, *itol2;
+    double *bb, *rr64, *scale, *coef, *rr0, *rr, *gamma, *gnew, *delta, *alpha, *beta, *diag_v, *dim, *itol2;
     float* diag_vf;                                           // diag_v in FP32 for the FP32-arithmetic sweeps
+    void* eoc = nullptr;                                      // eo: EO_NSETS x (alpha[W], beta[W]), arithmetic type
+    std::vector<double> dh;                                   // host copy of the per-slot diagonal
     cudaStream_t cs = nullptr;          // private stream: graphs cannot be captured on the legacy stream
     cudaEvent_t ev = nullptr;
     cudaGraphExec_t gexec = nullptr;
     // what the graph was captured with
     LaunchCfg g_cfg{0, 0, 0};
+    LaunchCfg g_eo_cfg{0, 0, 0};
     const void* g_links = nullptr;
     const double* g_diag = nullptr;
 };
@@ -125,7 +166,7 @@ void dirac_handle::free_solver_workspace()
     if (w->gexec) cudaGraphExecDestroy(w->gexec);
     if (w->ev) cudaEventDestroy(w->ev);
     if (w->cs) cudaStreamDestroy(w->cs);
-    void** ptrs[] = {&w->b64, &w->x64, &w->r64, &w->e, &w->r, &w->s, &w->p, &w->t};
+    void** ptrs[] = {&w->b64, &w->x64, &w->r64, &w->e, &w->r, &w->s, &w->p, &w->t, &w->tmp, &w->re, &w->ro};
     for (void** q : ptrs) release(*q);
     void* pp = w->part;
     release(pp);
@@ -139,10 +180,10 @@ void dirac_handle::free_solver_workspace()
     sw_nv = 0;
 }
 
-static dirac_status ensure_solver_ws(dirac_handle* h, SolverWS** out)
+static dirac_status ensure_solver_ws(dirac_handle* h, bool eo, SolverWS** out)
 {
     SolverWS* w = (SolverWS*)h->sw;
-    if (w && w->W == h->Nv && w->prec == h->prec) {
+    if (w && w->W == h->Nv && w->prec == h->prec && w->eo == eo) {
         *out = w;
         return DIRAC_OK;
     }
@@ -151,74 +192,149 @@ static dirac_status ensure_solver_ws(dirac_handle* h, SolverWS** out)
     h->sw = w;
     w->W = h->Nv;
     w->prec = h->prec;
-    const size_t n = (size_t)nsc_of(h->op) * nblk_of((size_t)h->g.vol) * 32;
-    const size_t f64 = n * h->Nv * 16, fp = n * h->Nv * cbytes(h->prec);
+    w->eo = eo;
+    w->cg = eo && h->op == OP_STAGGERED;
+    const size_t nfull = (size_t)nsc_of(h->op) * nblk_of((size_t)h->g.vol) * 32;
+    w->n = eo ? eo_half_n(h->op, h->g.vol) : nfull;
+    const size_t f64 = nfull * h->Nv * 16, fp = w->n * h->Nv * cbytes(h->prec);
     dirac_status st;
     if ((st = h->alloc(&w->b64, f64, "solver b"))) return st;
     if ((st = h->alloc(&w->x64, f64, "solver x"))) return st;
     if ((st = h->alloc(&w->r64, f64, "solver r"))) return st;
-    void** inner[] = {&w->e, &w->r, &w->s, &w->p, &w->t};
-    for (void** q : inner)
-        if ((st = h->alloc(q, fp, "solver inner field"))) return st;
+    void** inner[] = {&w->e, &w->r, &w->s, &w->p, &w->t, &w->tmp, &w->re, &w->ro};
+    const int ninner = eo ? 8 : 5;
+    for (int i = 0; i < ninner; ++i)
+        if ((st = h->alloc(inner[i], fp, "solver inner field"))) return st;
     // the padding sites of the last block of 32 stay zero (the vector kernels
     // run over whole blocks; the sweeps and packs write only real sites)
     void** fields64[] = {&w->b64, &w->x64, &w->r64};
     for (void** q : fields64)
         if ((st = h->cuda(cudaMemset(*q, 0, f64), "solver field clear"))) return st;
-    for (void** q : inner)
-        if ((st = h->cuda(cudaMemset(*q, 0, fp), "solver field clear"))) return st;
+    for (int i = 0; i < ninner; ++i)
+        if ((st = h->cuda(cudaMemset(*inner[i], 0, fp), "solver field clear"))) return st;
     void* pp = nullptr;
-    if ((st = h->alloc(&pp, 2 * blas_partials(n, h->Nv) * sizeof(double), "solver partials"))) return st;
+    if ((st = h->alloc(&pp, 2 * blas_partials(nfull, h->Nv) * sizeof(double), "solver partials"))) return st;
     w->part = (double*)pp;
-    const int nslots = 12;
-    if ((st = h->alloc(&pp, ((size_t)nslots * h->Nv + 1 + ((size_t)h->Nv + 1) / 2) * sizeof(double), "solver scalars")))
-        return st;
+    const int nslots = 13;
+    const size_t nscal = (size_t)nslots * h->Nv + 1 + ((size_t)h->Nv + 1) / 2 + (size_t)EO_NSETS * 2 * h->Nv;
+    if ((st = h->alloc(&pp, nscal * sizeof(double), "solver scalars"))) return st;
     w->scal = (double*)pp;
-    double** slots[] = {&w->bb, &w->rr64, &w->scale, &w->coef, &w->rr0, &w->rr,
-                        &w->gamma, &w->gnew, &w->delta, &w->alpha, &w->beta, &w->diag_v};
+    double** slots[] = {&w->bb, &w->rr64, &w->scale, &w->coef, &w->rr0, &w->rr, &w->gamma,
+                        &w->gnew, &w->delta, &w->alpha, &w->beta, &w->diag_v, &w->dim};
     for (int i = 0; i < nslots; ++i) *slots[i] = w->scal + (size_t)i * h->Nv;
     w->itol2 = w->scal + (size_t)nslots * h->Nv;
     w->diag_vf = reinterpret_cast<float*>(w->scal + (size_t)nslots * h->Nv + 1);
+    w->eoc = w->scal + (size_t)nslots * h->Nv + 1 + ((size_t)h->Nv + 1) / 2;
     if ((st = h->alloc(&pp, ((size_t)h->Nv + 2) * sizeof(int), "solver flags"))) return st;
     w->iflags = (int*)pp;
     if ((st = h->cuda(cudaStreamCreateWithFlags(&w->cs, cudaStreamNonBlocking), "solver stream"))) return st;
     if ((st = h->cuda(cudaEventCreateWithFlags(&w->ev, cudaEventDisableTiming), "solver event"))) return st;
-    h->sw_bytes = 3 * f64 + 5 * fp;
+    h->sw_bytes = 3 * f64 + ninner * fp;
     h->sw_nv = h->Nv;
+    w->dh.assign(h->Nv, h->diag);
     *out = w;
     return DIRAC_OK;
 }
 
-// one CGLS iteration over all W right-hand sides (kernel launches only, so it
-// can be captured)
+// coefficient set k of the even-odd sweeps (device, arithmetic type of the inner fields)
+static const void* eo_coef(SolverWS* w, int k)
+{
+    const size_t esz = w->prec == P_F64 ? sizeof(double) : sizeof(float);
+    return (const char*)w->eoc + (size_t)k * 2 * w->W * esz;
+}
+
+// uploads the even-odd coefficient sets for the per-slot diagonal w->dh
+static dirac_status upload_eo_coef(dirac_handle* h, SolverWS* w)
+{
+    const int W = w->W;
+    std::vector<double> c((size_t)EO_NSETS * 2 * W);
+    for (int v = 0; v < W; ++v) {
+        const double a = w->dh[v];
+        const double al[EO_NSETS] = {0.0, a, 1.0, 1.0 / a};
+        const double be[EO_NSETS] = {1.0, -1.0 / a, -1.0 / a, -1.0 / a};
+        for (int k = 0; k < EO_NSETS; ++k) {
+            c[(size_t)k * 2 * W + v] = al[k];
+            c[(size_t)k * 2 * W + W + v] = be[k];
+        }
+    }
+    if (w->prec == P_F64)
+        return h->cuda(cudaMemcpyAsync(w->eoc, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                       h->stream), "solve: even-odd coefficients");
+    // pageable source: the copy completes before cudaMemcpyAsync returns, so c may go
+    std::vector<float> cf(c.begin(), c.end());
+    return h->cuda(cudaMemcpyAsync(w->eoc, cf.data(), cf.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream),
+                   "solve: even-odd coefficients");
+}
+
+// one even-odd sweep out = alpha in2 + beta H in (or H^+) on the sites of parity par
+static dirac_status eo_sweep(dirac_handle* h, SolverWS* w, bool dag, int par, void* out, const void* in,
+                             const void* in2, int set)
+{
+    LaunchCfg c = h->eo_cfg;
+    if (c.R == 0 || !eo_rhs_supported(h->op, w->prec, w->W, c.R))
+        c = eo_default_config(h->op, w->prec, w->W, h->g.L[3]);
+    const EoArgs a = make_eo_args(h->g, w->W, par, in, in2, out, h->links, eo_coef(w, set), c.order);
+    return h->cuda(launch_eo(h->op, w->prec, dag, a, c, h->stream), "solve: even-odd sweep");
+}
+
+// out = A in (or A^+ in), A the operator of the inner solve: D on the whole
+// lattice, or the Schur complement S on the odd half fields
+static dirac_status apply_inner(dirac_handle* h, SolverWS* w, bool dag, void* out, const void* in,
+                                const double* diag_v)
+{
+    if (!w->eo)
+        return h->run_apply(dag, out, in, w->W, h->diag, h->links, w->prec, h->cfg, diag_v, 0, 0,
+                            diag_v ? w->diag_vf : nullptr);
+    dirac_status st;
+    if ((st = eo_sweep(h, w, dag, 0, w->tmp, in, nullptr, EO_HOP))) return st;   // H_eo in
+    return eo_sweep(h, w, dag, 1, out, w->tmp, in, EO_S);                         // a in - H_oe (.) / a
+}
+
+// one inner iteration over all W right-hand sides (kernel launches only, so it
+// can be captured): CGLS on A, or CG when A is hermitian (w->cg)
 static dirac_status enqueue_iteration(dirac_handle* h, SolverWS* w, const double* diag_v)
 {
     const int W = w->W, P = w->prec;
-    const size_t n = (size_t)nsc_of(h->op) * nblk_of((size_t)h->g.vol) * 32;
+    const size_t n = w->n;
     cudaStream_t S = h->stream;
     int* active = w->iflags;
     int* breakdown = w->iflags + W;
     int* nactive = w->iflags + W + 1;
     const unsigned sb = (unsigned)((W + 127) / 128);
     dirac_status st;
-    const float* dvf = diag_v ? w->diag_vf : nullptr;
-    if ((st = h->run_apply(false, w->t, w->p, W, h->diag, h->links, P, h->cfg, diag_v, 0, 0, dvf))) return st;
-    if ((st = h->cuda(blas_norm2(P, n, W, w->t, w->part, w->delta, S), "solve: |t|"))) return st;
-    k_cgls_alpha<<<sb, 128, 0, S>>>(W, w->gamma, w->delta, active, w->alpha, breakdown);
-    if ((st = h->cuda(blas_cgls_step(P, n, W, w->alpha, w->e, w->p, w->r, w->t, w->part, w->rr, S), "solve: step")))
-        return st;
-    if ((st = h->run_apply(true, w->s, w->r, W, h->diag, h->links, P, h->cfg, diag_v, 0, 0, dvf))) return st;
-    if ((st = h->cuda(blas_norm2(P, n, W, w->s, w->part, w->gnew, S), "solve: |s|"))) return st;
-    k_cgls_beta<<<sb, 128, 0, S>>>(W, w->gnew, w->gamma, active, w->beta);
-    if ((st = h->cuda(blas_xpay(P, n, W, w->s, w->beta, w->p, S), "solve: p = s + beta p"))) return st;
+    if ((st = apply_inner(h, w, false, w->t, w->p, diag_v))) return st;
+    if (w->cg) {
+        // t = A p, delta = <p, t>, e += alpha p, r -= alpha t, gamma' = |r|^2, p = r + beta p
+        if ((st = h->cuda(blas_dot(P, n, W, w->p, w->t, w->part, w->delta, w->dim, S), "solve: <p, t>")))
+            return st;
+        k_cg_alpha<<<sb, 128, 0, S>>>(W, w->gamma, w->delta, active, w->alpha, breakdown);
+        if ((st = h->cuda(blas_cgls_step(P, n, W, w->alpha, w->e, w->p, w->r, w->t, w->part, w->rr, S),
+                          "solve: step")))
+            return st;
+        k_cgls_beta<<<sb, 128, 0, S>>>(W, w->rr, w->gamma, active, w->beta);
+        if ((st = h->cuda(blas_xpay(P, n, W, w->r, w->beta, w->p, S), "solve: p = r + beta p"))) return st;
+    } else {
+        if ((st = h->cuda(blas_norm2(P, n, W, w->t, w->part, w->delta, S), "solve: |t|"))) return st;
+        k_cgls_alpha<<<sb, 128, 0, S>>>(W, w->gamma, w->delta, active, w->alpha, breakdown);
+        if ((st = h->cuda(blas_cgls_step(P, n, W, w->alpha, w->e, w->p, w->r, w->t, w->part, w->rr, S),
+                          "solve: step")))
+            return st;
+        if ((st = apply_inner(h, w, true, w->s, w->r, diag_v))) return st;
+        if ((st = h->cuda(blas_norm2(P, n, W, w->s, w->part, w->gnew, S), "solve: |s|"))) return st;
+        k_cgls_beta<<<sb, 128, 0, S>>>(W, w->gnew, w->gamma, active, w->beta);
+        if ((st = h->cuda(blas_xpay(P, n, W, w->s, w->beta, w->p, S), "solve: p = s + beta p"))) return st;
+    }
     k_cgls_mask<<<1, 256, 0, S>>>(W, w->rr, w->rr0, w->itol2, active, nactive);
     return h->cuda(cudaGetLastError(), "solve: scalar kernels");
 }
 
 static dirac_status ensure_graph(dirac_handle* h, SolverWS* w, const double* diag_v)
 {
-    if (w->gexec && w->g_cfg.R == h->cfg.R && w->g_cfg.block == h->cfg.block && w->g_cfg.variant == h->cfg.variant &&
-        w->g_cfg.order == h->cfg.order && w->g_links == h->links && w->g_diag == diag_v)
+    auto same = [](const LaunchCfg& a, const LaunchCfg& b) {
+        return a.R == b.R && a.block == b.block && a.variant == b.variant && a.order == b.order;
+    };
+    if (w->gexec && same(w->g_cfg, h->cfg) && same(w->g_eo_cfg, h->eo_cfg) && w->g_links == h->links &&
+        w->g_diag == diag_v)
         return DIRAC_OK;
     if (w->gexec) {
         cudaGraphExecDestroy(w->gexec);
@@ -240,18 +356,22 @@ static dirac_status ensure_graph(dirac_handle* h, SolverWS* w, const double* dia
     cudaGraphDestroy(graph);
     if ((st = h->cuda(ce, "solve: graph instantiate"))) return st;
     w->g_cfg = h->cfg;
+    w->g_eo_cfg = h->eo_cfg;
     w->g_links = h->links;
     w->g_diag = diag_v;
     return DIRAC_OK;
 }
 
-// Inner CGLS on the active right-hand sides.  On entry: r holds r_hat, rr0 =
-// |r_hat|^2, active[] is set on the device.  e is zeroed here.
+// Inner solve on the active right-hand sides.  On entry: r holds the
+// right-hand side of the inner system (r_hat, or the Schur right-hand side),
+// rr0 = |r|^2, active[] is set on the device.  e is zeroed here.  Sweeps are
+// counted in whole-lattice equivalents (an application of S is two half
+// sweeps: one).
 static dirac_status inner_cgls(dirac_handle* h, SolverWS* w, const double* diag_v, int max_inner, double inner_tol,
                                dirac_solve_stats* S_, bool* breakdown_out)
 {
     const int W = w->W, P = w->prec;
-    const size_t n = (size_t)nsc_of(h->op) * nblk_of((size_t)h->g.vol) * 32;
+    const size_t n = w->n;
     cudaStream_t S = h->stream;
     dirac_status st;
     *breakdown_out = false;
@@ -260,13 +380,18 @@ static dirac_status inner_cgls(dirac_handle* h, SolverWS* w, const double* diag_
         return st;
     if ((st = h->cuda(cudaMemsetAsync(w->iflags + W, 0, 2 * sizeof(int), S), "solve: memset"))) return st;
     if ((st = h->cuda(cudaMemsetAsync(w->e, 0, n * W * cbytes(P), S), "solve: e = 0"))) return st;
-    // s = D^+ r, p = s, gamma = |s|^2
-    if ((st = h->run_apply(true, w->s, w->r, W, h->diag, h->links, P, h->cfg, diag_v, 0, 0,
-                           diag_v ? w->diag_vf : nullptr)))
-        return st;
-    S_->sweeps++;
-    if ((st = h->cuda(blas_scale_copy(P, n, W, w->s, nullptr, w->p, w->part, w->gamma, S), "solve: p = s")))
-        return st;
+    if (w->cg) {
+        // p = r, gamma = |r|^2
+        if ((st = h->cuda(blas_scale_copy(P, n, W, w->r, nullptr, w->p, w->part, w->gamma, S), "solve: p = r")))
+            return st;
+    } else {
+        // s = A^+ r, p = s, gamma = |s|^2
+        if ((st = apply_inner(h, w, true, w->s, w->r, diag_v))) return st;
+        S_->sweeps++;
+        if ((st = h->cuda(blas_scale_copy(P, n, W, w->s, nullptr, w->p, w->part, w->gamma, S), "solve: p = s")))
+            return st;
+    }
+    const int sweeps_per_it = w->cg ? 1 : 2;
     int done = 0, first = 1;
     while (done < max_inner) {
         const int chunk = std::min(GRAPH_ITERS, max_inner - done);
@@ -280,7 +405,7 @@ static dirac_status inner_cgls(dirac_handle* h, SolverWS* w, const double* diag_
         first = 0;
         done += chunk;
         S_->inner_iterations += chunk;
-        S_->sweeps += 2 * chunk;
+        S_->sweeps += sweeps_per_it * chunk;
         int flags[2] = {0, 0};   // breakdown, nactive
         if ((st = h->cuda(cudaMemcpyAsync(flags, w->iflags + W, 2 * sizeof(int), cudaMemcpyDeviceToHost, S),
                           "solve: copy")))
@@ -326,14 +451,27 @@ static dirac_status refine_step(dirac_handle* h, SolverWS* w, const double* diag
         return st;
     if ((st = h->cuda(cudaMemcpyAsync(w->iflags, act.data(), W * sizeof(int), cudaMemcpyHostToDevice, S), "copy")))
         return st;
-    if ((st = h->cuda(blas_convert(P_F64, P, nsc_of(h->op), h->g.vol, W, w->r64, w->scale, w->r, w->part, w->rr0, S),
-                      "solve: r_hat")))
-        return st;
     bool bd = false;
+    if (!w->eo) {
+        if ((st = h->cuda(blas_convert(P_F64, P, nsc_of(h->op), h->g.vol, W, w->r64, w->scale, w->r, w->part,
+                                       w->rr0, S), "solve: r_hat")))
+            return st;
+        if ((st = inner_cgls(h, w, diag_v, max_inner, inner_tol, S_, &bd))) return st;
+        // x += (|r| / sqrt(n)) e in FP64 (the update is kept even after a breakdown:
+        // the next FP64 residual decides)
+        return h->cuda(blas_axpy_to64(P, nsc_of(h->op), h->g.vol, W, w->coef, w->e, w->x64, S), "solve: x update");
+    }
+    // even-odd: r_hat -> (r_e, r_o); the Schur right-hand side r = r_o - H_oe r_e / a
+    if ((st = upload_eo_coef(h, w))) return st;
+    if ((st = h->cuda(eo_split(P, nsc_of(h->op), h->g, W, w->r64, w->scale, w->re, w->ro, S), "solve: r_hat")))
+        return st;
+    if ((st = eo_sweep(h, w, false, 1, w->r, w->re, w->ro, EO_RHS))) return st;
+    if ((st = h->cuda(blas_norm2(P, w->n, W, w->r, w->part, w->rr0, S), "solve: |r|"))) return st;
     if ((st = inner_cgls(h, w, diag_v, max_inner, inner_tol, S_, &bd))) return st;
-    // x += (|r| / sqrt(n)) e in FP64 (the update is kept even after a breakdown:
-    // the next FP64 residual decides)
-    return h->cuda(blas_axpy_to64(P, nsc_of(h->op), h->g.vol, W, w->coef, w->e, w->x64, S), "solve: x update");
+    // e_e = (r_e - H_eo e_o) / a, then x += (|r| / sqrt(n)) (e_e, e_o)
+    if ((st = eo_sweep(h, w, false, 0, w->tmp, w->e, w->re, EO_REC))) return st;
+    S_->sweeps++;   // the two half sweeps around the inner solve
+    return h->cuda(eo_axpy_to64(P, nsc_of(h->op), h->g, W, w->coef, w->tmp, w->e, w->x64, S), "solve: x update");
 }
 
 // r64 = b64 - D x64 in FP64; rr64 (host) = |r|^2 per slot
@@ -377,6 +515,19 @@ struct OnPrivateStream {
     }
 };
 
+// whether the inner solves take the even-odd Schur complement: Wilson or
+// staggered, every extent even (so that the hopping term only links opposite
+// parities), a nonzero diagonal for every system, and not switched off
+static bool use_even_odd(const dirac_handle* h, const double* diag, int ndiag)
+{
+    if (h->precond == 0 || (h->op != OP_WILSON && h->op != OP_STAGGERED)) return false;
+    for (int mu = 0; mu < 4; ++mu)
+        if (h->g.L[mu] % 2 != 0) return false;
+    for (int i = 0; i < ndiag; ++i)
+        if (!(diag[i] != 0.0) || !std::isfinite(diag[i])) return false;
+    return true;
+}
+
 static dirac_status check_solver_args(dirac_handle* h, double tol, int max_outer, int max_inner, double inner_tol,
                                       const char* name)
 {
@@ -401,7 +552,8 @@ extern "C" DIRAC_API dirac_status dirac_solve(dirac_handle* h, void* x, const vo
         return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_solve: x and b must be device pointers");
     if (h->op == OP_BRILLOUIN && (st = h->build_W64())) return st;
     SolverWS* w;
-    if ((st = ensure_solver_ws(h, &w))) return st;
+    if ((st = ensure_solver_ws(h, use_even_odd(h, &h->diag, 1), &w))) return st;
+    w->dh.assign(h->Nv, h->diag);
     OnPrivateStream guard(h, w);
     const int Nv = h->Nv, nsc = nsc_of(h->op);
     const size_t n = (size_t)nsc * nblk_of((size_t)h->g.vol) * 32;
@@ -443,6 +595,7 @@ extern "C" DIRAC_API dirac_status dirac_solve(dirac_handle* h, void* x, const vo
         if ((st = refine_step(h, w, nullptr, act, rr64, max_inner, inner_tol, &S_))) return st;
     }
     S_.outer_iterations = outer;
+    S_.even_odd = w->eo ? 1 : 0;
     CK(launch_unpack_spinor(P_F64, nsc, h->g, Nv, w->x64, x, true, S), "solve: unpack x");
     CK(cudaStreamSynchronize(S), "solve: sync");
 #undef CK
@@ -483,8 +636,10 @@ extern "C" DIRAC_API dirac_status dirac_solve_batched(dirac_handle* h, int nsys,
                                                   "pointers", i);
     }
     if (h->op == OP_BRILLOUIN && (st = h->build_W64())) return st;
+    std::vector<double> sys_diag(nsys);
+    for (int i = 0; i < nsys; ++i) sys_diag[i] = h->diag_of(mass_i[i]);
     SolverWS* w;
-    if ((st = ensure_solver_ws(h, &w))) return st;
+    if ((st = ensure_solver_ws(h, use_even_odd(h, sys_diag.data(), nsys), &w))) return st;
     OnPrivateStream guard(h, w);
     const int W = w->W, nsc = nsc_of(h->op);
     const size_t n = (size_t)nsc * nblk_of((size_t)h->g.vol) * 32;
@@ -545,6 +700,7 @@ extern "C" DIRAC_API dirac_status dirac_solve_batched(dirac_handle* h, int nsys,
         for (int v = 0; v < W; ++v) occupied = occupied || slot_sys[v] >= 0;
         if (!occupied) break;
         if (admitted) {
+            w->dh = diag;
             CK(cudaMemcpyAsync(w->diag_v, diag.data(), W * sizeof(double), cudaMemcpyHostToDevice, S), "copy");
             diagf.assign(diag.begin(), diag.end());
             CK(cudaMemcpyAsync(w->diag_vf, diagf.data(), W * sizeof(float), cudaMemcpyHostToDevice, S), "copy");
@@ -601,6 +757,7 @@ extern "C" DIRAC_API dirac_status dirac_solve_batched(dirac_handle* h, int nsys,
     if (rel_residual)
         for (size_t k = 0; k < col_base[nsys]; ++k) rel_residual[k] = res_col[k];
     S_.residual_max = rmax;
+    S_.even_odd = w->eo ? 1 : 0;
     S_.seconds = std::chrono::duration<double>(clk::now() - t0).count();
     if (stats) *stats = S_;
     if (any_breakdown) return h->fail(DIRAC_BREAKDOWN, "dirac_solve_batched: non-finite residual");

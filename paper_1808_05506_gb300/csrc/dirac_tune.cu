@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "dirac_eo.cuh"
 #include "dirac_handle.h"
 
 using namespace dirac;
@@ -69,6 +70,92 @@ static void cache_store(const std::string& key, int R, int B, int Pp, int T, dou
     if (!f) return;
     fprintf(f, "%s R%d B%d P%d T%d %.6f\n", key.c_str(), R, B, Pp, T, ms);
     fclose(f);
+}
+
+static bool trace_tune()
+{
+    const char* tr = getenv("DIRAC_TRACE");
+    return tr && *tr && *tr != '0';
+}
+
+// The even-odd sweep of the inner solves (dirac_eo.cuh), when the handle's
+// operator and lattice allow it: R in {1, 2, 4} (those built for Nv), 32, 64
+// or 128 half sites per block, lexicographic or t-chunked site order; timed
+// as the second sweep of an application of the Schur complement (both input
+// fields read).  Kept in h->eo_cfg and in the cache under "eo <key>".
+static dirac_status tune_even_odd(dirac_handle* h, int force)
+{
+    if ((h->op != OP_WILSON && h->op != OP_STAGGERED) || h->g.L[0] % 2 || h->g.L[1] % 2 || h->g.L[2] % 2 ||
+        h->g.L[3] % 2)
+        return DIRAC_OK;
+    const std::string key = "eo " + tune_key(h);
+    int R = 0, B = 0, Pp = 0, Tc = 0;
+    double best = 0.0;
+    if (!force && cache_lookup(key, &R, &B, &Pp, &Tc, &best) && eo_rhs_supported(h->op, h->prec, h->Nv, R) &&
+        (B == 32 || B == 64 || B == 128) && Tc >= 0 && Tc <= h->g.L[3]) {
+        h->eo_cfg = LaunchCfg{R, B, 0, Tc};
+        return DIRAC_OK;
+    }
+    dirac_status st;
+    if ((st = h->ensure_workspace())) return st;
+    // ws_in: both inputs (a half field fits a whole-lattice one); ws_out: the output
+    if ((st = h->cuda(cudaMemsetAsync(h->ws_in, 0, h->field_bytes_internal(h->Nv), h->stream), "autotune")))
+        return st;
+    void* coef = nullptr;
+    const size_t esz = h->prec == P_F64 ? sizeof(double) : sizeof(float);
+    if ((st = h->alloc(&coef, 2 * (size_t)h->Nv * esz, "autotune coefficients"))) return st;
+    if ((st = h->cuda(cudaMemsetAsync(coef, 0, 2 * (size_t)h->Nv * esz, h->stream), "autotune"))) {
+        h->release(coef);
+        return st;
+    }
+    cudaEvent_t e0, e1;
+    if ((st = h->cuda(cudaEventCreate(&e0), "autotune"))) {
+        h->release(coef);
+        return st;
+    }
+    if ((st = h->cuda(cudaEventCreate(&e1), "autotune"))) {
+        cudaEventDestroy(e0);
+        h->release(coef);
+        return st;
+    }
+    best = 1e30;
+    LaunchCfg win = eo_default_config(h->op, h->prec, h->Nv, h->g.L[3]);
+    const int Rs[] = {1, 2, 4}, blocks[] = {32, 64, 128};
+    for (int r : Rs) {
+        if (!eo_rhs_supported(h->op, h->prec, h->Nv, r)) continue;
+        for (int b : blocks)
+            for (int oi = 0; oi < 2 && st == DIRAC_OK; ++oi) {
+                const LaunchCfg c{r, b, 0, oi == 0 ? 0 : std::min(8, h->g.L[3])};
+                const EoArgs a = make_eo_args(h->g, h->Nv, 1, h->ws_in, h->ws_in, h->ws_out, h->links, coef, c.order);
+                std::vector<float> t;
+                for (int rep = 0; rep < 7 && st == DIRAC_OK; ++rep) {
+                    cudaEventRecord(e0, h->stream);
+                    st = h->cuda(launch_eo(h->op, h->prec, false, a, c, h->stream), "autotune: even-odd sweep");
+                    cudaEventRecord(e1, h->stream);
+                    if (!st) st = h->cuda(cudaEventSynchronize(e1), "autotune");
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep >= 2) t.push_back(ms);
+                }
+                if (st) break;
+                std::sort(t.begin(), t.end());
+                const double med = t[t.size() / 2];
+                if (trace_tune())
+                    fprintf(stderr, "[dirac] autotune %s R=%d block=%d order=%d: %.4f ms\n", key.c_str(), r, b,
+                            c.order, med);
+                if (med < best) {
+                    best = med;
+                    win = c;
+                }
+            }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->release(coef);
+    if (st) return st;
+    h->eo_cfg = win;
+    cache_store(key, win.R, win.block, 0, win.order, best);
+    return DIRAC_OK;
 }
 
 extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int* R_out, int* block_out,
@@ -154,6 +241,8 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
         h->cfg = win;
         cache_store(key, win.R, win.block, win.variant, win.order, best);
     }
+    dirac_status est = tune_even_odd(h, force);
+    if (est) return est;
     if (R_out) *R_out = h->cfg.R;
     if (block_out) *block_out = h->cfg.block;
     if (variant_out) *variant_out = h->cfg.variant;

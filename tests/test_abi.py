@@ -62,6 +62,8 @@ def test_create_validation(dg):
 
 def test_null_handle_calls(dg):
     assert dg.dirac_apply(None, None, None, 0) == dg.ERR_INVALID_ARG
+    assert dg.dirac_set_preconditioner(None, 1) == dg.ERR_INVALID_ARG
+    assert dg.dirac_get_preconditioner(None, None) == dg.ERR_INVALID_ARG
     assert dg.dirac_set_links(None, None, 0, 0) == dg.ERR_INVALID_ARG
     assert dg.dirac_destroy(None) == dg.OK
 
@@ -152,13 +154,16 @@ def test_binding_calls_match_the_c_signatures(dg, monkeypatch):
     D.kernel_config()
     D.set_site_order(8)
     D.site_order()
+    D.set_preconditioner(0)
+    D.preconditioner()
     D.autotune()
     D.solve(x.to(torch.complex128), x0=x.to(torch.complex128))
     D.solve_batched([x.to(torch.complex128)] * 2, [0.12, 0.121])
     D.close()
     for name in ("dirac_set_links", "dirac_apply", "dirac_apply_dagger", "dirac_force", "dirac_solve",
                  "dirac_set_kernel_config", "dirac_get_kernel_config", "dirac_autotune", "dirac_destroy",
-                 "dirac_solve_batched", "dirac_set_site_order", "dirac_get_site_order", "dirac_apply_host"):
+                 "dirac_solve_batched", "dirac_set_site_order", "dirac_get_site_order", "dirac_apply_host",
+                 "dirac_set_preconditioner", "dirac_get_preconditioner"):
         assert name in calls, name
 
 

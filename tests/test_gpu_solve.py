@@ -68,6 +68,38 @@ def test_solve_small_vs_dense_lu(dg, op, mass, prec):
     assert np.linalg.norm(xg - xl) / np.linalg.norm(xl) <= cond * 1e-10
 
 
+@pytest.mark.parametrize("op,mass", [("wilson", 0.122), ("staggered", 0.08), ("staggered", -0.08)])
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_solve_even_odd_vs_whole_lattice(dg, op, mass, prec):
+    """The even-odd inner solve (Schur complement of the odd sites: CGLS for
+    Wilson, CG for staggered, including a negative staggered mass, where the
+    Schur complement is negative definite) and the whole-lattice one both
+    reach the oracle-checked FP64 residual 1e-10 and agree on x within the
+    tolerance; with FP32 / FP64 inner arithmetic the even-odd one needs fewer
+    sweeps."""
+    L, Nv = (4, 4, 4, 8), 4
+    V = links_for(prec, synth.gauge_links(L, 3, "near_identity", 330))
+    b = synth.spinor(L, Nv, NS[op], 3, 331)
+    D = dg.Dirac(op, L, Nv, mass, prec)
+    D.set_links(torch.from_numpy(V.astype(np.complex64 if prec != "f64" else np.complex128)).cuda())
+    assert D.preconditioner() == 1   # the default
+    out = {}
+    for precond in (1, 0):
+        D.set_preconditioner(precond)
+        x, res, st, status = D.solve(torch.from_numpy(b).cuda(), tol=1e-10, max_outer=40, max_inner=3000)
+        assert status == dg.OK, (precond, res, st)
+        assert st["even_odd"] == precond
+        x = x.cpu().numpy()
+        true_res = oracle_residual(op, V, x, b, m0_of(op, mass))
+        assert true_res.max() <= 1e-10, (precond, true_res)
+        out[precond] = (x, st)
+    D.close()
+    x1, x0 = out[1][0], out[0][0]
+    assert np.linalg.norm(x1 - x0) / np.linalg.norm(x0) < 1e-7
+    if prec in ("f32", "f64"):
+        assert out[1][1]["sweeps"] < out[0][1]["sweeps"], (out[1][1], out[0][1])
+
+
 def test_solve_resume_and_zero_rhs(dg):
     """x0 = the solution: no refinement step is taken; a zero right-hand side
     converges at once; the result does not depend on the other columns."""
@@ -100,10 +132,11 @@ def test_solve_not_converged_status(dg):
     D.close()
 
 
-def _batched_case(dg, op, L, nv_list, masses, prec, window, seed, tol=1e-10):
+def _batched_case(dg, op, L, nv_list, masses, prec, window, seed, tol=1e-10, precond=1):
     V = links_for(prec, synth.gauge_links(L, 3, "near_identity", seed))
     bs = [synth.spinor(L, nv, NS[op], 3, seed + 1 + i) for i, nv in enumerate(nv_list)]
     D = dg.Dirac(op, L, window, masses[0], prec)
+    D.set_preconditioner(precond)
     D.set_links(torch.from_numpy(V.astype(np.complex64 if prec != "f64" else np.complex128)).cuda())
     xs, res, sys_stats, tot, status = D.solve_batched([torch.from_numpy(b).cuda() for b in bs], masses, tol=tol,
                                                       max_outer=40, max_inner=4000)
@@ -115,14 +148,18 @@ def _batched_case(dg, op, L, nv_list, masses, prec, window, seed, tol=1e-10):
                                        ("staggered", [0.05, 0.11, 0.2, 0.08, 0.3]),
                                        ("brillouin", [0.05, 0.1, 0.2, 0.07, 0.3])])
 @pytest.mark.parametrize("prec", ["bf16", "f32"])
-def test_solve_batched_queue(dg, op, masses, prec):
+@pytest.mark.parametrize("precond", [1, 0])
+def test_solve_batched_queue(dg, op, masses, prec, precond):
     """Five systems with uneven Nv and masses through a window of 4 slots
     (columns are admitted and retired while others are still iterating);
-    every column's true FP64 residual, re-evaluated by the oracle, is <= 1e-10."""
+    every column's true FP64 residual, re-evaluated by the oracle, is <= 1e-10.
+    Both inner solvers: even-odd (Wilson, staggered) and whole lattice."""
     L = (4, 4, 2, 4)
     nv_list = [1, 3, 2, 4, 1]
-    V, bs, xs, res, sys_stats, tot, status = _batched_case(dg, op, L, nv_list, masses, prec, 4, 400)
+    V, bs, xs, res, sys_stats, tot, status = _batched_case(dg, op, L, nv_list, masses, prec, 4, 400,
+                                                          precond=precond)
     assert status == dg.OK, (sys_stats, tot)
+    assert tot["even_odd"] == (1 if precond and op != "brillouin" else 0)
     k = 0
     for i, (b, x, m) in enumerate(zip(bs, xs, masses)):
         true_res = oracle_residual(op, V, x, b, m0_of(op, m))
@@ -146,11 +183,13 @@ def test_solve_ragged_volume(dg, op, mass, prec):
     x, res, st, status = D.solve(torch.from_numpy(b).cuda(), tol=1e-10, max_outer=40, max_inner=3000)
     D.close()
     assert status == dg.OK, (res, st)
+    assert st["even_odd"] == 0   # odd extents: the whole-lattice inner solve
     true_res = oracle_residual(op, V, x.cpu().numpy(), b, m0_of(op, mass))
     assert true_res.max() <= 1e-10, true_res
     V, bs, xs, res, sys_stats, tot, status = _batched_case(dg, op, L, [2, 1, 3], [mass, mass * 1.01, mass * 0.99],
                                                           prec, 4, 412)
     assert status == dg.OK, (sys_stats, tot)
+    assert tot["even_odd"] == 0
     for b, x, m in zip(bs, xs, [mass, mass * 1.01, mass * 0.99]):
         assert oracle_residual(op, V, x, b, m0_of(op, m)).max() <= 1e-10
 
