@@ -504,6 +504,8 @@ def main():
     if not args.no_solve and not args.no_extra:
         line["solve"] = solve_times(dg, torch)
         line["batched_solve"] = batched_solve_times(dg, torch, rank=rank, ws=ws, dist=dist)
+        # the same systems with the whole-lattice inner solver, for comparison
+        line["batched_solve_whole_lattice"] = batched_solve_times(dg, torch, rank=rank, ws=ws, dist=dist, precond=0)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_rate(w, inputs=(V, psi))
     if rank == 0:

@@ -196,6 +196,7 @@ typedef struct {
                                inner solves, each pair of half-lattice sweeps counts one) */
     int fp64_sweeps;        /* FP64 applications of D (outer residuals) */
     int even_odd;           /* 1 if the inner solves took the even-odd Schur complement */
+    int df_residual;        /* 1 if the outer residuals ran in double-float arithmetic */
     double residual_max;    /* max over right-hand sides of |b - D x| / |b|, FP64 */
     double seconds;         /* host wall time of the call */
 } dirac_solve_stats;
@@ -298,6 +299,23 @@ DIRAC_API dirac_status dirac_apply_static(dirac_handle* h, void* out, const void
  * mode. */
 DIRAC_API dirac_status dirac_set_preconditioner(dirac_handle* h, int mode);
 DIRAC_API dirac_status dirac_get_preconditioner(const dirac_handle* h, int* mode);
+
+/* Arithmetic of the outer residual r = b - D x of dirac_solve and
+ * dirac_solve_batched (the FP64 step of the defect correction).
+ *   mode 0: FP64 links, fields and arithmetic (the default of DIRAC_F64 handles).
+ *   mode 1: the same FP64 links and fields, with the sweep D x in double-float
+ *           arithmetic -- each value an unevaluated sum of two FP32 numbers,
+ *           48-bit significand, relative precision about 4e-15 -- and b - D x
+ *           and the norms in FP64 (the default of the other handles).  FP64
+ *           arithmetic runs at a small fraction of the FP32 rate on this GPU,
+ *           so this sweep is several times faster, and it resolves
+ *           |r| / |b| well below 1e-10.
+ * Mode 1 needs values within FP32's exponent range: a call falls back to
+ * mode 0 when a right-hand side's mean square |b|^2 / n lies outside
+ * (1e-36, 1e36).  The stats field df_residual reports which one ran.
+ * Errors: DIRAC_ERR_INVALID_ARG for another mode. */
+DIRAC_API dirac_status dirac_set_residual_arithmetic(dirac_handle* h, int mode);
+DIRAC_API dirac_status dirac_get_residual_arithmetic(const dirac_handle* h, int* mode);
 
 /* Kernel configuration (the launch shape of the sweeps):
  *   R        right-hand sides per thread (1..4 for Wilson and Brillouin; 1, 2, 4

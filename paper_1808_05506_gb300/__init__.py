@@ -70,6 +70,8 @@ SIGNATURES = {
     "dirac_apply_host": (I, [P, P, P, I]),
     "dirac_get_site_order": (I, [P, ctypes.POINTER(I)]),
     "dirac_set_preconditioner": (I, [P, I]),
+    "dirac_set_residual_arithmetic": (I, [P, I]),
+    "dirac_get_residual_arithmetic": (I, [P, ctypes.POINTER(I)]),
     "dirac_get_preconditioner": (I, [P, ctypes.POINTER(I)]),
     "dirac_last_error": (ctypes.c_char_p, [P]),
     "dirac_solve": (I, [P, P, P, D, I, I, D, P, P]),
@@ -91,6 +93,7 @@ class SolveStats(ctypes.Structure):
     """dirac_solve_stats of include/dirac.h."""
     _fields_ = [("outer_iterations", ctypes.c_int), ("inner_iterations", ctypes.c_int),
                 ("sweeps", ctypes.c_int), ("fp64_sweeps", ctypes.c_int), ("even_odd", ctypes.c_int),
+                ("df_residual", ctypes.c_int),
                 ("residual_max", ctypes.c_double), ("seconds", ctypes.c_double)]
 
     def as_dict(self):
@@ -409,6 +412,16 @@ class Dirac:
     def preconditioner(self) -> int:
         t = I()
         check(lib().dirac_get_preconditioner(self.h, ctypes.byref(t)), self.h, "dirac_get_preconditioner")
+        return t.value
+
+    def set_residual_arithmetic(self, mode: int):
+        """Outer residual: 1 double-float sweep, 0 FP64; see dirac_set_residual_arithmetic."""
+        check(lib().dirac_set_residual_arithmetic(self.h, mode), self.h, "dirac_set_residual_arithmetic")
+
+    def residual_arithmetic(self) -> int:
+        t = I()
+        check(lib().dirac_get_residual_arithmetic(self.h, ctypes.byref(t)), self.h,
+              "dirac_get_residual_arithmetic")
         return t.value
 
     def autotune(self, force: bool = False):

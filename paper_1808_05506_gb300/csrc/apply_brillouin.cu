@@ -7,6 +7,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "dirac_df.cuh"
 #include "dirac_internal.h"
 
 namespace dirac {
@@ -144,6 +145,23 @@ cudaError_t upload_brillouin_table(cudaStream_t st)
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
     return e;
+}
+
+// double-float residual sweep (dirac_df.cuh): one thread per (site, right-hand side)
+__global__ void __launch_bounds__(128) k_brillouin_df(ApplyArgs a)
+{
+    const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.nsites) return;
+    brillouin_site<f64df, 1, false>(a, slab_site(a, p), (int)blockIdx.y, c_bri_dirs);
+}
+
+cudaError_t launch_brillouin_df(const ApplyArgs& a, cudaStream_t st)
+{
+    cudaError_t e = upload_brillouin_table(st);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)((a.nsites + 127) / 128), (unsigned)a.Nv);
+    k_brillouin_df<<<grid, 128, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace dirac

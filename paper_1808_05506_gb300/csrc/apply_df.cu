@@ -1,0 +1,47 @@
+// Double-float residual sweeps (dirac_df.cuh) of the Wilson and staggered
+// operators, and the FP64 -> double-float conversion of fields and links.
+#include "dirac_df.cuh"
+
+namespace dirac {
+
+// one thread per (site, right-hand side): blockIdx.y is the right-hand side
+template <int OP>
+__global__ void __launch_bounds__(128) k_apply_df(ApplyArgs a)
+{
+    const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.nsites) return;
+    const long s = slab_site(a, p);
+    if constexpr (OP == OP_WILSON) wilson_site<f64df, 1, false, 0>(a, s, (int)blockIdx.y);
+    else staggered_site<f64df, 1, false, 0>(a, s, (int)blockIdx.y);
+}
+
+cudaError_t launch_apply_df(int op, const ApplyArgs& a, cudaStream_t st)
+{
+    if (a.nsites == 0 || a.Nv == 0) return cudaSuccess;
+    if (op == OP_BRILLOUIN) return launch_brillouin_df(a, st);
+    const dim3 grid((unsigned)((a.nsites + 127) / 128), (unsigned)a.Nv);
+    if (op == OP_WILSON) k_apply_df<OP_WILSON><<<grid, 128, 0, st>>>(a);
+    else if (op == OP_STAGGERED) k_apply_df<OP_STAGGERED><<<grid, 128, 0, st>>>(a);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+__global__ void k_df_from_f64(size_t n16, const double2* __restrict__ src, float4* dst)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 v = src[i];
+        const dfl re(v.x), im(v.y);
+        dst[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+}
+
+cudaError_t df_from_f64(size_t n16, const void* src, void* dst, cudaStream_t st)
+{
+    if (n16 == 0) return cudaSuccess;
+    size_t b = (n16 + 1023) / 1024;
+    if (b > 4096) b = 4096;
+    k_df_from_f64<<<(unsigned)b, 256, 0, st>>>(n16, static_cast<const double2*>(src), static_cast<float4*>(dst));
+    return cudaGetLastError();
+}
+
+}  // namespace dirac

@@ -7,6 +7,7 @@
 #include <string>
 
 #include "../../include/dirac.h"
+#include "dirac_df.cuh"
 #include "dirac_handle.h"
 
 using namespace dirac;
@@ -204,6 +205,7 @@ dirac_status dirac_create(dirac_handle** h, dirac_op op, int Nc, int Nx, int Ny,
     H->Nc = Nc;
     H->Nv = Nv;
     H->prec = (int)prec;
+    H->outer_df = prec == DIRAC_F64 ? 0 : 1;   // FP64 handles keep an FP64 outer residual
     H->g = make_geom(Nx, Ny, Nz, Nt);
     H->mass = mass;
     H->diag = H->diag_of(mass);
@@ -242,6 +244,7 @@ dirac_handle::~dirac_handle()
     release(links64);
     release(W64);
     release(links64b);
+    release(links_df);
     release(ws_in);
     release(ws_out);
     free_solver_workspace();
@@ -311,6 +314,7 @@ dirac_status dirac_set_links(dirac_handle* h, const void* V, dirac_prec V_prec, 
     if (st) return st;
     h->release(h->W64);
     h->release(h->links64b);
+    h->release(h->links_df);
     const int nmat = (h->op == OP_BRILLOUIN) ? 40 : 4;
     if (!h->links && (st = h->alloc(&h->links, nblk_of((size_t)h->g.vol) * 32 * 9 * nmat * cbytes(h->prec), "links")))
         return st;
@@ -349,6 +353,24 @@ dirac_status dirac_handle::ensure_links64b(const void** out)
         }
     }
     *out = links64b;
+    return DIRAC_OK;
+}
+
+dirac_status dirac_handle::ensure_links_df(const void** out)
+{
+    if (!links_df) {
+        const void* L64 = nullptr;
+        dirac_status st;
+        if ((st = ensure_links64b(&L64))) return st;
+        const int nmat = (op == OP_BRILLOUIN) ? 40 : 4;
+        const size_t n16 = nblk_of((size_t)g.vol) * 32 * 9 * nmat;
+        if ((st = alloc(&links_df, n16 * 16, "double-float links"))) return st;
+        if ((st = cuda(df_from_f64(n16, L64, links_df, stream), "double-float links"))) {
+            release(links_df);
+            return st;
+        }
+    }
+    *out = links_df;
     return DIRAC_OK;
 }
 
@@ -470,6 +492,22 @@ dirac_status dirac_set_preconditioner(dirac_handle* h, int mode)
     if (mode != 0 && mode != 1)
         return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_set_preconditioner: mode %d is not 0 or 1", mode);
     h->precond = mode;
+    return DIRAC_OK;
+}
+
+dirac_status dirac_set_residual_arithmetic(dirac_handle* h, int mode)
+{
+    if (!h) return DIRAC_ERR_INVALID_ARG;
+    if (mode != 0 && mode != 1)
+        return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_set_residual_arithmetic: mode %d is not 0 or 1", mode);
+    h->outer_df = mode;
+    return DIRAC_OK;
+}
+
+dirac_status dirac_get_residual_arithmetic(const dirac_handle* h, int* mode)
+{
+    if (!h || !mode) return DIRAC_ERR_INVALID_ARG;
+    *mode = h->outer_df;
     return DIRAC_OK;
 }
 

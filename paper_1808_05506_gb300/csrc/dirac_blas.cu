@@ -282,6 +282,24 @@ __global__ void k_residual64(size_t n, const void* __restrict__ b, const void* _
     block_partial(s, part, (size_t)v * gridDim.x + blockIdx.x);
 }
 
+// r = b - a with a in double-float storage (four floats re.hi, re.lo, im.hi,
+// im.lo per complex); a may alias r: each element is read (plainly, not
+// through the read-only path) before the same thread writes it
+__global__ void k_residual_df(size_t n, const void* __restrict__ b, const void* a, void* r, double* part)
+{
+    const int v = blockIdx.y;
+    const size_t base = (size_t)v * n;
+    double s = 0.0;
+    for (size_t i = (size_t)blockIdx.x * BT + threadIdx.x; i < n; i += (size_t)gridDim.x * BT) {
+        const cx<double> bv = ld_one<double>(b, base + i);
+        const float4 q = static_cast<const float4*>(a)[base + i];
+        cx<double> rv{bv.re - ((double)q.x + (double)q.y), bv.im - ((double)q.z + (double)q.w)};
+        st_one<double>(r, base + i, rv);
+        s += rv.re * rv.re + rv.im * rv.im;
+    }
+    block_partial(s, part, (size_t)v * gridDim.x + blockIdx.x);
+}
+
 // Fields of different storage types pack the complex numbers of a site into
 // 16-byte elements differently, so conversions between them go site by site
 // through load_spinor / store_spinor (one thread per site and right-hand side).
@@ -467,6 +485,15 @@ cudaError_t blas_residual64(size_t n, int Nv, const void* b, const void* a, void
 {
     dim3 g = grid_of(n, Nv);
     k_residual64<<<g, BT, 0, st>>>(n, b, a, r, part);
+    k_reduce_partials<<<Nv, BT, 0, st>>>(part, g.x, rr, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t blas_residual_df(size_t n, int Nv, const void* b, const void* a_df, void* r, double* part, double* rr,
+                             cudaStream_t st)
+{
+    dim3 g = grid_of(n, Nv);
+    k_residual_df<<<g, BT, 0, st>>>(n, b, a_df, r, part);
     k_reduce_partials<<<Nv, BT, 0, st>>>(part, g.x, rr, 0);
     return cudaGetLastError();
 }

@@ -33,5 +33,8 @@ cudaError_t blas_axpy_to64(int prec, int nsc, long vol, int Nv, const double* co
 // r = b - a (FP64), rr_v = |r_v|^2
 cudaError_t blas_residual64(size_t n, int Nv, const void* b, const void* a, void* r, double* part, double* rr,
                             cudaStream_t st);
+// the same with a in double-float storage (dirac_df.cuh); a_df may alias r
+cudaError_t blas_residual_df(size_t n, int Nv, const void* b, const void* a_df, void* r, double* part, double* rr,
+                             cudaStream_t st);
 
 }  // namespace dirac

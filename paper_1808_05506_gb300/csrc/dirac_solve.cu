@@ -43,6 +43,7 @@
 #include <vector>
 
 #include "dirac_blas.h"
+#include "dirac_df.cuh"
 #include "dirac_eo.cuh"
 #include "dirac_handle.h"
 
@@ -139,6 +140,7 @@ struct SolverWS {
     // storage precision: whole-lattice fields, or odd half fields when eo
     void *e = nullptr, *r = nullptr, *s = nullptr, *p = nullptr, *t = nullptr;
     void *tmp = nullptr, *re = nullptr, *ro = nullptr;        // eo: even scratch, r_hat halves
+    void* xdf = nullptr;                                      // x in double-float storage (lazy)
     size_t n = 0;                                             // complex numbers per rhs of the inner fields
     double* part = nullptr;                                   // reduction partials
     double* scal = nullptr;                                   // per-rhs scalar slots
@@ -166,7 +168,7 @@ void dirac_handle::free_solver_workspace()
     if (w->gexec) cudaGraphExecDestroy(w->gexec);
     if (w->ev) cudaEventDestroy(w->ev);
     if (w->cs) cudaStreamDestroy(w->cs);
-    void** ptrs[] = {&w->b64, &w->x64, &w->r64, &w->e, &w->r, &w->s, &w->p, &w->t, &w->tmp, &w->re, &w->ro};
+    void** ptrs[] = {&w->b64, &w->x64, &w->r64, &w->e, &w->r, &w->s, &w->p, &w->t, &w->tmp, &w->re, &w->ro, &w->xdf};
     for (void** q : ptrs) release(*q);
     void* pp = w->part;
     release(pp);
@@ -474,25 +476,54 @@ static dirac_status refine_step(dirac_handle* h, SolverWS* w, const double* diag
     return h->cuda(eo_axpy_to64(P, nsc_of(h->op), h->g, W, w->coef, w->tmp, w->e, w->x64, S), "solve: x update");
 }
 
-// r64 = b64 - D x64 in FP64; rr64 (host) = |r|^2 per slot
+// r64 = b64 - D x64 with FP64 links and FP64 data, rr64 (host) = |r|^2 per
+// slot.  With df the sweep runs in double-float arithmetic (dirac_df.cuh) on
+// a double-float copy of x and writes D x (double-float) into r64, which the
+// residual kernel then overwrites with b - D x in FP64.
 static dirac_status fp64_residual(dirac_handle* h, SolverWS* w, const double* diag_v, std::vector<double>& rr64,
-                                  dirac_solve_stats* S_)
+                                  dirac_solve_stats* S_, bool df)
 {
     const int W = w->W;
     const size_t n = (size_t)nsc_of(h->op) * nblk_of((size_t)h->g.vol) * 32;
     cudaStream_t S = h->stream;
-    const void* L64 = nullptr;
     dirac_status st;
-    if ((st = h->ensure_links64b(&L64))) return st;
-    const LaunchCfg cfg64 = default_config(h->op, P_F64, W);
-    if ((st = h->run_apply(false, w->r64, w->x64, W, h->diag, L64, P_F64, cfg64, diag_v))) return st;
+    if (df) {
+        const void* Ldf = nullptr;
+        if ((st = h->ensure_links_df(&Ldf))) return st;
+        if (!w->xdf && (st = h->alloc(&w->xdf, n * W * 16, "solver x (double-float)"))) return st;
+        if ((st = h->cuda(df_from_f64(n * W, w->x64, w->xdf, S), "solve: x to double-float"))) return st;
+        ApplyArgs a = h->args(w->r64, w->xdf, W, h->diag);
+        a.links = Ldf;
+        a.diag_v = diag_v;
+        if ((st = h->cuda(launch_apply_df(h->op, a, S), "solve: double-float residual sweep"))) return st;
+        if ((st = h->cuda(blas_residual_df(n, W, w->b64, w->r64, w->r64, w->part, w->rr64, S), "solve: residual")))
+            return st;
+    } else {
+        const void* L64 = nullptr;
+        if ((st = h->ensure_links64b(&L64))) return st;
+        const LaunchCfg cfg64 = default_config(h->op, P_F64, W);
+        if ((st = h->run_apply(false, w->r64, w->x64, W, h->diag, L64, P_F64, cfg64, diag_v))) return st;
+        if ((st = h->cuda(blas_residual64(n, W, w->b64, w->r64, w->r64, w->part, w->rr64, S), "solve: residual")))
+            return st;
+    }
     S_->fp64_sweeps++;
-    if ((st = h->cuda(blas_residual64(n, W, w->b64, w->r64, w->r64, w->part, w->rr64, S), "solve: residual")))
-        return st;
     rr64.resize(W);
     if ((st = h->cuda(cudaMemcpyAsync(rr64.data(), w->rr64, W * sizeof(double), cudaMemcpyDeviceToHost, S), "copy")))
         return st;
     return h->cuda(cudaStreamSynchronize(S), "solve: sync");
+}
+
+// whether the outer residual may run in double-float: asked for, and every
+// right-hand side's mean square |b|^2 / n well inside FP32's exponent range
+// (the halves of a double-float value are FP32 numbers)
+static bool use_df(const dirac_handle* h, const std::vector<double>& bb, size_t n)
+{
+    if (!h->outer_df) return false;
+    for (double v : bb) {
+        const double ms = v / (double)n;
+        if (v > 0.0 && !(ms > 1e-36 && ms < 1e36)) return false;
+    }
+    return true;
 }
 
 // Runs a solve on the workspace's private stream, ordered after the work
@@ -573,8 +604,10 @@ extern "C" DIRAC_API dirac_status dirac_solve(dirac_handle* h, void* x, const vo
     CK(cudaMemcpyAsync(bb.data(), w->bb, Nv * sizeof(double), cudaMemcpyDeviceToHost, S), "solve: copy");
     dirac_status result = DIRAC_NOT_CONVERGED;
     int outer = 0;
+    CK(cudaStreamSynchronize(S), "solve: sync");   // bb on the host
+    const bool df = use_df(h, bb, n);
     for (;; ++outer) {
-        if ((st = fp64_residual(h, w, nullptr, rr64, &S_))) return st;
+        if ((st = fp64_residual(h, w, nullptr, rr64, &S_, df))) return st;
         bool all = true, finite = true;
         for (int v = 0; v < Nv; ++v) {
             res[v] = bb[v] > 0.0 ? std::sqrt(rr64[v] / bb[v]) : std::sqrt(rr64[v]);
@@ -596,6 +629,7 @@ extern "C" DIRAC_API dirac_status dirac_solve(dirac_handle* h, void* x, const vo
     }
     S_.outer_iterations = outer;
     S_.even_odd = w->eo ? 1 : 0;
+    S_.df_residual = df ? 1 : 0;
     CK(launch_unpack_spinor(P_F64, nsc, h->g, Nv, w->x64, x, true, S), "solve: unpack x");
     CK(cudaStreamSynchronize(S), "solve: sync");
 #undef CK
@@ -665,6 +699,7 @@ extern "C" DIRAC_API dirac_status dirac_solve_batched(dirac_handle* h, int nsys,
     CK(cudaMemsetAsync(w->b64, 0, n * W * 16, S), "batched: clear b");
     CK(cudaMemsetAsync(w->x64, 0, n * W * 16, S), "batched: clear x");
     bool any_breakdown = false;
+    bool df = h->outer_df != 0;   // cleared for good once an admitted b is out of the double-float range
 
     auto retire = [&](int v, double res, bool conv) -> dirac_status {
         const int i = slot_sys[v], c = slot_col[v];
@@ -707,7 +742,11 @@ extern "C" DIRAC_API dirac_status dirac_solve_batched(dirac_handle* h, int nsys,
             CK(blas_norm2(P_F64, n, W, w->b64, w->part, w->bb, S), "batched: |b|");
             CK(cudaMemcpyAsync(bb.data(), w->bb, W * sizeof(double), cudaMemcpyDeviceToHost, S), "copy");
         }
-        if ((st = fp64_residual(h, w, w->diag_v, rr64, &S_))) return st;
+        if (admitted) {
+            CK(cudaStreamSynchronize(S), "batched: sync");   // bb on the host
+            df = df && use_df(h, bb, n);
+        }
+        if ((st = fp64_residual(h, w, w->diag_v, rr64, &S_, df))) return st;
         std::vector<int> act(W, 0);
         bool freed = false, any_active = false;
         for (int v = 0; v < W; ++v) {
@@ -758,6 +797,7 @@ extern "C" DIRAC_API dirac_status dirac_solve_batched(dirac_handle* h, int nsys,
         for (size_t k = 0; k < col_base[nsys]; ++k) rel_residual[k] = res_col[k];
     S_.residual_max = rmax;
     S_.even_odd = w->eo ? 1 : 0;
+    S_.df_residual = df ? 1 : 0;
     S_.seconds = std::chrono::duration<double>(clk::now() - t0).count();
     if (stats) *stats = S_;
     if (any_breakdown) return h->fail(DIRAC_BREAKDOWN, "dirac_solve_batched: non-finite residual");

@@ -100,6 +100,36 @@ def test_solve_even_odd_vs_whole_lattice(dg, op, mass, prec):
         assert out[1][1]["sweeps"] < out[0][1]["sweeps"], (out[1][1], out[0][1])
 
 
+@pytest.mark.parametrize("op,mass", [("wilson", 0.123), ("staggered", 0.06), ("brillouin", 0.07)])
+def test_solve_residual_arithmetic(dg, op, mass):
+    """The outer residual in double-float arithmetic (default of non-FP64
+    handles) and in FP64 both certify the oracle-checked 1e-10, and the
+    library's residuals match the oracle's at that level (so the
+    double-float residual resolves far below 1e-10); a right-hand side
+    outside FP32's exponent range falls back to FP64."""
+    L, Nv = (4, 4, 2, 6), 2
+    V = links_for("bf16", synth.gauge_links(L, 3, "near_identity", 340))
+    b = synth.spinor(L, Nv, NS[op], 3, 341)
+    D = dg.Dirac(op, L, Nv, mass, "bf16")
+    D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
+    assert D.residual_arithmetic() == 1   # the default of 16-bit handles
+    m0 = m0_of(op, mass)
+    for mode in (1, 0):
+        D.set_residual_arithmetic(mode)
+        x, res, st, status = D.solve(torch.from_numpy(b).cuda(), tol=1e-10, max_outer=60, max_inner=3000)
+        assert status == dg.OK, (mode, res, st)
+        assert st["df_residual"] == mode
+        true_res = oracle_residual(op, V, x.cpu().numpy(), b, m0)
+        assert true_res.max() <= 1e-10, (mode, true_res)
+        assert np.allclose(true_res, res, rtol=1e-3, atol=1e-14), (mode, true_res, res)
+    D.set_residual_arithmetic(1)
+    tiny = b * 1e-20   # mean square 1e-40: outside the double-float range
+    x, res, st, status = D.solve(torch.from_numpy(tiny).cuda(), tol=1e-10, max_outer=60, max_inner=3000)
+    assert status == dg.OK and st["df_residual"] == 0, st
+    assert oracle_residual(op, V, x.cpu().numpy(), tiny, m0).max() <= 1e-10
+    D.close()
+
+
 def test_solve_resume_and_zero_rhs(dg):
     """x0 = the solution: no refinement step is taken; a zero right-hand side
     converges at once; the result does not depend on the other columns."""
