@@ -246,7 +246,7 @@ def solve_times(dg, torch, L=(24, 24, 24, 48), Nv=12, m0=0.05, precs=("f32", "bf
 
 
 def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=("f32", "bf16", "f16"),
-                        rank=0, ws=1, dist=None, precond=1):
+                        rank=0, ws=1, dist=None, precond=1, autotune=True):
     """Wilson systems D(kappa_i) x_i = b_i on one gauge field, Nv_i ~ U{1..24},
     kappa_i ~ U[0.120, 0.124], through dirac_solve_batched with `slots` resident
     right-hand-side columns, each precision to a true FP64 residual of 1e-10:
@@ -275,7 +275,8 @@ def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=(
         D = dg.Dirac("wilson", L, slots, 0.122, prec)
         D.set_preconditioner(precond)
         D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
-        D.autotune()
+        if autotune:
+            D.autotune()
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -372,6 +373,10 @@ def main():
                     help="R,block,variant[,tchunk]: fixed launch shape (and site order) instead of the autotuner")
     ap.add_argument("--op", default="wilson", choices=["wilson", "staggered", "brillouin"],
                     help="operator of the timed sweep (the default workload is Wilson; the others are for profiling)")
+    ap.add_argument("--batched-solve-only", action="store_true",
+                    help="only the batched Wilson solve (for profiling; --lattice, --prec, --precond, --no-autotune)")
+    ap.add_argument("--precond", type=int, default=1, choices=[0, 1], help="with --batched-solve-only")
+    ap.add_argument("--no-autotune", action="store_true", help="with --batched-solve-only: default launch shapes")
     args = ap.parse_args()
     global WORKLOAD
     if args.lattice:
@@ -389,6 +394,17 @@ def main():
     if ws == 1:
         torch.cuda.set_device(0)
     import paper_1808_05506_gb300 as dg
+
+    if args.batched_solve_only:
+        out = batched_solve_times(dg, torch, L=WORKLOAD["L"] if args.lattice else (32, 32, 32, 64),
+                                  precs=(args.prec,) if args.prec else ("f32", "bf16", "f16"), rank=rank, ws=ws,
+                                  dist=dist, precond=args.precond, autotune=not args.no_autotune)
+        if rank == 0:
+            print(json.dumps({"batched_solve": out}), flush=True)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
 
     w = WORKLOAD
     V, psi = gen_inputs(w)
