@@ -246,7 +246,7 @@ def solve_times(dg, torch, L=(24, 24, 24, 48), Nv=12, m0=0.05, precs=("f32", "bf
 
 
 def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=("f32", "bf16", "f16"),
-                        rank=0, ws=1, dist=None, precond=1, autotune=True):
+                        rank=0, ws=1, dist=None, precond=1, autotune=True, inner_fields=0):
     """Wilson systems D(kappa_i) x_i = b_i on one gauge field, Nv_i ~ U{1..24},
     kappa_i ~ U[0.120, 0.124], through dirac_solve_batched with `slots` resident
     right-hand-side columns, each precision to a true FP64 residual of 1e-10:
@@ -274,6 +274,7 @@ def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=(
     for prec in precs:
         D = dg.Dirac("wilson", L, slots, 0.122, prec)
         D.set_preconditioner(precond)
+        D.set_inner_fields(inner_fields)
         D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
         if autotune:
             D.autotune()
@@ -295,7 +296,7 @@ def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=(
                      "outer_max": max(s["outer_iterations"] for s in stats),
                      "all_converged": all(s["converged"] for s in stats), "kernel": list(D.kernel_config()),
                      "rank0_totals": {k: tot.get(k) for k in ("outer_iterations", "inner_iterations", "sweeps",
-                                                                "fp64_sweeps", "even_odd")}}
+                                                                "fp64_sweeps", "even_odd", "split_fields")}}
         D.close()
         del xs
         torch.cuda.empty_cache()
@@ -377,6 +378,8 @@ def main():
                     help="only the batched Wilson solve (for profiling; --lattice, --prec, --precond, --no-autotune)")
     ap.add_argument("--precond", type=int, default=1, choices=[0, 1], help="with --batched-solve-only")
     ap.add_argument("--no-autotune", action="store_true", help="with --batched-solve-only: default launch shapes")
+    ap.add_argument("--inner-fields", type=int, default=0, choices=[0, 1],
+                    help="with --batched-solve-only: 1 split inner fields for 16-bit storage")
     args = ap.parse_args()
     global WORKLOAD
     if args.lattice:
@@ -398,7 +401,8 @@ def main():
     if args.batched_solve_only:
         out = batched_solve_times(dg, torch, L=WORKLOAD["L"] if args.lattice else (32, 32, 32, 64),
                                   precs=(args.prec,) if args.prec else ("f32", "bf16", "f16"), rank=rank, ws=ws,
-                                  dist=dist, precond=args.precond, autotune=not args.no_autotune)
+                                  dist=dist, precond=args.precond, autotune=not args.no_autotune,
+                                  inner_fields=args.inner_fields)
         if rank == 0:
             print(json.dumps({"batched_solve": out}), flush=True)
         if dist:
@@ -520,6 +524,12 @@ def main():
     if not args.no_solve and not args.no_extra:
         line["solve"] = solve_times(dg, torch)
         line["batched_solve"] = batched_solve_times(dg, torch, rank=rank, ws=ws, dist=dist)
+        # 16-bit storage with split inner fields (FP32 residual and solution, 16-bit search directions)
+        split = batched_solve_times(dg, torch, precs=("bf16", "f16"), rank=rank, ws=ws, dist=dist, inner_fields=1)
+        for p in ("bf16", "f16"):
+            split[p]["speedup_vs_f32"] = line["batched_solve"]["f32"]["seconds"] / split[p]["seconds"]
+        split["inner_solver"] += "; split fields: FP32 e, r, t and links, 16-bit p, s"
+        line["batched_solve_split"] = split
         # the same systems with the whole-lattice inner solver, for comparison
         line["batched_solve_whole_lattice"] = batched_solve_times(dg, torch, rank=rank, ws=ws, dist=dist, precond=0)
     if rank == 0 and not args.no_cpu:

@@ -197,6 +197,7 @@ typedef struct {
     int fp64_sweeps;        /* FP64 applications of D (outer residuals) */
     int even_odd;           /* 1 if the inner solves took the even-odd Schur complement */
     int df_residual;        /* 1 if the outer residuals ran in double-float arithmetic */
+    int split_fields;       /* 1 if the inner solves kept split fields (dirac_set_inner_fields) */
     double residual_max;    /* max over right-hand sides of |b - D x| / |b|, FP64 */
     double seconds;         /* host wall time of the call */
 } dirac_solve_stats;
@@ -299,6 +300,22 @@ DIRAC_API dirac_status dirac_apply_static(dirac_handle* h, void* out, const void
  * mode. */
 DIRAC_API dirac_status dirac_set_preconditioner(dirac_handle* h, int mode);
 DIRAC_API dirac_status dirac_get_preconditioner(const dirac_handle* h, int* mode);
+
+/* Fields of the even-odd inner solves of 16-bit Wilson handles.
+ *   mode 0 (default): every inner field in the handle's 16-bit precision.
+ *   mode 1 (split): the search directions p and s = S^+ r (and the adjoint
+ *          sweep's intermediate) in 16 bits; the solution e, the residual r,
+ *          the products t = S p and the links in FP32.  Because t is formed
+ *          exactly (to FP32) from the 16-bit p that also updates e, the
+ *          recursive residual stays the true one to FP32 accuracy, so an
+ *          inner solve reaches FP32-level reductions (the rounding of p only
+ *          perturbs the search directions) while half of its vector traffic
+ *          and the sweeps' direction inputs stay 16-bit.
+ * Other handles (FP32, FP64, staggered, Brillouin, whole-lattice inner
+ * solves) ignore the mode.  The stats field split_fields reports it.
+ * Errors: DIRAC_ERR_INVALID_ARG for another mode. */
+DIRAC_API dirac_status dirac_set_inner_fields(dirac_handle* h, int mode);
+DIRAC_API dirac_status dirac_get_inner_fields(const dirac_handle* h, int* mode);
 
 /* Arithmetic of the outer residual r = b - D x of dirac_solve and
  * dirac_solve_batched (the FP64 step of the defect correction).

@@ -71,6 +71,8 @@ SIGNATURES = {
     "dirac_get_site_order": (I, [P, ctypes.POINTER(I)]),
     "dirac_set_preconditioner": (I, [P, I]),
     "dirac_set_residual_arithmetic": (I, [P, I]),
+    "dirac_set_inner_fields": (I, [P, I]),
+    "dirac_get_inner_fields": (I, [P, ctypes.POINTER(I)]),
     "dirac_get_residual_arithmetic": (I, [P, ctypes.POINTER(I)]),
     "dirac_get_preconditioner": (I, [P, ctypes.POINTER(I)]),
     "dirac_last_error": (ctypes.c_char_p, [P]),
@@ -93,7 +95,7 @@ class SolveStats(ctypes.Structure):
     """dirac_solve_stats of include/dirac.h."""
     _fields_ = [("outer_iterations", ctypes.c_int), ("inner_iterations", ctypes.c_int),
                 ("sweeps", ctypes.c_int), ("fp64_sweeps", ctypes.c_int), ("even_odd", ctypes.c_int),
-                ("df_residual", ctypes.c_int),
+                ("df_residual", ctypes.c_int), ("split_fields", ctypes.c_int),
                 ("residual_max", ctypes.c_double), ("seconds", ctypes.c_double)]
 
     def as_dict(self):
@@ -322,7 +324,7 @@ class Dirac:
         import numpy as np
         torch = _torch()
         if inner_tol is None:
-            inner_tol = {"f64": 1e-10, "f32": 1e-5, "f16": 2e-3, "bf16": 1e-2}[self.prec]
+            inner_tol = self._default_inner_tol()
         b = self._canon_in(b, "b", dtype=torch.complex128)
         x = torch.zeros_like(b) if x0 is None else self._canon_in(x0, "x0", dtype=torch.complex128).clone()
         res = np.zeros(self.Nv, dtype=np.float64)
@@ -343,7 +345,7 @@ class Dirac:
         import numpy as np
         torch = _torch()
         if inner_tol is None:
-            inner_tol = {"f64": 1e-10, "f32": 1e-5, "f16": 2e-3, "bf16": 1e-2}[self.prec]
+            inner_tol = self._default_inner_tol()
         nsys = len(bs)
         Nx, Ny, Nz, Nt = self.L
         for i, b in enumerate(bs):
@@ -412,6 +414,25 @@ class Dirac:
     def preconditioner(self) -> int:
         t = I()
         check(lib().dirac_get_preconditioner(self.h, ctypes.byref(t)), self.h, "dirac_get_preconditioner")
+        return t.value
+
+    def _default_inner_tol(self) -> float:
+        # the reduction one inner solve can reach in its storage precision; split
+        # fields (16-bit Wilson, see set_inner_fields) reach FP32's
+        split = getattr(self, "_inner_fields", 0) == 1 and self.op == "wilson" and self.prec in ("bf16", "f16")
+        if split:
+            return 1e-5
+        return {"f64": 1e-10, "f32": 1e-5, "f16": 2e-3, "bf16": 1e-2}[self.prec]
+
+    def set_inner_fields(self, mode: int):
+        """16-bit Wilson even-odd inner solves: 1 split fields (FP32 e, r, t; 16-bit p, s), 0 all
+        16-bit; see dirac_set_inner_fields."""
+        check(lib().dirac_set_inner_fields(self.h, mode), self.h, "dirac_set_inner_fields")
+        self._inner_fields = int(mode)
+
+    def inner_fields(self) -> int:
+        t = I()
+        check(lib().dirac_get_inner_fields(self.h, ctypes.byref(t)), self.h, "dirac_get_inner_fields")
         return t.value
 
     def set_residual_arithmetic(self, mode: int):

@@ -245,6 +245,7 @@ dirac_handle::~dirac_handle()
     release(W64);
     release(links64b);
     release(links_df);
+    release(links32);
     release(ws_in);
     release(ws_out);
     free_solver_workspace();
@@ -315,6 +316,7 @@ dirac_status dirac_set_links(dirac_handle* h, const void* V, dirac_prec V_prec, 
     h->release(h->W64);
     h->release(h->links64b);
     h->release(h->links_df);
+    h->release(h->links32);
     const int nmat = (h->op == OP_BRILLOUIN) ? 40 : 4;
     if (!h->links && (st = h->alloc(&h->links, nblk_of((size_t)h->g.vol) * 32 * 9 * nmat * cbytes(h->prec), "links")))
         return st;
@@ -371,6 +373,25 @@ dirac_status dirac_handle::ensure_links_df(const void** out)
         }
     }
     *out = links_df;
+    return DIRAC_OK;
+}
+
+dirac_status dirac_handle::ensure_links32(const void** out)
+{
+    if (prec == P_F32 && op != OP_BRILLOUIN) {
+        *out = links;
+        return DIRAC_OK;
+    }
+    if (op == OP_BRILLOUIN) return fail(DIRAC_ERR_UNSUPPORTED, "FP32 link copy: Wilson and staggered only");
+    if (!links32) {
+        dirac_status st;
+        if ((st = alloc(&links32, nblk_of((size_t)g.vol) * 32 * 9 * 4 * 8, "FP32 links (blocked)"))) return st;
+        if ((st = cuda(launch_convert_links(P_F32, g, 4, links64, links32, stream), "FP32 links (blocked)"))) {
+            release(links32);
+            return st;
+        }
+    }
+    *out = links32;
     return DIRAC_OK;
 }
 
@@ -508,6 +529,22 @@ dirac_status dirac_get_residual_arithmetic(const dirac_handle* h, int* mode)
 {
     if (!h || !mode) return DIRAC_ERR_INVALID_ARG;
     *mode = h->outer_df;
+    return DIRAC_OK;
+}
+
+dirac_status dirac_set_inner_fields(dirac_handle* h, int mode)
+{
+    if (!h) return DIRAC_ERR_INVALID_ARG;
+    if (mode != 0 && mode != 1)
+        return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_set_inner_fields: mode %d is not 0 or 1", mode);
+    h->inner_fields = mode;
+    return DIRAC_OK;
+}
+
+dirac_status dirac_get_inner_fields(const dirac_handle* h, int* mode)
+{
+    if (!h || !mode) return DIRAC_ERR_INVALID_ARG;
+    *mode = h->inner_fields;
     return DIRAC_OK;
 }
 

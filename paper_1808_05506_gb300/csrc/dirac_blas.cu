@@ -226,6 +226,48 @@ __global__ void k_cgls_step_v(size_t m, const double* __restrict__ alpha, void* 
     block_partial(s.total(), part, (size_t)v * gridDim.x + blockIdx.x);
 }
 
+// The split inner solve's step: e += alpha p, r -= alpha t, |r|^2 with e, r,
+// t FP32 and p in the 16-bit type H, on Wilson fields (12 complex per site).
+// One 16-byte element of p holds 4 complex numbers of one site (plane k of
+// 3 in its block of 32 sites); the same numbers sit in planes 2k and 2k + 1
+// (of 6) of the FP32 fields, one 16-byte element each.
+template <typename H>
+__global__ void k_cgls_step_split(size_t m16, const double* __restrict__ alpha, void* e, const void* __restrict__ p,
+                                  void* r, const void* __restrict__ t, double* part)
+{
+    const int v = blockIdx.y;
+    const size_t base16 = (size_t)v * m16, base32 = 2 * base16;
+    const float a = (float)alpha[v];
+    Acc<float> s;
+    for (size_t i = (size_t)blockIdx.x * BT + threadIdx.x; i < m16; i += (size_t)gridDim.x * BT) {
+        const size_t blk = i / 96, k = (i / 32) % 3, lane = i % 32;
+        const size_t j0 = base32 + (blk * 6 + 2 * k) * 32 + lane, j1 = j0 + 32;
+        cx<float> pv[4], ev[4], rv[4], tv[4];
+        ld_vec<H>(p, base16 + i, pv);
+        ld_vec<float>(e, j0, ev);
+        ld_vec<float>(e, j1, ev + 2);
+        ld_vec<float>(r, j0, rv);
+        ld_vec<float>(r, j1, rv + 2);
+        ld_vec<float>(t, j0, tv);
+        ld_vec<float>(t, j1, tv + 2);
+        float q = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            ev[j].re = fmaf(a, pv[j].re, ev[j].re);
+            ev[j].im = fmaf(a, pv[j].im, ev[j].im);
+            rv[j].re = fmaf(-a, tv[j].re, rv[j].re);
+            rv[j].im = fmaf(-a, tv[j].im, rv[j].im);
+            q = fmaf(rv[j].re, rv[j].re, fmaf(rv[j].im, rv[j].im, q));
+        }
+        st_vec<float>(e, j0, ev);
+        st_vec<float>(e, j1, ev + 2);
+        st_vec<float>(r, j0, rv);
+        st_vec<float>(r, j1, rv + 2);
+        s.add(q);
+    }
+    block_partial(s.total(), part, (size_t)v * gridDim.x + blockIdx.x);
+}
+
 template <typename T>
 __global__ void k_xpay_v(size_t m, const void* __restrict__ s, const double* __restrict__ beta, void* p)
 {
@@ -485,6 +527,18 @@ cudaError_t blas_residual64(size_t n, int Nv, const void* b, const void* a, void
 {
     dim3 g = grid_of(n, Nv);
     k_residual64<<<g, BT, 0, st>>>(n, b, a, r, part);
+    k_reduce_partials<<<Nv, BT, 0, st>>>(part, g.x, rr, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t blas_cgls_step_split(int prec16, size_t n, int Nv, const double* alpha, void* e, const void* p, void* r,
+                                 const void* t, double* part, double* rr, cudaStream_t st)
+{
+    const size_t m16 = n / 4;
+    dim3 g = grid_of(m16, Nv);
+    if (prec16 == P_BF16) k_cgls_step_split<__nv_bfloat16><<<g, BT, 0, st>>>(m16, alpha, e, p, r, t, part);
+    else if (prec16 == P_F16) k_cgls_step_split<__half><<<g, BT, 0, st>>>(m16, alpha, e, p, r, t, part);
+    else return cudaErrorInvalidValue;
     k_reduce_partials<<<Nv, BT, 0, st>>>(part, g.x, rr, 0);
     return cudaGetLastError();
 }

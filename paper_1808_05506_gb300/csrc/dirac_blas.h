@@ -18,6 +18,10 @@ cudaError_t blas_dot(int prec, size_t n, int Nv, const void* x, const void* y, d
 // e += alpha_v p ; r -= alpha_v t ; rr_v = |r_v|^2
 cudaError_t blas_cgls_step(int prec, size_t n, int Nv, const double* alpha, void* e, const void* p, void* r,
                            const void* t, double* part, double* rr, cudaStream_t st);
+// the same with e, r, t FP32 and p in the 16-bit prec16, Wilson fields (the
+// split inner solve); n = complex numbers per right-hand side
+cudaError_t blas_cgls_step_split(int prec16, size_t n, int Nv, const double* alpha, void* e, const void* p, void* r,
+                                 const void* t, double* part, double* rr, cudaStream_t st);
 // p = s + beta_v p
 cudaError_t blas_xpay(int prec, size_t n, int Nv, const void* s, const double* beta, void* p, cudaStream_t st);
 // dst = scale_v src within one storage type (scale NULL: 1); nrm2_v = |dst_v|^2

@@ -52,17 +52,22 @@ HD long eo_site(const EoArgs& a, long h)
     return 2 * h + ((a.par + yzt) & 1);
 }
 
+// Storage types: TL links, TI the input field `in`, TI2 the field `in2`, TO
+// the output; one arithmetic type for all (Store<TI>::A: FP64 for FP64
+// fields, else FP32).  The uniform sweeps take one type for all four; the
+// split inner solve mixes FP32 and 16-bit fields.
+
 // acc_r += (1 + S gamma_MU) U psi_r(h_nbr), U = V_MU(lsite) or its adjoint (BACK)
-template <typename T, int R, int MU, int S, bool BACK>
-DEV_INLINE void eo_wilson_hop(const EoArgs& a, long hn, long lsite, int v0, cx<typename Store<T>::A> (&acc)[R][12])
+template <typename TL, typename TI, int R, int MU, int S, bool BACK>
+DEV_INLINE void eo_wilson_hop(const EoArgs& a, long hn, long lsite, int v0, cx<typename Store<TI>::A> (&acc)[R][12])
 {
-    using A = typename Store<T>::A;
+    using A = typename Store<TI>::A;
     cx<A> U[9];
-    load_link<T>(a.links, a.g.vol, MU, lsite, U);
+    load_link<TL>(a.links, a.g.vol, MU, lsite, U);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         cx<A> p[12], h[6], w[6];
-        load_spinor<T, 12>(a.in, a.vh, v0 + r, hn, p);
+        load_spinor<TI, 12>(a.in, a.vh, v0 + r, hn, p);
         wilson_project<MU, S>(p, h);
         if constexpr (BACK) { mat_dag_vec(U, h, w); mat_dag_vec(U, h + 3, w + 3); }
         else { mat_vec(U, h, w); mat_vec(U, h + 3, w + 3); }
@@ -73,10 +78,10 @@ DEV_INLINE void eo_wilson_hop(const EoArgs& a, long hn, long lsite, int v0, cx<t
 // out = alpha in2 + beta (H in) at one site; H = -1/2 sum_mu [(1 - gamma_mu)
 // V_mu(x) psi(x + mu) + (1 + gamma_mu) V_mu(x - mu)^+ psi(x - mu)], the
 // adjoint swapping the two projectors.  R divides Nv.
-template <typename T, int R, bool DAG>
+template <typename TL, typename TI, typename TI2, typename TO, int R, bool DAG>
 DEV_INLINE void wilson_eo_site(const EoArgs& a, long h, int group)
 {
-    using A = typename Store<T>::A;
+    using A = typename Store<TI>::A;
     const long s = eo_site(a, h);
     long fwd[4], bwd[4];
     int x[4];
@@ -89,14 +94,14 @@ DEV_INLINE void wilson_eo_site(const EoArgs& a, long h, int group)
         for (int i = 0; i < 12; ++i) acc[r][i] = cx<A>{A(0), A(0)};
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
-    eo_wilson_hop<T, R, 0, SF, false>(a, (s + fwd[0]) >> 1, s, v0, acc);
-    eo_wilson_hop<T, R, 0, SB, true>(a, (s + bwd[0]) >> 1, s + bwd[0], v0, acc);
-    eo_wilson_hop<T, R, 1, SF, false>(a, (s + fwd[1]) >> 1, s, v0, acc);
-    eo_wilson_hop<T, R, 1, SB, true>(a, (s + bwd[1]) >> 1, s + bwd[1], v0, acc);
-    eo_wilson_hop<T, R, 2, SF, false>(a, (s + fwd[2]) >> 1, s, v0, acc);
-    eo_wilson_hop<T, R, 2, SB, true>(a, (s + bwd[2]) >> 1, s + bwd[2], v0, acc);
-    eo_wilson_hop<T, R, 3, SF, false>(a, (s + fwd[3]) >> 1, s, v0, acc);
-    eo_wilson_hop<T, R, 3, SB, true>(a, (s + bwd[3]) >> 1, s + bwd[3], v0, acc);
+    eo_wilson_hop<TL, TI, R, 0, SF, false>(a, (s + fwd[0]) >> 1, s, v0, acc);
+    eo_wilson_hop<TL, TI, R, 0, SB, true>(a, (s + bwd[0]) >> 1, s + bwd[0], v0, acc);
+    eo_wilson_hop<TL, TI, R, 1, SF, false>(a, (s + fwd[1]) >> 1, s, v0, acc);
+    eo_wilson_hop<TL, TI, R, 1, SB, true>(a, (s + bwd[1]) >> 1, s + bwd[1], v0, acc);
+    eo_wilson_hop<TL, TI, R, 2, SF, false>(a, (s + fwd[2]) >> 1, s, v0, acc);
+    eo_wilson_hop<TL, TI, R, 2, SB, true>(a, (s + bwd[2]) >> 1, s + bwd[2], v0, acc);
+    eo_wilson_hop<TL, TI, R, 3, SF, false>(a, (s + fwd[3]) >> 1, s, v0, acc);
+    eo_wilson_hop<TL, TI, R, 3, SB, true>(a, (s + bwd[3]) >> 1, s + bwd[3], v0, acc);
     const A* cf = static_cast<const A*>(a.coef);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -104,7 +109,7 @@ DEV_INLINE void wilson_eo_site(const EoArgs& a, long h, int group)
         const A al = cf[v], be = A(-0.5) * cf[a.Nv + v];
         cx<A> o[12];
         if (a.in2) {
-            load_spinor<T, 12>(a.in2, a.vh, v, h, o);
+            load_spinor<TI2, 12>(a.in2, a.vh, v, h, o);
 #pragma unroll
             for (int i = 0; i < 12; ++i) {
                 o[i].re = fma(be, acc[r][i].re, al * o[i].re);
@@ -114,16 +119,16 @@ DEV_INLINE void wilson_eo_site(const EoArgs& a, long h, int group)
 #pragma unroll
             for (int i = 0; i < 12; ++i) o[i] = cx<A>{be * acc[r][i].re, be * acc[r][i].im};
         }
-        store_spinor<T, 12>(a.out, a.vh, v, h, o);
+        store_spinor<TO, 12>(a.out, a.vh, v, h, o);
     }
 }
 
 // out = alpha in2 + beta (H in) at one site; H = 1/2 sum_mu eta_mu(x)
 // [V_mu(x) psi(x + mu) - V_mu(x - mu)^+ psi(x - mu)], H^+ = -H.  R divides Nv.
-template <typename T, int R, bool DAG>
+template <typename TL, typename TI, typename TI2, typename TO, int R, bool DAG>
 DEV_INLINE void staggered_eo_site(const EoArgs& a, long h, int group)
 {
-    using A = typename Store<T>::A;
+    using A = typename Store<TI>::A;
     const long s = eo_site(a, h);
     long fwd[4], bwd[4];
     int x[4];
@@ -140,14 +145,14 @@ DEV_INLINE void staggered_eo_site(const EoArgs& a, long h, int group)
         const A eta = (par & 1) ? A(-1) : A(1);
         par += x[mu];
         cx<A> Uf[9], Ub[9];
-        load_link<T>(a.links, a.g.vol, mu, s, Uf);
-        load_link<T>(a.links, a.g.vol, mu, s + bwd[mu], Ub);
+        load_link<TL>(a.links, a.g.vol, mu, s, Uf);
+        load_link<TL>(a.links, a.g.vol, mu, s + bwd[mu], Ub);
         const long hf = (s + fwd[mu]) >> 1, hb = (s + bwd[mu]) >> 1;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             cx<A> pf[3], pb[3], w[3] = {}, wb[3] = {};
-            load_spinor<T, 3>(a.in, a.vh, v0 + r, hf, pf);
-            load_spinor<T, 3>(a.in, a.vh, v0 + r, hb, pb);
+            load_spinor<TI, 3>(a.in, a.vh, v0 + r, hf, pf);
+            load_spinor<TI, 3>(a.in, a.vh, v0 + r, hb, pb);
             mat_vec(Uf, pf, w);
             mat_dag_vec(Ub, pb, wb);
 #pragma unroll
@@ -165,7 +170,7 @@ DEV_INLINE void staggered_eo_site(const EoArgs& a, long h, int group)
         const A al = cf[v], be = (DAG ? A(-0.5) : A(0.5)) * cf[a.Nv + v];
         cx<A> o[3];
         if (a.in2) {
-            load_spinor<T, 3>(a.in2, a.vh, v, h, o);
+            load_spinor<TI2, 3>(a.in2, a.vh, v, h, o);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 o[c].re = fma(be, acc[r][c].re, al * o[c].re);
@@ -175,14 +180,14 @@ DEV_INLINE void staggered_eo_site(const EoArgs& a, long h, int group)
 #pragma unroll
             for (int c = 0; c < 3; ++c) o[c] = cx<A>{be * acc[r][c].re, be * acc[r][c].im};
         }
-        store_spinor<T, 3>(a.out, a.vh, v, h, o);
+        store_spinor<TO, 3>(a.out, a.vh, v, h, o);
     }
 }
 
 // blockDim = (half sites, gy groups); block b covers a run of half sites (in
 // the site order of the half lattice) and gy groups of R right-hand sides
 
-template <int OP, typename T, int R, bool DAG>
+template <int OP, typename TL, typename TI, typename TI2, typename TO, int R, bool DAG>
 __global__ void __launch_bounds__(192, 2) k_eo(EoArgs a, int ngroups, int gy)
 {
     const int nchunks = (ngroups + gy - 1) / gy;
@@ -191,23 +196,28 @@ __global__ void __launch_bounds__(192, 2) k_eo(EoArgs a, int ngroups, int gy)
     const long p = (b / nchunks) * blockDim.x + threadIdx.x;
     if (p >= a.vh || group >= ngroups) return;
     const long h = site_of(a.gh, p, a.tc, a.g.L[3], a.fdc, a.fdt);
-    if constexpr (OP == OP_WILSON) wilson_eo_site<T, R, DAG>(a, h, group);
-    else staggered_eo_site<T, R, DAG>(a, h, group);
+    if constexpr (OP == OP_WILSON) wilson_eo_site<TL, TI, TI2, TO, R, DAG>(a, h, group);
+    else staggered_eo_site<TL, TI, TI2, TO, R, DAG>(a, h, group);
 }
 
 // block: half sites per block (32, 64 or 128), times gy = min(192 / block,
 // groups) right-hand-side groups
-template <int OP, typename T, int R>
-cudaError_t eo_go(bool dag, const EoArgs& a, int block, cudaStream_t st)
+template <int OP, typename TL, typename TI, typename TI2, typename TO, int R, bool DAG>
+cudaError_t eo_go_typed(const EoArgs& a, int block, cudaStream_t st)
 {
     if (block != 32 && block != 64 && block != 128) return cudaErrorInvalidValue;
     const int ngroups = a.Nv / R;
     const int gy = groups_per_block(block, ngroups);
     const long nb = ((a.vh + block - 1) / block) * (long)((ngroups + gy - 1) / gy);
-    const dim3 bd(block, gy);
-    if (dag) k_eo<OP, T, R, true><<<(unsigned)nb, bd, 0, st>>>(a, ngroups, gy);
-    else k_eo<OP, T, R, false><<<(unsigned)nb, bd, 0, st>>>(a, ngroups, gy);
+    k_eo<OP, TL, TI, TI2, TO, R, DAG><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
     return cudaGetLastError();
+}
+
+// the uniform sweep: every field and the links in storage type T
+template <int OP, typename T, int R>
+cudaError_t eo_go(bool dag, const EoArgs& a, int block, cudaStream_t st)
+{
+    return dag ? eo_go_typed<OP, T, T, T, T, R, true>(a, block, st) : eo_go_typed<OP, T, T, T, T, R, false>(a, block, st);
 }
 
 // right-hand sides per thread R of the even-odd sweeps that are built: R
@@ -239,6 +249,15 @@ namespace dirac {
 cudaError_t launch_eo_wilson(int prec, bool dag, const EoArgs& a, int R, int block, cudaStream_t st);
 cudaError_t launch_eo_staggered(int prec, bool dag, const EoArgs& a, int R, int block, cudaStream_t st);
 cudaError_t launch_eo(int op, int prec, bool dag, const EoArgs& a, LaunchCfg cfg, cudaStream_t st);
+
+// The sweeps of the split inner solve (Wilson, 16-bit handle prec16): FP32
+// links, solution, residual and operator products, 16-bit search directions.
+//   EO_SPLIT_HP:  tmp(F32) = H_eo p(16)                      (no adjoint)
+//   EO_SPLIT_SP:  t(F32) = a p(16) - H_oe tmp(F32) / a       (no adjoint)
+//   EO_SPLIT_HR:  tmp2(16) = H^+_eo r(F32)                   (adjoint)
+//   EO_SPLIT_SR:  s(16) = a r(F32) - H^+_oe tmp2(16) / a     (adjoint)
+enum { EO_SPLIT_HP = 0, EO_SPLIT_SP = 1, EO_SPLIT_HR = 2, EO_SPLIT_SR = 3 };
+cudaError_t launch_eo_wilson_split(int prec16, int kind, const EoArgs& a, LaunchCfg cfg, cudaStream_t st);
 
 // arguments of a sweep over the sites of parity par (the lattice extents all
 // even); tc: site order of the half lattice (0 lexicographic, else t-chunks)

@@ -20,12 +20,14 @@ struct dirac_handle {
     dirac::LaunchCfg cfg{1, 128, dirac::V_DIRECT};
     int precond = 1;          // inner solves: 1 even-odd where it applies, 0 whole lattice
     int outer_df = 1;         // outer residual: 1 double-float sweep (non-FP64 handles), 0 FP64
+    int inner_fields = 0;     // 16-bit Wilson even-odd inner solves: 1 split fields, 0 all 16-bit
     dirac::LaunchCfg eo_cfg{0, 0, 0, 0};   // launch shape of the even-odd sweeps (R = 0: not tuned)
 
     void* links = nullptr;    // storage-precision links [m][9][site] (m = mu, or 40 stored W)
     void* links64 = nullptr;  // FP64 V_mu [4][9][site]
     void* W64 = nullptr;      // FP64 W [40][9][site] (Brillouin; kept for F64 handles, lazy otherwise)
     void* links_df = nullptr; // the same in double-float storage (dirac_df.cuh), for the residual (lazy)
+    void* links32 = nullptr;  // FP32 V_mu, blocked layout, for the split inner solve (lazy)
     void* links64b = nullptr; // FP64 links of the operator (V or W) in the blocked layout of the
                               // sweeps, for the solver's FP64 residual (lazy; F64 handles use links)
     bool have_links = false;
@@ -58,6 +60,7 @@ struct dirac_handle {
     dirac_status build_W64();
     dirac_status ensure_links64b(const void** out);
     dirac_status ensure_links_df(const void** out);
+    dirac_status ensure_links32(const void** out);
     dirac::ApplyArgs args(void* out, const void* in, int nv, double diag_value) const;
     dirac_status run_apply(bool dagger, void* out, const void* in, int nv, double diag_value,
                            const void* link_ptr, int p, dirac::LaunchCfg c, const double* diag_v = nullptr,

@@ -136,10 +136,13 @@ struct SolverWS {
     int prec = 0;
     bool eo = false;                                          // even-odd inner solve (half fields)
     bool cg = false;                                          // CG on the hermitian Schur complement
+    bool split = false;                                       // split fields (see dirac_set_inner_fields)
+    int pa = 0, pd = 0;   // precision of e, r, t, tmp, re, ro (pa) and of p, s, tmp2 (pd); = prec unless split
     void *b64 = nullptr, *x64 = nullptr, *r64 = nullptr;     // FP64 internal fields
-    // storage precision: whole-lattice fields, or odd half fields when eo
+    // inner fields: whole-lattice fields, or odd half fields when eo
     void *e = nullptr, *r = nullptr, *s = nullptr, *p = nullptr, *t = nullptr;
     void *tmp = nullptr, *re = nullptr, *ro = nullptr;        // eo: even scratch, r_hat halves
+    void* tmp2 = nullptr;                                     // split: the adjoint sweep's intermediate
     void* xdf = nullptr;                                      // x in double-float storage (lazy)
     size_t n = 0;                                             // complex numbers per rhs of the inner fields
     double* part = nullptr;                                   // reduction partials
@@ -168,7 +171,8 @@ void dirac_handle::free_solver_workspace()
     if (w->gexec) cudaGraphExecDestroy(w->gexec);
     if (w->ev) cudaEventDestroy(w->ev);
     if (w->cs) cudaStreamDestroy(w->cs);
-    void** ptrs[] = {&w->b64, &w->x64, &w->r64, &w->e, &w->r, &w->s, &w->p, &w->t, &w->tmp, &w->re, &w->ro, &w->xdf};
+    void** ptrs[] = {&w->b64, &w->x64, &w->r64, &w->e, &w->r, &w->s, &w->p, &w->t, &w->tmp, &w->re, &w->ro, &w->xdf,
+                     &w->tmp2};
     for (void** q : ptrs) release(*q);
     void* pp = w->part;
     release(pp);
@@ -182,10 +186,10 @@ void dirac_handle::free_solver_workspace()
     sw_nv = 0;
 }
 
-static dirac_status ensure_solver_ws(dirac_handle* h, bool eo, SolverWS** out)
+static dirac_status ensure_solver_ws(dirac_handle* h, bool eo, bool split, SolverWS** out)
 {
     SolverWS* w = (SolverWS*)h->sw;
-    if (w && w->W == h->Nv && w->prec == h->prec && w->eo == eo) {
+    if (w && w->W == h->Nv && w->prec == h->prec && w->eo == eo && w->split == split) {
         *out = w;
         return DIRAC_OK;
     }
@@ -195,25 +199,33 @@ static dirac_status ensure_solver_ws(dirac_handle* h, bool eo, SolverWS** out)
     w->W = h->Nv;
     w->prec = h->prec;
     w->eo = eo;
+    w->split = split;
     w->cg = eo && h->op == OP_STAGGERED;
+    w->pa = split ? P_F32 : h->prec;
+    w->pd = h->prec;
     const size_t nfull = (size_t)nsc_of(h->op) * nblk_of((size_t)h->g.vol) * 32;
     w->n = eo ? eo_half_n(h->op, h->g.vol) : nfull;
-    const size_t f64 = nfull * h->Nv * 16, fp = w->n * h->Nv * cbytes(h->prec);
+    const size_t f64 = nfull * h->Nv * 16, fa = w->n * h->Nv * cbytes(w->pa), fd = w->n * h->Nv * cbytes(w->pd);
     dirac_status st;
     if ((st = h->alloc(&w->b64, f64, "solver b"))) return st;
     if ((st = h->alloc(&w->x64, f64, "solver x"))) return st;
     if ((st = h->alloc(&w->r64, f64, "solver r"))) return st;
-    void** inner[] = {&w->e, &w->r, &w->s, &w->p, &w->t, &w->tmp, &w->re, &w->ro};
-    const int ninner = eo ? 8 : 5;
-    for (int i = 0; i < ninner; ++i)
-        if ((st = h->alloc(inner[i], fp, "solver inner field"))) return st;
+    // e, r, t, tmp, re, ro in pa; s, p, tmp2 in pd
+    void** inner[] = {&w->e, &w->r, &w->t, &w->s, &w->p, &w->tmp, &w->re, &w->ro, &w->tmp2};
+    const bool in_pa[] = {true, true, true, false, false, true, true, true, false};
+    const int ninner = split ? 9 : (eo ? 8 : 5);
+    size_t inner_bytes = 0;
+    for (int i = 0; i < ninner; ++i) {
+        const size_t fb = in_pa[i] ? fa : fd;
+        if ((st = h->alloc(inner[i], fb, "solver inner field"))) return st;
+        if ((st = h->cuda(cudaMemset(*inner[i], 0, fb), "solver field clear"))) return st;
+        inner_bytes += fb;
+    }
     // the padding sites of the last block of 32 stay zero (the vector kernels
     // run over whole blocks; the sweeps and packs write only real sites)
     void** fields64[] = {&w->b64, &w->x64, &w->r64};
     for (void** q : fields64)
         if ((st = h->cuda(cudaMemset(*q, 0, f64), "solver field clear"))) return st;
-    for (int i = 0; i < ninner; ++i)
-        if ((st = h->cuda(cudaMemset(*inner[i], 0, fp), "solver field clear"))) return st;
     void* pp = nullptr;
     if ((st = h->alloc(&pp, 2 * blas_partials(nfull, h->Nv) * sizeof(double), "solver partials"))) return st;
     w->part = (double*)pp;
@@ -231,7 +243,7 @@ static dirac_status ensure_solver_ws(dirac_handle* h, bool eo, SolverWS** out)
     w->iflags = (int*)pp;
     if ((st = h->cuda(cudaStreamCreateWithFlags(&w->cs, cudaStreamNonBlocking), "solver stream"))) return st;
     if ((st = h->cuda(cudaEventCreateWithFlags(&w->ev, cudaEventDisableTiming), "solver event"))) return st;
-    h->sw_bytes = 3 * f64 + ninner * fp;
+    h->sw_bytes = 3 * f64 + inner_bytes;
     h->sw_nv = h->Nv;
     w->dh.assign(h->Nv, h->diag);
     *out = w;
@@ -269,18 +281,43 @@ static dirac_status upload_eo_coef(dirac_handle* h, SolverWS* w)
 }
 
 // one even-odd sweep out = alpha in2 + beta H in (or H^+) on the sites of parity par
-static dirac_status eo_sweep(dirac_handle* h, SolverWS* w, bool dag, int par, void* out, const void* in,
-                             const void* in2, int set)
+static LaunchCfg eo_cfg_of(const dirac_handle* h, const SolverWS* w)
 {
     LaunchCfg c = h->eo_cfg;
     if (c.R == 0 || !eo_rhs_supported(h->op, w->prec, w->W, c.R))
         c = eo_default_config(h->op, w->prec, w->W, h->g.L[3]);
-    const EoArgs a = make_eo_args(h->g, w->W, par, in, in2, out, h->links, eo_coef(w, set), c.order);
-    return h->cuda(launch_eo(h->op, w->prec, dag, a, c, h->stream), "solve: even-odd sweep");
+    return c;
+}
+
+// one even-odd sweep with every field in precision w->pa (the links of that
+// precision: the handle's, or the FP32 copy of the split solve)
+static dirac_status eo_sweep(dirac_handle* h, SolverWS* w, bool dag, int par, void* out, const void* in,
+                             const void* in2, int set)
+{
+    const LaunchCfg c = eo_cfg_of(h, w);
+    const void* L = h->links;
+    dirac_status st;
+    if (w->split && (st = h->ensure_links32(&L))) return st;
+    const EoArgs a = make_eo_args(h->g, w->W, par, in, in2, out, L, eo_coef(w, set), c.order);
+    return h->cuda(launch_eo(h->op, w->pa, dag, a, c, h->stream), "solve: even-odd sweep");
+}
+
+// one sweep of the split solve (EO_SPLIT_*)
+static dirac_status eo_split_sweep(dirac_handle* h, SolverWS* w, int kind, int par, void* out, const void* in,
+                                   const void* in2, int set)
+{
+    const LaunchCfg c = eo_cfg_of(h, w);
+    const void* L = nullptr;
+    dirac_status st;
+    if ((st = h->ensure_links32(&L))) return st;
+    const EoArgs a = make_eo_args(h->g, w->W, par, in, in2, out, L, eo_coef(w, set), c.order);
+    return h->cuda(launch_eo_wilson_split(w->pd, kind, a, c, h->stream), "solve: even-odd sweep");
 }
 
 // out = A in (or A^+ in), A the operator of the inner solve: D on the whole
-// lattice, or the Schur complement S on the odd half fields
+// lattice, or the Schur complement S on the odd half fields.  Split fields:
+// A p reads p in 16 bits and writes t in FP32; A^+ r reads r in FP32 and
+// writes s in 16 bits.
 static dirac_status apply_inner(dirac_handle* h, SolverWS* w, bool dag, void* out, const void* in,
                                 const double* diag_v)
 {
@@ -288,6 +325,14 @@ static dirac_status apply_inner(dirac_handle* h, SolverWS* w, bool dag, void* ou
         return h->run_apply(dag, out, in, w->W, h->diag, h->links, w->prec, h->cfg, diag_v, 0, 0,
                             diag_v ? w->diag_vf : nullptr);
     dirac_status st;
+    if (w->split) {
+        if (!dag) {
+            if ((st = eo_split_sweep(h, w, EO_SPLIT_HP, 0, w->tmp, in, nullptr, EO_HOP))) return st;
+            return eo_split_sweep(h, w, EO_SPLIT_SP, 1, out, w->tmp, in, EO_S);
+        }
+        if ((st = eo_split_sweep(h, w, EO_SPLIT_HR, 0, w->tmp2, in, nullptr, EO_HOP))) return st;
+        return eo_split_sweep(h, w, EO_SPLIT_SR, 1, out, w->tmp2, in, EO_S);
+    }
     if ((st = eo_sweep(h, w, dag, 0, w->tmp, in, nullptr, EO_HOP))) return st;   // H_eo in
     return eo_sweep(h, w, dag, 1, out, w->tmp, in, EO_S);                         // a in - H_oe (.) / a
 }
@@ -316,15 +361,18 @@ static dirac_status enqueue_iteration(dirac_handle* h, SolverWS* w, const double
         k_cgls_beta<<<sb, 128, 0, S>>>(W, w->rr, w->gamma, active, w->beta);
         if ((st = h->cuda(blas_xpay(P, n, W, w->r, w->beta, w->p, S), "solve: p = r + beta p"))) return st;
     } else {
-        if ((st = h->cuda(blas_norm2(P, n, W, w->t, w->part, w->delta, S), "solve: |t|"))) return st;
+        // t = A p (pa), delta = |t|^2, e += alpha p, r -= alpha t (pa; p in pd),
+        // s = A^+ r (pd), gamma' = |s|^2, p = s + beta p (pd)
+        if ((st = h->cuda(blas_norm2(w->pa, n, W, w->t, w->part, w->delta, S), "solve: |t|"))) return st;
         k_cgls_alpha<<<sb, 128, 0, S>>>(W, w->gamma, w->delta, active, w->alpha, breakdown);
-        if ((st = h->cuda(blas_cgls_step(P, n, W, w->alpha, w->e, w->p, w->r, w->t, w->part, w->rr, S),
-                          "solve: step")))
-            return st;
+        const cudaError_t ce =
+            w->split ? blas_cgls_step_split(w->pd, n, W, w->alpha, w->e, w->p, w->r, w->t, w->part, w->rr, S)
+                     : blas_cgls_step(P, n, W, w->alpha, w->e, w->p, w->r, w->t, w->part, w->rr, S);
+        if ((st = h->cuda(ce, "solve: step"))) return st;
         if ((st = apply_inner(h, w, true, w->s, w->r, diag_v))) return st;
-        if ((st = h->cuda(blas_norm2(P, n, W, w->s, w->part, w->gnew, S), "solve: |s|"))) return st;
+        if ((st = h->cuda(blas_norm2(w->pd, n, W, w->s, w->part, w->gnew, S), "solve: |s|"))) return st;
         k_cgls_beta<<<sb, 128, 0, S>>>(W, w->gnew, w->gamma, active, w->beta);
-        if ((st = h->cuda(blas_xpay(P, n, W, w->s, w->beta, w->p, S), "solve: p = s + beta p"))) return st;
+        if ((st = h->cuda(blas_xpay(w->pd, n, W, w->s, w->beta, w->p, S), "solve: p = s + beta p"))) return st;
     }
     k_cgls_mask<<<1, 256, 0, S>>>(W, w->rr, w->rr0, w->itol2, active, nactive);
     return h->cuda(cudaGetLastError(), "solve: scalar kernels");
@@ -381,7 +429,7 @@ static dirac_status inner_cgls(dirac_handle* h, SolverWS* w, const double* diag_
     if ((st = h->cuda(cudaMemcpyAsync(w->itol2, &itol2, sizeof(double), cudaMemcpyHostToDevice, S), "solve: copy")))
         return st;
     if ((st = h->cuda(cudaMemsetAsync(w->iflags + W, 0, 2 * sizeof(int), S), "solve: memset"))) return st;
-    if ((st = h->cuda(cudaMemsetAsync(w->e, 0, n * W * cbytes(P), S), "solve: e = 0"))) return st;
+    if ((st = h->cuda(cudaMemsetAsync(w->e, 0, n * W * cbytes(w->pa), S), "solve: e = 0"))) return st;
     if (w->cg) {
         // p = r, gamma = |r|^2
         if ((st = h->cuda(blas_scale_copy(P, n, W, w->r, nullptr, w->p, w->part, w->gamma, S), "solve: p = r")))
@@ -390,7 +438,7 @@ static dirac_status inner_cgls(dirac_handle* h, SolverWS* w, const double* diag_
         // s = A^+ r, p = s, gamma = |s|^2
         if ((st = apply_inner(h, w, true, w->s, w->r, diag_v))) return st;
         S_->sweeps++;
-        if ((st = h->cuda(blas_scale_copy(P, n, W, w->s, nullptr, w->p, w->part, w->gamma, S), "solve: p = s")))
+        if ((st = h->cuda(blas_scale_copy(w->pd, n, W, w->s, nullptr, w->p, w->part, w->gamma, S), "solve: p = s")))
             return st;
     }
     const int sweeps_per_it = w->cg ? 1 : 2;
@@ -465,15 +513,15 @@ static dirac_status refine_step(dirac_handle* h, SolverWS* w, const double* diag
     }
     // even-odd: r_hat -> (r_e, r_o); the Schur right-hand side r = r_o - H_oe r_e / a
     if ((st = upload_eo_coef(h, w))) return st;
-    if ((st = h->cuda(eo_split(P, nsc_of(h->op), h->g, W, w->r64, w->scale, w->re, w->ro, S), "solve: r_hat")))
+    if ((st = h->cuda(eo_split(w->pa, nsc_of(h->op), h->g, W, w->r64, w->scale, w->re, w->ro, S), "solve: r_hat")))
         return st;
     if ((st = eo_sweep(h, w, false, 1, w->r, w->re, w->ro, EO_RHS))) return st;
-    if ((st = h->cuda(blas_norm2(P, w->n, W, w->r, w->part, w->rr0, S), "solve: |r|"))) return st;
+    if ((st = h->cuda(blas_norm2(w->pa, w->n, W, w->r, w->part, w->rr0, S), "solve: |r|"))) return st;
     if ((st = inner_cgls(h, w, diag_v, max_inner, inner_tol, S_, &bd))) return st;
     // e_e = (r_e - H_eo e_o) / a, then x += (|r| / sqrt(n)) (e_e, e_o)
     if ((st = eo_sweep(h, w, false, 0, w->tmp, w->e, w->re, EO_REC))) return st;
     S_->sweeps++;   // the two half sweeps around the inner solve
-    return h->cuda(eo_axpy_to64(P, nsc_of(h->op), h->g, W, w->coef, w->tmp, w->e, w->x64, S), "solve: x update");
+    return h->cuda(eo_axpy_to64(w->pa, nsc_of(h->op), h->g, W, w->coef, w->tmp, w->e, w->x64, S), "solve: x update");
 }
 
 // r64 = b64 - D x64 with FP64 links and FP64 data, rr64 (host) = |r|^2 per
@@ -559,6 +607,13 @@ static bool use_even_odd(const dirac_handle* h, const double* diag, int ndiag)
     return true;
 }
 
+// whether the even-odd inner solve keeps split fields: asked for, Wilson
+// (CGLS), 16-bit storage
+static bool use_split(const dirac_handle* h, bool eo)
+{
+    return eo && h->inner_fields == 1 && h->op == OP_WILSON && (h->prec == P_BF16 || h->prec == P_F16);
+}
+
 static dirac_status check_solver_args(dirac_handle* h, double tol, int max_outer, int max_inner, double inner_tol,
                                       const char* name)
 {
@@ -583,7 +638,8 @@ extern "C" DIRAC_API dirac_status dirac_solve(dirac_handle* h, void* x, const vo
         return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_solve: x and b must be device pointers");
     if (h->op == OP_BRILLOUIN && (st = h->build_W64())) return st;
     SolverWS* w;
-    if ((st = ensure_solver_ws(h, use_even_odd(h, &h->diag, 1), &w))) return st;
+    const bool eo = use_even_odd(h, &h->diag, 1);
+    if ((st = ensure_solver_ws(h, eo, use_split(h, eo), &w))) return st;
     w->dh.assign(h->Nv, h->diag);
     OnPrivateStream guard(h, w);
     const int Nv = h->Nv, nsc = nsc_of(h->op);
@@ -630,6 +686,7 @@ extern "C" DIRAC_API dirac_status dirac_solve(dirac_handle* h, void* x, const vo
     S_.outer_iterations = outer;
     S_.even_odd = w->eo ? 1 : 0;
     S_.df_residual = df ? 1 : 0;
+    S_.split_fields = w->split ? 1 : 0;
     CK(launch_unpack_spinor(P_F64, nsc, h->g, Nv, w->x64, x, true, S), "solve: unpack x");
     CK(cudaStreamSynchronize(S), "solve: sync");
 #undef CK
@@ -673,7 +730,8 @@ extern "C" DIRAC_API dirac_status dirac_solve_batched(dirac_handle* h, int nsys,
     std::vector<double> sys_diag(nsys);
     for (int i = 0; i < nsys; ++i) sys_diag[i] = h->diag_of(mass_i[i]);
     SolverWS* w;
-    if ((st = ensure_solver_ws(h, use_even_odd(h, sys_diag.data(), nsys), &w))) return st;
+    const bool eo = use_even_odd(h, sys_diag.data(), nsys);
+    if ((st = ensure_solver_ws(h, eo, use_split(h, eo), &w))) return st;
     OnPrivateStream guard(h, w);
     const int W = w->W, nsc = nsc_of(h->op);
     const size_t n = (size_t)nsc * nblk_of((size_t)h->g.vol) * 32;
@@ -798,6 +856,7 @@ extern "C" DIRAC_API dirac_status dirac_solve_batched(dirac_handle* h, int nsys,
     S_.residual_max = rmax;
     S_.even_odd = w->eo ? 1 : 0;
     S_.df_residual = df ? 1 : 0;
+    S_.split_fields = w->split ? 1 : 0;
     S_.seconds = std::chrono::duration<double>(clk::now() - t0).count();
     if (stats) *stats = S_;
     if (any_breakdown) return h->fail(DIRAC_BREAKDOWN, "dirac_solve_batched: non-finite residual");

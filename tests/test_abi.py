@@ -66,6 +66,8 @@ def test_null_handle_calls(dg):
     assert dg.dirac_get_preconditioner(None, None) == dg.ERR_INVALID_ARG
     assert dg.dirac_set_residual_arithmetic(None, 1) == dg.ERR_INVALID_ARG
     assert dg.dirac_get_residual_arithmetic(None, None) == dg.ERR_INVALID_ARG
+    assert dg.dirac_set_inner_fields(None, 1) == dg.ERR_INVALID_ARG
+    assert dg.dirac_get_inner_fields(None, None) == dg.ERR_INVALID_ARG
     assert dg.dirac_set_links(None, None, 0, 0) == dg.ERR_INVALID_ARG
     assert dg.dirac_destroy(None) == dg.OK
 
@@ -160,6 +162,8 @@ def test_binding_calls_match_the_c_signatures(dg, monkeypatch):
     D.preconditioner()
     D.set_residual_arithmetic(0)
     D.residual_arithmetic()
+    D.set_inner_fields(1)
+    D.inner_fields()
     D.autotune()
     D.solve(x.to(torch.complex128), x0=x.to(torch.complex128))
     D.solve_batched([x.to(torch.complex128)] * 2, [0.12, 0.121])
@@ -168,7 +172,7 @@ def test_binding_calls_match_the_c_signatures(dg, monkeypatch):
                  "dirac_set_kernel_config", "dirac_get_kernel_config", "dirac_autotune", "dirac_destroy",
                  "dirac_solve_batched", "dirac_set_site_order", "dirac_get_site_order", "dirac_apply_host",
                  "dirac_set_preconditioner", "dirac_get_preconditioner", "dirac_set_residual_arithmetic",
-                 "dirac_get_residual_arithmetic"):
+                 "dirac_get_residual_arithmetic", "dirac_set_inner_fields", "dirac_get_inner_fields"):
         assert name in calls, name
 
 

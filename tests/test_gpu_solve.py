@@ -130,6 +130,39 @@ def test_solve_residual_arithmetic(dg, op, mass):
     D.close()
 
 
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+def test_solve_split_inner_fields(dg, prec):
+    """Split inner fields for 16-bit Wilson handles (FP32 solution, residual,
+    operator products and links; 16-bit search directions): single and
+    batched solves certified by the oracle, and fewer refinement steps than
+    with every inner field in 16 bits (the inner solve reaches FP32-level
+    reductions)."""
+    L, Nv = (4, 4, 4, 8), 4
+    V = links_for(prec, synth.gauge_links(L, 3, "near_identity", 350))
+    b = synth.spinor(L, Nv, 4, 3, 351)
+    D = dg.Dirac("wilson", L, Nv, 0.1235, prec)
+    D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
+    assert D.inner_fields() == 0   # the default
+    m0 = oracle.kappa_to_m0(0.1235)
+    outer = {}
+    for mode in (1, 0):
+        D.set_inner_fields(mode)
+        x, res, st, status = D.solve(torch.from_numpy(b).cuda(), tol=1e-10, max_outer=60, max_inner=3000)
+        assert status == dg.OK, (mode, res, st)
+        assert st["split_fields"] == mode and st["even_odd"] == 1
+        true_res = oracle_residual("wilson", V, x.cpu().numpy(), b, m0)
+        assert true_res.max() <= 1e-10, (mode, true_res)
+        outer[mode] = st["outer_iterations"]
+    D.close()
+    assert outer[1] < outer[0], outer
+    nv_list, kap = [1, 3, 2, 4, 1], [0.120, 0.1225, 0.124, 0.121, 0.1232]
+    V, bs, xs, res, sys_stats, tot, status = _batched_case(dg, "wilson", (4, 4, 2, 4), nv_list, kap, prec, 4, 360,
+                                                          inner_fields=1)
+    assert status == dg.OK and tot["split_fields"] == 1, (sys_stats, tot)
+    for bi, xi, k in zip(bs, xs, kap):
+        assert oracle_residual("wilson", V, xi, bi, oracle.kappa_to_m0(k)).max() <= 1e-10
+
+
 def test_solve_resume_and_zero_rhs(dg):
     """x0 = the solution: no refinement step is taken; a zero right-hand side
     converges at once; the result does not depend on the other columns."""
@@ -162,11 +195,12 @@ def test_solve_not_converged_status(dg):
     D.close()
 
 
-def _batched_case(dg, op, L, nv_list, masses, prec, window, seed, tol=1e-10, precond=1):
+def _batched_case(dg, op, L, nv_list, masses, prec, window, seed, tol=1e-10, precond=1, inner_fields=0):
     V = links_for(prec, synth.gauge_links(L, 3, "near_identity", seed))
     bs = [synth.spinor(L, nv, NS[op], 3, seed + 1 + i) for i, nv in enumerate(nv_list)]
     D = dg.Dirac(op, L, window, masses[0], prec)
     D.set_preconditioner(precond)
+    D.set_inner_fields(inner_fields)
     D.set_links(torch.from_numpy(V.astype(np.complex64 if prec != "f64" else np.complex128)).cuda())
     xs, res, sys_stats, tot, status = D.solve_batched([torch.from_numpy(b).cuda() for b in bs], masses, tol=tol,
                                                       max_outer=40, max_inner=4000)
