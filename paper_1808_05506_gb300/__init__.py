@@ -324,7 +324,7 @@ class Dirac:
         import numpy as np
         torch = _torch()
         if inner_tol is None:
-            inner_tol = self._default_inner_tol()
+            inner_tol = 0.0   # the library's default for the inner solve that runs
         b = self._canon_in(b, "b", dtype=torch.complex128)
         x = torch.zeros_like(b) if x0 is None else self._canon_in(x0, "x0", dtype=torch.complex128).clone()
         res = np.zeros(self.Nv, dtype=np.float64)
@@ -345,7 +345,7 @@ class Dirac:
         import numpy as np
         torch = _torch()
         if inner_tol is None:
-            inner_tol = self._default_inner_tol()
+            inner_tol = 0.0   # the library's default for the inner solve that runs
         nsys = len(bs)
         Nx, Ny, Nz, Nt = self.L
         for i, b in enumerate(bs):
@@ -416,19 +416,10 @@ class Dirac:
         check(lib().dirac_get_preconditioner(self.h, ctypes.byref(t)), self.h, "dirac_get_preconditioner")
         return t.value
 
-    def _default_inner_tol(self) -> float:
-        # the reduction one inner solve can reach in its storage precision; split
-        # fields (16-bit Wilson, see set_inner_fields) reach FP32's
-        split = getattr(self, "_inner_fields", 0) == 1 and self.op == "wilson" and self.prec in ("bf16", "f16")
-        if split:
-            return 1e-5
-        return {"f64": 1e-10, "f32": 1e-5, "f16": 2e-3, "bf16": 1e-2}[self.prec]
-
     def set_inner_fields(self, mode: int):
         """16-bit Wilson even-odd inner solves: 1 split fields (FP32 e, r, t; 16-bit p, s), 0 all
         16-bit; see dirac_set_inner_fields."""
         check(lib().dirac_set_inner_fields(self.h, mode), self.h, "dirac_set_inner_fields")
-        self._inner_fields = int(mode)
 
     def inner_fields(self) -> int:
         t = I()

@@ -20,7 +20,7 @@ struct dirac_handle {
     dirac::LaunchCfg cfg{1, 128, dirac::V_DIRECT};
     int precond = 1;          // inner solves: 1 even-odd where it applies, 0 whole lattice
     int outer_df = 1;         // outer residual: 1 double-float sweep (non-FP64 handles), 0 FP64
-    int inner_fields = 0;     // 16-bit Wilson even-odd inner solves: 1 split fields, 0 all 16-bit
+    int inner_fields = 1;     // 16-bit Wilson even-odd inner solves: 1 split fields, 0 all 16-bit
     dirac::LaunchCfg eo_cfg{0, 0, 0, 0};   // launch shape of the even-odd sweeps (R = 0: not tuned)
 
     void* links = nullptr;    // storage-precision links [m][9][site] (m = mu, or 40 stored W)

@@ -607,6 +607,16 @@ static bool use_even_odd(const dirac_handle* h, const double* diag, int ndiag)
     return true;
 }
 
+// inner_tol = 0: the reduction an inner solve can reach with the fields it
+// keeps -- FP64 1e-10; FP32 (or split fields, whose residual is FP32) 1e-5;
+// FP16 2e-3; BF16 1e-2
+static double default_inner_tol(const SolverWS* w)
+{
+    if (w->pa == P_F64) return 1e-10;
+    if (w->pa == P_F32) return 1e-5;
+    return w->pd == P_F16 ? 2e-3 : 1e-2;
+}
+
 // whether the even-odd inner solve keeps split fields: asked for, Wilson
 // (CGLS), 16-bit storage
 static bool use_split(const dirac_handle* h, bool eo)
@@ -618,9 +628,9 @@ static dirac_status check_solver_args(dirac_handle* h, double tol, int max_outer
                                       const char* name)
 {
     if (!h->have_links) return h->fail(DIRAC_ERR_INVALID_ARG, "%s: call dirac_set_links first", name);
-    if (!(tol > 0.0) || max_outer < 1 || max_inner < 1 || !(inner_tol > 0.0) || !(inner_tol < 1.0))
+    if (!(tol > 0.0) || max_outer < 1 || max_inner < 1 || !(inner_tol >= 0.0) || !(inner_tol < 1.0))
         return h->fail(DIRAC_ERR_INVALID_ARG,
-                       "%s: need tol > 0, max_outer >= 1, max_inner >= 1, 0 < inner_tol < 1", name);
+                       "%s: need tol > 0, max_outer >= 1, max_inner >= 1, 0 <= inner_tol < 1", name);
     return DIRAC_OK;
 }
 
@@ -641,6 +651,7 @@ extern "C" DIRAC_API dirac_status dirac_solve(dirac_handle* h, void* x, const vo
     const bool eo = use_even_odd(h, &h->diag, 1);
     if ((st = ensure_solver_ws(h, eo, use_split(h, eo), &w))) return st;
     w->dh.assign(h->Nv, h->diag);
+    if (inner_tol == 0.0) inner_tol = default_inner_tol(w);
     OnPrivateStream guard(h, w);
     const int Nv = h->Nv, nsc = nsc_of(h->op);
     const size_t n = (size_t)nsc * nblk_of((size_t)h->g.vol) * 32;
@@ -732,6 +743,7 @@ extern "C" DIRAC_API dirac_status dirac_solve_batched(dirac_handle* h, int nsys,
     SolverWS* w;
     const bool eo = use_even_odd(h, sys_diag.data(), nsys);
     if ((st = ensure_solver_ws(h, eo, use_split(h, eo), &w))) return st;
+    if (inner_tol == 0.0) inner_tol = default_inner_tol(w);
     OnPrivateStream guard(h, w);
     const int W = w->W, nsc = nsc_of(h->op);
     const size_t n = (size_t)nsc * nblk_of((size_t)h->g.vol) * 32;

@@ -142,7 +142,7 @@ def test_solve_split_inner_fields(dg, prec):
     b = synth.spinor(L, Nv, 4, 3, 351)
     D = dg.Dirac("wilson", L, Nv, 0.1235, prec)
     D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
-    assert D.inner_fields() == 0   # the default
+    assert D.inner_fields() == 1   # the default
     m0 = oracle.kappa_to_m0(0.1235)
     outer = {}
     for mode in (1, 0):
@@ -195,7 +195,7 @@ def test_solve_not_converged_status(dg):
     D.close()
 
 
-def _batched_case(dg, op, L, nv_list, masses, prec, window, seed, tol=1e-10, precond=1, inner_fields=0):
+def _batched_case(dg, op, L, nv_list, masses, prec, window, seed, tol=1e-10, precond=1, inner_fields=1):
     V = links_for(prec, synth.gauge_links(L, 3, "near_identity", seed))
     bs = [synth.spinor(L, nv, NS[op], 3, seed + 1 + i) for i, nv in enumerate(nv_list)]
     D = dg.Dirac(op, L, window, masses[0], prec)
