@@ -62,6 +62,11 @@ HD float df_fma(float a, float b, float c)
 #endif
 }
 
+// dfl and its operators live in a namespace of their own: they are found by
+// argument-dependent lookup for dfl operands only, and never hide the FP32 /
+// FP64 fma of the other kernel bodies from ordinary lookup
+namespace dd {
+
 struct dfl {
     float hi, lo;
     HD dfl() : hi(0.f), lo(0.f) {}
@@ -116,6 +121,10 @@ HD dfl operator*(dfl a, dfl b) { return fma(a, b, dfl()); }
 
 // the double nearest to hi + lo (exact: the two halves fit 53 bits)
 HD double df_to_double(dfl a) { return (double)a.hi + (double)a.lo; }
+
+}  // namespace dd
+
+using dd::dfl;
 
 struct f64df {
     float4 v;   // storage tag (never instantiated as data)
