@@ -316,7 +316,6 @@ dirac_status dirac_set_links(dirac_handle* h, const void* V, dirac_prec V_prec, 
     h->release(h->W64);
     h->release(h->links64b);
     h->release(h->links_df);
-    h->release(h->links32);
     const int nmat = (h->op == OP_BRILLOUIN) ? 40 : 4;
     if (!h->links && (st = h->alloc(&h->links, nblk_of((size_t)h->g.vol) * 32 * 9 * nmat * cbytes(h->prec), "links")))
         return st;
@@ -328,6 +327,12 @@ dirac_status dirac_set_links(dirac_handle* h, const void* V, dirac_prec V_prec, 
     } else {
         st = h->cuda(launch_convert_links(h->prec, h->g, 4, h->links64, h->links, h->stream), "links conversion");
         if (st) return st;
+        // the FP32 copy of the split inner solve is refreshed in place, like the
+        // storage links: a captured solver graph holds both addresses
+        if (h->links32 && h->links32 != h->links) {
+            st = h->cuda(launch_convert_links(P_F32, h->g, 4, h->links64, h->links32, h->stream), "FP32 links");
+            if (st) return st;
+        }
     }
     st = h->cuda(cudaStreamSynchronize(h->stream), "dirac_set_links");
     if (st) return st;

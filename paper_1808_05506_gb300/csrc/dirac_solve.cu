@@ -160,6 +160,7 @@ struct SolverWS {
     LaunchCfg g_eo_cfg{0, 0, 0};
     const void* g_links = nullptr;
     const double* g_diag = nullptr;
+    double g_dval = 0.0;
 };
 
 }  // namespace dirac
@@ -383,8 +384,9 @@ static dirac_status ensure_graph(dirac_handle* h, SolverWS* w, const double* dia
     auto same = [](const LaunchCfg& a, const LaunchCfg& b) {
         return a.R == b.R && a.block == b.block && a.variant == b.variant && a.order == b.order;
     };
+    // the whole-lattice sweeps take the handle's diagonal by value (dirac_set_mass may change it)
     if (w->gexec && same(w->g_cfg, h->cfg) && same(w->g_eo_cfg, h->eo_cfg) && w->g_links == h->links &&
-        w->g_diag == diag_v)
+        w->g_diag == diag_v && w->g_dval == h->diag)
         return DIRAC_OK;
     if (w->gexec) {
         cudaGraphExecDestroy(w->gexec);
@@ -409,6 +411,7 @@ static dirac_status ensure_graph(dirac_handle* h, SolverWS* w, const double* dia
     w->g_eo_cfg = h->eo_cfg;
     w->g_links = h->links;
     w->g_diag = diag_v;
+    w->g_dval = h->diag;
     return DIRAC_OK;
 }
 

@@ -163,6 +163,33 @@ def test_solve_split_inner_fields(dg, prec):
         assert oracle_residual("wilson", V, xi, bi, oracle.kappa_to_m0(k)).max() <= 1e-10
 
 
+def test_solve_after_set_mass_and_set_links(dg):
+    """A second solve on the same handle after dirac_set_mass, and after
+    dirac_set_links with new links, solves the current operator: the captured
+    inner-iteration graphs and the FP32 link copy of the split inner solve
+    follow the change (Brillouin: whole-lattice inner solve; BF16 Wilson:
+    even-odd with split fields)."""
+    L, Nv = (4, 4, 2, 4), 2
+    V = links_for("f32", synth.gauge_links(L, 3, "near_identity", 370))
+    b = synth.spinor(L, Nv, 4, 3, 371)
+    D = dg.Dirac("brillouin", L, Nv, 0.05, "f32")
+    D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
+    for m in (0.05, 0.2):
+        D.set_mass(m)
+        x, res, st, status = D.solve(torch.from_numpy(b).cuda(), tol=1e-10, max_outer=40, max_inner=3000)
+        assert status == dg.OK, (m, res, st)
+        assert oracle_residual("brillouin", V, x.cpu().numpy(), b, m).max() <= 1e-10
+    D.close()
+    V2 = links_for("f32", synth.gauge_links(L, 3, "near_identity", 372))
+    D = dg.Dirac("wilson", L, Nv, 0.122, "bf16")
+    for VV in (V, V2):
+        D.set_links(torch.from_numpy(VV.astype(np.complex64)).cuda())
+        x, res, st, status = D.solve(torch.from_numpy(b).cuda(), tol=1e-10, max_outer=40, max_inner=3000)
+        assert status == dg.OK and st["split_fields"] == 1, (res, st)
+        assert oracle_residual("wilson", VV, x.cpu().numpy(), b, oracle.kappa_to_m0(0.122)).max() <= 1e-10
+    D.close()
+
+
 def test_solve_resume_and_zero_rhs(dg):
     """x0 = the solution: no refinement step is taken; a zero right-hand side
     converges at once; the result does not depend on the other columns."""
