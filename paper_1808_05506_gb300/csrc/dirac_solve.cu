@@ -466,7 +466,7 @@ static dirac_status inner_cgls(dirac_handle* h, SolverWS* w, const double* diag_
         if ((st = h->cuda(cudaStreamSynchronize(S), "solve: sync"))) return st;
         if (flags[0]) {
             // a zero or non-finite curvature on an active right-hand side: stop the
-            // inner solve and let the FP64 outer residual judge the update
+            // inner solve and let the FP64 outer residual decide on the update
             *breakdown_out = true;
             break;
         }
