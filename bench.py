@@ -260,14 +260,18 @@ def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=(
     directions), 0 every inner field in 16 bits."""
     from paper_1808_05506_gb300 import sharding
     nsys = nsys * ws
-    rng = np.random.default_rng(7)
-    nvs = [int(v) for v in rng.integers(1, 25, nsys)]
-    kap = [float(v) for v in rng.uniform(0.120, 0.124, nsys)]
-    V = synth.gauge_links(L, 3, "near_identity", 1005, eps=0.3)
-
-    # this rank's right-hand sides, generated before any timing
-    local_b = {i: torch.from_numpy(synth.spinor(L, nvs[i], 4, 3, 2100 + i)).cuda()
-               for i in sharding.assign_systems(nvs, ws)[rank]}
+    key = (tuple(L), nsys, ws, rank)
+    if key not in _BATCHED_INPUTS:
+        rng = np.random.default_rng(7)
+        nvs = [int(v) for v in rng.integers(1, 25, nsys)]
+        kap = [float(v) for v in rng.uniform(0.120, 0.124, nsys)]
+        V = synth.gauge_links(L, 3, "near_identity", 1005, eps=0.3)
+        # this rank's right-hand sides, generated before any timing (and kept for
+        # the next call on the same systems)
+        local_b = {i: torch.from_numpy(synth.spinor(L, nvs[i], 4, 3, 2100 + i)).cuda()
+                   for i in sharding.assign_systems(nvs, ws)[rank]}
+        _BATCHED_INPUTS[key] = (nvs, kap, V, local_b)
+    nvs, kap, V, local_b = _BATCHED_INPUTS[key]
 
     def make_b(i):
         return local_b[i]
@@ -313,10 +317,11 @@ def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=(
                            else "whole lattice: CGLS on D")
     if inner_fields and precond:
         out["inner_solver"] += "; 16-bit storage: split fields (FP32 e, r, t and links, 16-bit p, s)"
-
-    del local_b
-    torch.cuda.empty_cache()
     return out
+
+
+# inputs of batched_solve_times, shared by its calls on the same systems
+_BATCHED_INPUTS = {}
 
 
 def cpu_oracle_rate(w, inputs=None, seconds=15.0):
@@ -537,6 +542,8 @@ def main():
         line["batched_solve_all16"] = uni
         # the same systems with the whole-lattice inner solver, for comparison
         line["batched_solve_whole_lattice"] = batched_solve_times(dg, torch, rank=rank, ws=ws, dist=dist, precond=0)
+        _BATCHED_INPUTS.clear()
+        torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_rate(w, inputs=(V, psi))
     if rank == 0:
