@@ -125,6 +125,10 @@ def test_binding_calls_match_the_c_signatures(dg, monkeypatch):
             argtypes = dg.SIGNATURES[self.name][1]
             assert len(args) == len(argtypes), (self.name, len(args), len(argtypes))
             calls.append(self.name)
+            if self.name in ("dirac_solve", "dirac_solve_batched"):
+                # inner_tol not given: 0, the library's choice for the inner solve that runs
+                inner_tol = args[6] if self.name == "dirac_solve" else args[9]
+                assert float(inner_tol) == 0.0, (self.name, inner_tol)
             return dg.OK if dg.SIGNATURES[self.name][0] is ctypes.c_int else b""
 
     class FakeLib:
