@@ -145,7 +145,7 @@ DIRAC_API dirac_status dirac_apply(dirac_handle* h, void* out, const void* in, d
  * fields in HOST memory (no counterpart in the paper, whose fields live in
  * the memory of the node that sweeps them): the same result as copying in
  * to the device, dirac_apply(..., DIRAC_CANONICAL) and copying out, with the
- * copies overlapped with the work.  The lattice is cut into about 8 slabs of
+ * copies overlapped with the work.  The lattice is cut into about 16 slabs of
  * t-slices; the host-to-device copy of one slab, the pack / sweep / unpack
  * of an earlier one and the device-to-host copy of a finished one run at
  * the same time on two copy streams of the handle and the handle's stream.
@@ -267,21 +267,27 @@ DIRAC_API dirac_status dirac_solve_batched(dirac_handle* h, int nsys, const int*
  * work fields of the canonical apply live in a fixed 64 MiB array inside the
  * library's device image instead of memory the handle allocates.  (This entry
  * point has no counterpart in the paper; it exists for callers that cannot
- * allocate while they run: code enqueuing into a stream that is being captured
- * into a CUDA graph, where cudaMalloc is not allowed; loops that cannot afford
- * the device synchronisation cudaMalloc / cudaFree may cause; and hosts whose
- * device memory is reserved up front by their own allocator.)
+ * allocate while they run: loops that cannot afford the device
+ * synchronisation cudaMalloc / cudaFree may cause, and hosts whose device
+ * memory is reserved up front by their own allocator, where a library
+ * allocation would fail or take memory the host has promised elsewhere.)
  *   - The array is reserved on every GPU that loads the library and kept
  *     until the process exits.
- *   - The first call on a device looks up the array's device address (once
- *     per device, with that device current); make that first call before any
- *     stream capture.  The handle's device must be the current device.
+ *   - The first call on a device (and the first after that device's context
+ *     was destroyed and recreated, e.g. by cudaDeviceReset) looks up the
+ *     array's device address with that device current; make that first call
+ *     before any stream capture.  The handle's device must be the current
+ *     device.
  *   - Fields whose two internal copies need more than 64 MiB (2 x
  *     dirac_field_bytes(h, DIRAC_INTERNAL), each rounded up to 256 bytes) are
- *     rejected with DIRAC_ERR_INVALID_ARG; use dirac_apply for those.
- *   - Every call uses the same array, and a call leaves its contents behind.
- *     Calls whose work overlaps on the GPU (other streams, other handles, other
- *     host threads) race on it: serialise them.
+ *     rejected with DIRAC_ERR_INVALID_ARG; use dirac_apply for those.  An
+ *     FP32 Wilson or Brillouin field takes 96 bytes per site and right-hand
+ *     side, so 2 x 96 x Nv x sites <= 64 MiB: 16^4 with Nv <= 5, 8^4 with
+ *     Nv <= 85 (BF16 / FP16 half of that, FP64 twice, staggered a quarter).
+ *   - Every call uses the same array, and a call leaves its contents behind
+ *     (the padding sites of the last block of 32 are never read, so nothing
+ *     needs clearing).  Calls whose work overlaps on the GPU (other streams,
+ *     other handles, other host threads) race on it: serialise them.
  * Requires dirac_set_links first.  Asynchronous on the handle's stream. */
 DIRAC_API dirac_status dirac_apply_static(dirac_handle* h, void* out, const void* in, int dagger);
 

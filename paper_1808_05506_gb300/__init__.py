@@ -10,6 +10,7 @@ loading fails loudly if the library has not been built.
 from __future__ import annotations
 
 import ctypes
+import weakref
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -172,6 +173,8 @@ class Dirac:
         check(st, None, "dirac_create")
         self.h = h
         self.canon_dtype = torch.complex128 if prec == "f64" else torch.complex64
+        self.links_generation = 0   # advanced by every set_links
+        self._links = None          # what set_links last loaded (set_links_if_changed)
 
     def close(self):
         if getattr(self, "h", None):
@@ -248,8 +251,11 @@ class Dirac:
         check(lib().dirac_set_stream(self.h, _stream_ptr(self._stream)), self.h, "dirac_set_stream")
 
     # -- calls ------------------------------------------------------------------
-    def set_links(self, V):
-        """V: canonical links (Nt, Nz, Ny, Nx, 4, 3, 3), complex128/complex64, host or device."""
+    def set_links(self, V, remember: bool = True):
+        """V: canonical links (Nt, Nz, Ny, Nx, 4, 3, 3), complex128/complex64, host or device.
+        remember: record V (a weak reference and its version counter) for
+        set_links_if_changed; False when V may change without its version
+        counter moving (writes through V.data)."""
         torch = _torch()
         if V.dtype not in (torch.complex128, torch.complex64):
             raise TypeError("links must be complex128 or complex64")
@@ -257,10 +263,34 @@ class Dirac:
         if V.numel() != Nx * Ny * Nz * Nt * 4 * self.Nc * self.Nc:
             raise ValueError(f"links must have {Nx * Ny * Nz * Nt * 4 * self.Nc * self.Nc} entries "
                              "(Nt, Nz, Ny, Nx, 4, 3, 3)")
-        V = V.contiguous()
-        prec = F64 if V.dtype == torch.complex128 else F32
+        key = self._links_key(V)
+        Vc = V.contiguous()
+        self._links = None
+        self._load_links(Vc, F64 if Vc.dtype == torch.complex128 else F32)
+        # what was loaded: a weak reference to the tensor object (a tensor
+        # freed and replaced by another at the same address does not match)
+        # and its version
+        self._links = (key, weakref.ref(V)) if remember else None
+        self.links_generation = getattr(self, "links_generation", 0) + 1
+
+    def _load_links(self, Vc, prec):
         self._sync_stream()
-        check(lib().dirac_set_links(self.h, _ptr(V), prec, 1 if V.is_cuda else 0), self.h, "dirac_set_links")
+        check(lib().dirac_set_links(self.h, _ptr(Vc), prec, 1 if Vc.is_cuda else 0), self.h, "dirac_set_links")
+
+    @staticmethod
+    def _links_key(V):
+        return (V.data_ptr(), V._version, tuple(V.shape), tuple(V.stride()), V.dtype, str(V.device))
+
+    def set_links_if_changed(self, V):
+        """set_links(V) unless V is the tensor last loaded and unchanged since:
+        the same memory, shape, dtype and version counter (which every tracked
+        in-place change advances; writes through V.data are not tracked, so
+        after those call set_links).  Returns True if the links were loaded."""
+        rec = getattr(self, "_links", None)
+        if rec is not None and rec[1]() is V and rec[0] == self._links_key(V):
+            return False
+        self.set_links(V)
+        return True
 
     def set_mass(self, mass: float):
         check(lib().dirac_set_mass(self.h, float(mass)), self.h, "dirac_set_mass")

@@ -7,6 +7,17 @@ backward: dL/dpsi = D^+ g (dirac_apply_dagger) and dL/dV = the link force
           PyTorch's convention for real losses of complex tensors
           (grad = dL/dRe + i dL/dIm), so that for L = Re <g, D psi> the
           gradients are exactly D^+ g and F.
+
+Loading the links into the handle (dirac_set_links: a conversion and, for
+Brillouin, the FP64 build of W) is skipped where it would load what is
+already there:
+  - backward reloads V only if the handle was given other links after this
+    node's forward pass (autograd itself rejects a V changed in place since);
+  - forward, with reuse_links=True (the default), skips the load when V is
+    the tensor object the handle last loaded and its version counter has not
+    moved, so a training loop over fixed links loads them once.  Writes
+    through V.data do not move the version counter: code that changes the
+    links that way (torch.autograd.gradcheck does) passes reuse_links=False.
 """
 from __future__ import annotations
 
@@ -17,8 +28,12 @@ from . import Dirac
 
 class DiracApply(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, psi, V, D: Dirac):
-        D.set_links(V.detach())
+    def forward(ctx, psi, V, D: Dirac, reuse_links: bool = True):
+        if reuse_links:
+            D.set_links_if_changed(V)
+        else:
+            D.set_links(V, remember=False)   # a later reuse_links=True call loads again
+        ctx.links_generation = D.links_generation
         out = D.apply(psi.detach().to(D.canon_dtype).contiguous())
         ctx.D = D
         ctx.save_for_backward(psi, V)
@@ -29,16 +44,16 @@ class DiracApply(torch.autograd.Function):
         D = ctx.D
         psi, V = ctx.saved_tensors
         g = g.to(D.canon_dtype).contiguous()
-        # the handle may have been reused with other links since the forward pass
-        D.set_links(V.detach())
+        if D.links_generation != ctx.links_generation:
+            D.set_links(V)   # the handle was given other links since the forward pass
         gpsi = gV = None
         if ctx.needs_input_grad[0]:
             gpsi = D.apply_dagger(g).to(psi.dtype)
         if ctx.needs_input_grad[1]:
             gV = D.force(psi.detach().to(D.canon_dtype).contiguous(), g).to(V.dtype)
-        return gpsi, gV, None
+        return gpsi, gV, None, None
 
 
-def dirac_apply(D: Dirac, psi: torch.Tensor, V: torch.Tensor) -> torch.Tensor:
+def dirac_apply(D: Dirac, psi: torch.Tensor, V: torch.Tensor, reuse_links: bool = True) -> torch.Tensor:
     """out = D(V) psi, differentiable in psi and V."""
-    return DiracApply.apply(psi, V, D)
+    return DiracApply.apply(psi, V, D, reuse_links)

@@ -9,6 +9,7 @@
 // Steps (all gathers, one write per output element, no atomics):
 //   1. G_dir(y) = dL/dW_dir(y) = sum_{v,s} g_v(y)_s (M_dir psi_v(y+dir))_s^+
 //      for the 80 directions, M_dir = rho_k (dir . gamma) - lambda_k / 2;
+//   (every step in FP64 arithmetic, whatever the storage precision)
 //   2. for k = 4, 3, 2 the (k-1)-hop gradients collect what the k-hop
 //      directions pass down: G_{d'}(y) += (1/k) H_a(y-a)^+ G_{d'+a}(y-a) over
 //      the hops a on the axes d' does not use;
@@ -78,7 +79,10 @@ __device__ __forceinline__ void mm(const cx<double>* Am, bool adag, const cx<dou
         }
 }
 
-// step 1: one thread per (site, direction j = 0..79)
+// step 1: one thread per (site, direction j = 0..79).  The arithmetic is FP64
+// for every storage precision: FP32 and 16-bit values are exact in FP64, so
+// G is the FP64 gradient of the stored psi and g (the steps below are FP64
+// as well), and F is rounded once, at its store.
 template <typename T>
 __global__ void __launch_bounds__(128) k_bri_gradW(Geom g, int Nv, const void* psi, const void* gv, double2* G81)
 {
@@ -96,14 +100,20 @@ __global__ void __launch_bounds__(128) k_bri_gradW(Geom g, int Nv, const void* p
     long nb = y;
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) nb += d[mu] > 0 ? fwd[mu] : (d[mu] < 0 ? bwd[mu] : 0);
-    const BriDirA<A> m = coeffs_of<A>(d);
-    cx<A> acc[9];
+    const BriDirA<double> m = coeffs_of<double>(d);
+    cx<double> acc[9];
 #pragma unroll
-    for (int e = 0; e < 9; ++e) acc[e] = cx<A>{A(0), A(0)};
+    for (int e = 0; e < 9; ++e) acc[e] = cx<double>{0.0, 0.0};
     for (int v = 0; v < Nv; ++v) {
-        cx<A> p[12], chi[12], gg[12];
-        load_spinor<T, 12>(psi, g.vol, v, nb, p);
-        load_spinor<T, 12>(gv, g.vol, v, y, gg);
+        cx<A> ps[12], gs[12];
+        load_spinor<T, 12>(psi, g.vol, v, nb, ps);
+        load_spinor<T, 12>(gv, g.vol, v, y, gs);
+        cx<double> p[12], chi[12], gg[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            p[k] = cx<double>{(double)ps[k].re, (double)ps[k].im};
+            gg[k] = cx<double>{(double)gs[k].re, (double)gs[k].im};
+        }
         bri_spin(m, p, chi);
 #pragma unroll
         for (int s = 0; s < 4; ++s)

@@ -1,7 +1,7 @@
 """GPU parity of the Dirac sweeps against the FP64 oracle, through the C ABI.
 
-Bar (stated in the benchmark spec for this path): relative L2 error per call
-<= 1e-6 in FP32 and <= 1e-13 in FP64, the oracle run on the same rounded
+Bar: relative L2 error per right-hand side, the maximum over the
+right-hand sides, <= 1e-6 in FP32 and <= 1e-13 in FP64, the oracle run on the same rounded
 inputs the GPU saw.  BF16/FP16 storage has no apply parity target; the sweep
 is checked against its own rounding bound (a few units of the storage
 precision's epsilon).
@@ -41,8 +41,14 @@ def inputs(op, L, Nv, prec, seed, kind="haar"):
     return V, psi
 
 
-def rel_l2(got, want):
-    return np.linalg.norm((got - want).ravel()) / np.linalg.norm(want.ravel())
+def rel_l2(got, want, rhs_axis=4):
+    """max over right-hand sides v of |got_v - want_v|_2 / |want_v|_2 (the
+    parity metric per right-hand side; rhs_axis is v's axis: 4 for canonical
+    fields (Nt, Nz, Ny, Nx, Nv, ...), 1 for sampled sites (n, Nv, ...))."""
+    n = got.shape[rhs_axis]
+    d = np.moveaxis(got - want, rhs_axis, 0).reshape(n, -1)
+    w = np.moveaxis(want, rhs_axis, 0).reshape(n, -1)
+    return float(np.max(np.linalg.norm(d, axis=1) / np.linalg.norm(w, axis=1)))
 
 
 def run(dg, op, L, Nv, mass, prec, V, psi, dagger=False, cfg=None, internal=False):
@@ -302,7 +308,7 @@ def test_wilson_full_size_sampled(dg):
                     y = D.unpack(yi).reshape(-1, Nv, 4, 3)
                     assert bool(torch.isfinite(torch.view_as_real(y)).all())
                     got = y[st].cpu().numpy().astype(np.complex128)
-                    assert rel_l2(got, want[dag]) <= TOL["f32"], (R, block, variant, dag)
+                    assert rel_l2(got, want[dag], rhs_axis=1) <= TOL["f32"], (R, block, variant, dag)
     D.close()
 
 
@@ -314,7 +320,7 @@ def test_brillouin_full_size_sampled(dg):
     got = run(dg, "brillouin", L, Nv, 0.05, "f32", V, psi).reshape(-1, Nv, 4, 3)
     sites = _sampled(L, 48, 8)
     want = oracle.apply("brillouin", V, psi, 0.05, sites=sites)
-    assert rel_l2(got[sites], want) <= TOL["f32"]
+    assert rel_l2(got[sites], want, rhs_axis=1) <= TOL["f32"]
 
 
 def test_error_paths(dg):

@@ -44,7 +44,8 @@ def test_force_vs_oracle_16x4(dg, op, mass, prec, tol):
     F = D.force(torch.from_numpy(psi).to(cdt).cuda(), torch.from_numpy(g).to(cdt).cuda()).cpu().numpy()
     D.close()
     want = oracle.force(op, V, psi, g, m0_of(op, mass))
-    assert np.linalg.norm(F - want) / np.linalg.norm(want) <= tol
+    err = np.linalg.norm(F - want) / np.linalg.norm(want)
+    assert err <= tol, err
 
 
 @pytest.mark.parametrize("op,mass", [("wilson", 0.121), ("staggered", 0.2)])
@@ -88,7 +89,7 @@ def test_autograd_function(dg, op, mass):
     psi = torch.from_numpy(synth.spinor(L, Nv, NS[op], 3, 2006)).cuda().requires_grad_(True)
     D = dg.Dirac(op, L, Nv, mass, "f64")
     # gradcheck: Jacobian of the differentiable apply by finite differences vs our backward
-    assert torch.autograd.gradcheck(lambda p, v: dirac_apply(D, p, v), (psi, V), eps=1e-6, atol=1e-7,
+    assert torch.autograd.gradcheck(lambda p, v: dirac_apply(D, p, v, reuse_links=False), (psi, V), eps=1e-6, atol=1e-7,
                                     rtol=1e-6, fast_mode=True)
     g = torch.from_numpy(synth.spinor(L, Nv, NS[op], 3, 3006)).cuda()
     out = dirac_apply(D, psi, V)
@@ -103,11 +104,13 @@ def test_autograd_function(dg, op, mass):
     D.close()
 
 
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-6)])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("f32", 1e-6)])
 @pytest.mark.parametrize("L", [(4, 4, 2, 6), (6, 6, 4, 4), (2, 3, 2, 4)])
 def test_brillouin_force_vs_oracle(dg, prec, tol, L):
     """The Brillouin link gradient through the rebuilt transporters against the
-    oracle's path enumeration; extent 2 makes paths reuse links."""
+    oracle's path enumeration; extent 2 makes paths reuse links.  Every step
+    of the GPU gradient runs in FP64 (the FP32 inputs are exact there), so
+    the FP32 result differs from the oracle's by its final rounding."""
     Nv = 3
     rin = "f64" if prec == "f64" else "f32"
     V = synth.round_to(synth.gauge_links(L, 3, "haar", 1010), rin)
@@ -119,7 +122,8 @@ def test_brillouin_force_vs_oracle(dg, prec, tol, L):
     F = D.force(torch.from_numpy(psi).to(cdt).cuda(), torch.from_numpy(g).to(cdt).cuda()).cpu().numpy()
     D.close()
     want = oracle.force("brillouin", V, psi, g, 0.05)
-    assert np.linalg.norm(F - want) / np.linalg.norm(want) <= tol
+    err = np.linalg.norm(F - want) / np.linalg.norm(want)
+    assert err <= tol, err
 
 
 def test_brillouin_force_finite_differences(dg):
@@ -162,7 +166,7 @@ def test_brillouin_autograd_function(dg):
     V = torch.from_numpy(synth.gauge_links(L, 3, "haar", 1013)).cuda().requires_grad_(True)
     psi = torch.from_numpy(synth.spinor(L, Nv, 4, 3, 2013)).cuda().requires_grad_(True)
     D = dg.Dirac("brillouin", L, Nv, 0.1, "f64")
-    assert torch.autograd.gradcheck(lambda p, v: dirac_apply(D, p, v), (psi, V), eps=1e-6, atol=1e-7,
+    assert torch.autograd.gradcheck(lambda p, v: dirac_apply(D, p, v, reuse_links=False), (psi, V), eps=1e-6, atol=1e-7,
                                     rtol=1e-6, fast_mode=True)
     g = torch.from_numpy(synth.spinor(L, Nv, 4, 3, 3013)).cuda()
     out = dirac_apply(D, psi, V)
