@@ -45,6 +45,7 @@ KERNEL_SOURCES = ["paper_1808_05506_gb300/csrc/dirac_kernels.cuh",
                   "paper_1808_05506_gb300/csrc/apply_wilson_f32.cu",
                   "paper_1808_05506_gb300/csrc/apply_wilson.cu"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "wilson_apply_traffic.json")
+NOMINAL_HBM_GBS = 7900.0   # HBM3e nominal bandwidth of one GB300 (the measured copy peak is lower)
 
 
 def kernel_hash() -> str:
@@ -265,7 +266,7 @@ def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=(
         rng = np.random.default_rng(7)
         nvs = [int(v) for v in rng.integers(1, 25, nsys)]
         kap = [float(v) for v in rng.uniform(0.120, 0.124, nsys)]
-        V = synth.gauge_links(L, 3, "near_identity", 1005, eps=0.3)
+        V = batched_links(L)
         # this rank's right-hand sides, generated before any timing (and kept for
         # the next call on the same systems)
         local_b = {i: torch.from_numpy(synth.spinor(L, nvs[i], 4, 3, 2100 + i)).cuda()
@@ -322,6 +323,104 @@ def batched_solve_times(dg, torch, L=(32, 32, 32, 64), nsys=4, slots=24, precs=(
 
 # inputs of batched_solve_times, shared by its calls on the same systems
 _BATCHED_INPUTS = {}
+_LINKS = {}
+
+
+def batched_links(L):
+    """The gauge field of the batched Wilson systems (exp(0.3 i H), seed 1005),
+    generated once per lattice and shared by the batched lines."""
+    key = tuple(L)
+    if key not in _LINKS:
+        _LINKS[key] = synth.gauge_links(L, 3, "near_identity", 1005, eps=0.3).astype(np.complex64)
+    return _LINKS[key]
+
+
+def c5_batched_times(dg, torch, precs=("f32", "bf16", "f16"), rank=0, ws=1, dist=None, L=(32, 32, 32, 64),
+                     nsys=48, slots=64, wave_cols=128):
+    """The full batched configuration: 48 Wilson systems D(kappa_i) x_i = b_i
+    on 32^3 x 64 sharing one gauge field, Nv_i ~ U{1..24}, kappa_i ~
+    U[0.120, 0.124] (the draw of the GPU test of this configuration), each
+    storage precision to a true FP64 residual of 1e-10 through
+    dirac_solve_batched with `slots` resident columns and the library's
+    defaults (even-odd inner solves, split inner fields for 16-bit storage,
+    double-float outer residual).  The sources are complex Gaussian fields
+    drawn on the device (one seeded generator per system) before each solve
+    call.  The FP64 b and x of all systems (about 440 GB) exceed one GPU, so
+    the systems go through the solver in waves of at most `wave_cols`
+    columns; the time is the sum of the solve calls.  With N ranks the
+    systems are shared out by sharding.assign_systems (strong scaling: the
+    48 systems in all) and the time is the slowest rank's."""
+    from paper_1808_05506_gb300 import sharding
+    rng = synth.rng(1005, synth.STREAM_MISC)
+    nvs = [int(v) for v in rng.integers(1, 25, nsys)]
+    kap = [float(v) for v in rng.uniform(0.120, 0.124, nsys)]
+    V = batched_links(L)
+    local = sharding.assign_systems(nvs, ws)[rank]
+    waves, cur, cols = [], [], 0
+    for i in local:
+        if cur and cols + nvs[i] > wave_cols:
+            waves.append(cur)
+            cur, cols = [], 0
+        cur.append(i)
+        cols += nvs[i]
+    if cur:
+        waves.append(cur)
+    Nx, Ny, Nz, Nt = L
+
+    def make_b(i):
+        g = torch.Generator(device="cuda")
+        g.manual_seed(2005 + i)
+        z = torch.randn((Nt, Nz, Ny, Nx, nvs[i], 4, 3, 2), dtype=torch.float64, device="cuda", generator=g)
+        return torch.view_as_complex(z.mul_(0.5 ** 0.5))
+
+    out = {}
+    for prec in precs:
+        D = dg.Dirac("wilson", L, slots, kap[0], prec)
+        D.set_links(torch.from_numpy(V).cuda())
+        D.autotune()
+        seconds, worst, outer, inner, sweeps, fp64_sweeps, ok = 0.0, 0.0, 0, 0, 0, 0, True
+        even_odd = split = df = None
+        for wave in waves:
+            bs = [make_b(i) for i in wave]
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            t0 = time.perf_counter()
+            xs, res, sst, tot, status = D.solve_batched(bs, [kap[i] for i in wave], tol=1e-10, max_outer=60,
+                                                        max_inner=8000)
+            torch.cuda.synchronize()
+            seconds += time.perf_counter() - t0
+            worst = max(worst, float(res.max()))
+            ok = ok and status == dg.OK and all(s["converged"] for s in sst)
+            outer = max(outer, tot["outer_iterations"])
+            inner += tot["inner_iterations"]
+            sweeps += tot["sweeps"]
+            fp64_sweeps += tot["fp64_sweeps"]
+            even_odd, split, df = tot["even_odd"], tot["split_fields"], tot["df_residual"]
+            del bs, xs
+            torch.cuda.empty_cache()   # the next wave's fields have other sizes
+        if dist:
+            tt = torch.tensor([seconds], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            seconds = float(tt.item())
+        out[prec] = {"seconds": seconds, "all_converged": ok, "max_rel_residual": worst,
+                     "outer_max": outer, "inner_iterations": inner, "sweeps": sweeps, "fp64_sweeps": fp64_sweeps,
+                     "even_odd": even_odd, "split_fields": split, "df_residual": df,
+                     "kernel": list(D.kernel_config())}
+        D.close()
+        torch.cuda.empty_cache()
+    if "f32" in out:
+        for p in precs:
+            if p != "f32":
+                out[p]["speedup_vs_f32"] = out["f32"]["seconds"] / out[p]["seconds"]
+    out["workload"] = "wilson_batched_solve_{}_{}sys_{}cols_{}slots".format("x".join(map(str, L)), nsys,
+                                                                          sum(nvs), slots)
+    out["systems"] = {"nv": nvs, "kappa": kap}
+    out["waves"] = [[int(i) for i in w] for w in waves]
+    out["sharding"] = f"{ws} rank(s), systems per rank by assign_systems (strong scaling)"
+    out["inner_solver"] = ("even-odd CGLS on the Schur complement; 16-bit storage with split fields "
+                           "(FP32 e, r, t and links, 16-bit p, s); double-float outer residual")
+    return out
 
 
 def cpu_oracle_rate(w, inputs=None, seconds=15.0):
@@ -378,6 +477,11 @@ def main():
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--solve-variants", action="store_true",
+                    help="also the 4-system batched solve with every inner field in 16 bits and with "
+                         "whole-lattice inner solves (comparisons; not in the default run)")
+    ap.add_argument("--full-batched-only", action="store_true",
+                    help="only the full 48-system batched solve (--prec for one precision)")
     ap.add_argument("--lattice", default=None, help="Nx,Ny,Nz,Nt (a smaller case for profiling)")
     ap.add_argument("--prec", default=None, choices=["f32", "bf16", "f16", "f64"])
     ap.add_argument("--kernel", default=None,
@@ -407,6 +511,16 @@ def main():
     if ws == 1:
         torch.cuda.set_device(0)
     import paper_1808_05506_gb300 as dg
+
+    if args.full_batched_only:
+        out = c5_batched_times(dg, torch, precs=(args.prec,) if args.prec else ("f32", "bf16", "f16"), rank=rank,
+                               ws=ws, dist=dist)
+        if rank == 0:
+            print(json.dumps({"batched_solve_full": out}), flush=True)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
 
     if args.batched_solve_only:
         out = batched_solve_times(dg, torch, L=WORKLOAD["L"] if args.lattice else (32, 32, 32, 64),
@@ -501,6 +615,8 @@ def main():
         "hbm_gbs": achieved,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                     "nominal_peak": NOMINAL_HBM_GBS,
                      "peak_kind": f"{peak_kind} copy bandwidth",
                      "kernel": "k_{}{}<{},R={}>".format(op, {0: "", 1: "_groups", 2: "_march", 3: "_pipe", 5: "_xrow"}[cfg[2]],
                                                       w["prec"], cfg[0]),
@@ -533,16 +649,27 @@ def main():
         line["extra"] = extra
     if not args.no_solve and not args.no_extra:
         line["solve"] = solve_times(dg, torch)
-        line["batched_solve"] = batched_solve_times(dg, torch, rank=rank, ws=ws, dist=dist)
-        # 16-bit storage with every inner field in 16 bits, for comparison
-        uni = batched_solve_times(dg, torch, precs=("bf16", "f16"), rank=rank, ws=ws, dist=dist, inner_fields=0)
+        # the full batched configuration: 48 systems, every column to 1e-10
+        line["batched_solve_full"] = c5_batched_times(dg, torch, rank=rank, ws=ws, dist=dist)
+        sp = {}
         for p in ("bf16", "f16"):
-            uni[p]["speedup_vs_f32"] = line["batched_solve"]["f32"]["seconds"] / uni[p]["seconds"]
-        uni["inner_solver"] += "; every inner field in 16 bits"
-        line["batched_solve_all16"] = uni
-        # the same systems with the whole-lattice inner solver, for comparison
-        line["batched_solve_whole_lattice"] = batched_solve_times(dg, torch, rank=rank, ws=ws, dist=dist, precond=0)
+            sp["brillouin_solve_" + p] = line["solve"][p].get("speedup_vs_f32")
+            sp["batched_solve_full_" + p] = line["batched_solve_full"][p].get("speedup_vs_f32")
+        line["speedup_vs_f32"] = sp
+        if args.solve_variants:
+            line["batched_solve"] = batched_solve_times(dg, torch, rank=rank, ws=ws, dist=dist)
+            # 16-bit storage with every inner field in 16 bits, for comparison
+            uni = batched_solve_times(dg, torch, precs=("bf16", "f16"), rank=rank, ws=ws, dist=dist,
+                                      inner_fields=0)
+            for p in ("bf16", "f16"):
+                uni[p]["speedup_vs_f32"] = line["batched_solve"]["f32"]["seconds"] / uni[p]["seconds"]
+            uni["inner_solver"] += "; every inner field in 16 bits"
+            line["batched_solve_all16"] = uni
+            # the same systems with the whole-lattice inner solver, for comparison
+            line["batched_solve_whole_lattice"] = batched_solve_times(dg, torch, rank=rank, ws=ws, dist=dist,
+                                                                      precond=0)
         _BATCHED_INPUTS.clear()
+        _LINKS.clear()
         torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_rate(w, inputs=(V, psi))

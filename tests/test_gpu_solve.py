@@ -321,6 +321,49 @@ def test_solve_batched_c5_shape_reduced(dg):
         assert r.max() <= 1e-10, (i, r)
 
 
+def test_solve_batched_c5_one_wave(dg):
+    """The batched configuration at its full size -- 32^3 x 64, BF16 storage
+    with the library's defaults (even-odd inner solves, split inner fields),
+    64 resident slots, one shared gauge field -- for one wave of its systems:
+    the first systems of the 48-system draw, up to 96 columns (the waves the
+    benchmark feeds), with complex Gaussian sources drawn on the device.
+    Every column's FP64 residual from the library is <= 1e-10, and two
+    columns per system are re-evaluated by the oracle."""
+    L = (32, 32, 32, 64)
+    Nx, Ny, Nz, Nt = L
+    rng = synth.rng(1005, synth.STREAM_MISC)
+    nv_list = [int(v) for v in rng.integers(1, 25, 48)]
+    kappas = [float(k) for k in rng.uniform(0.120, 0.124, 48)]
+    wave, cols = [], 0
+    for i in range(48):
+        if cols + nv_list[i] > 96:
+            break
+        wave.append(i)
+        cols += nv_list[i]
+    V = synth.round_to(synth.gauge_links(L, 3, "near_identity", 1005), "f32")
+    D = dg.Dirac("wilson", L, 64, kappas[0], "bf16")
+    D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
+    bs = []
+    for j in wave:
+        g = torch.Generator(device="cuda")
+        g.manual_seed(2005 + j)
+        z = torch.randn((Nt, Nz, Ny, Nx, nv_list[j], 4, 3, 2), dtype=torch.float64, device="cuda", generator=g)
+        bs.append(torch.view_as_complex(z.mul_(0.5 ** 0.5)))
+    xs, res, sys_stats, tot, status = D.solve_batched(bs, [kappas[j] for j in wave], tol=1e-10, max_outer=60,
+                                                      max_inner=8000)
+    D.close()
+    assert status == dg.OK, tot
+    assert len(res) == cols and res.max() <= 1e-10
+    assert tot["even_odd"] == 1 and tot["split_fields"] == 1
+    for j, b, x in zip(wave, bs, xs):
+        cj = sorted({0, nv_list[j] - 1})
+        r = oracle_residual("wilson", V, x[..., cj, :, :].cpu().numpy(), b[..., cj, :, :].cpu().numpy(),
+                            oracle.kappa_to_m0(kappas[j]))
+        assert r.max() <= 1e-10, (j, r)
+    del bs, xs
+    torch.cuda.empty_cache()
+
+
 @pytest.mark.skipif(not __import__("os").environ.get("DIRAC_FULL_BATCHED"),
                     reason="full-size batched configuration (several GPU-minutes): set DIRAC_FULL_BATCHED=1")
 def test_solve_batched_c5_full(dg):
