@@ -423,12 +423,81 @@ def c5_batched_times(dg, torch, precs=("f32", "bf16", "f16"), rank=0, ws=1, dist
     return out
 
 
-def cpu_oracle_rate(w, inputs=None, seconds=15.0):
+def cpu_oracle_rate(w, inputs=None, seconds=15.0, seconds_1thread=5.0):
+    """The FP64 oracle on all host cores (the line's cpu_baseline) and on one
+    thread (single_thread), each on a bounded random sample of output sites."""
     s = OracleSample(w, inputs)
     n = s.calibrate(seconds)
     dt = s.run(n)
-    return {"value": s.rate(n, dt), "unit": "Gflop/s", "cores": s.cores, "kind": "oracle",
-            "sample": s.describe(n, dt)}
+    out = {"value": s.rate(n, dt), "unit": "Gflop/s", "cores": s.cores, "kind": "oracle",
+           "sample": s.describe(n, dt)}
+    s.cores = s.oracle.set_threads(1)
+    n1 = s.calibrate(seconds_1thread)
+    dt1 = s.run(n1)
+    out["single_thread"] = {"value": s.rate(n1, dt1), "unit": "Gflop/s", "cores": 1, "sample": s.describe(n1, dt1)}
+    s.oracle.set_threads(0)
+    return out
+
+
+CPU_TABLE = [
+    ("C1", dict(op="staggered", L=(8, 8, 8, 8), Nv=4, mass=0.0, links="haar")),
+    ("C2", dict(op="wilson", L=(32, 32, 32, 32), Nv=12, mass=0.125, links="near_identity")),
+    ("C3", dict(op="brillouin", L=(24, 24, 24, 48), Nv=12, mass=0.05, links="near_identity")),
+    ("H", dict(op="staggered", L=(34, 34, 34, 68), Nv=12, mass=0.0, links="gaussian")),
+    ("H", dict(op="wilson", L=(34, 34, 34, 68), Nv=12, mass=0.125, links="gaussian")),
+    ("H", dict(op="brillouin", L=(34, 34, 34, 68), Nv=12, mass=0.05, links="gaussian")),
+]
+
+
+def cpu_table(seconds=2.0):
+    """The oracle (as it stands: the FP64 build and its FP32 instance) on the
+    host cores, on 1 thread and on all of them, for the configurations of the
+    CPU-baseline protocol: staggered 8^4 Nv=4, Wilson 32^4 Nv=12, Brillouin
+    24^3x48 Nv=12 and the paper's 34^3x68 lattice (Nv=12, all three
+    operators).  Each entry times a random sample of output sites sized to
+    take about `seconds`, and extrapolates to one whole-lattice apply.  The
+    34^3x68 inputs are complex Gaussian links and sources (the oracle's time
+    does not depend on the values); the others use the configurations' own
+    generators."""
+    import oracle
+    rows = []
+    nproc = os.cpu_count() or 1
+    for name, c in CPU_TABLE:
+        L, Nv, op = c["L"], c["Nv"], c["op"]
+        ns = 1 if op == "staggered" else 4
+        if c["links"] == "gaussian":
+            V = synth.complex_gaussian(synth.lattice_shape(L) + (4, 3, 3), 1100)
+        else:
+            V = synth.gauge_links(L, 3, c["links"], 1000 + int(name[1]) if name != "H" else 1100)
+        psi = synth.spinor(L, Nv, ns, 3, 2000 + (int(name[1]) if name != "H" else 100), dtype=np.complex64)
+        m0 = oracle.kappa_to_m0(c["mass"]) if op == "wilson" else c["mass"]
+        vol = int(np.prod(L))
+        flops_site = {"staggered": 570, "wilson": 1368, "brillouin": 29208}[op] * Nv
+        for prec in ("f64", "f32"):
+            fp32 = prec == "f32"
+            Vp = V.astype(np.complex64 if fp32 else np.complex128)
+            pp = psi.astype(np.complex64 if fp32 else np.complex128)
+            for threads in (1, nproc):
+                used = oracle.set_threads(threads, fp32=fp32)
+                rng = np.random.default_rng(0)
+                n = 16
+                while True:
+                    sites = rng.integers(0, vol, n)
+                    t0 = time.perf_counter()
+                    oracle.apply(op, Vp, pp, m0, sites=sites, fp32=fp32)
+                    dt = time.perf_counter() - t0
+                    if dt >= seconds or n >= vol:
+                        break
+                    n = min(vol, max(2 * n, int(n * seconds * 1.2 / max(dt, 1e-4))))
+                rows.append({"config": name, "op": op, "lattice": list(L), "Nv": Nv, "prec": prec,
+                             "threads": used, "sites_sampled": int(n), "seconds": dt,
+                             "gflops": flops_site * n / dt / 1e9,
+                             "seconds_per_apply": dt * vol / n})
+            oracle.set_threads(0, fp32=fp32)
+        del V, psi
+    return {"cpu_table": rows, "host_cores": nproc,
+            "note": "model flops (570 / 1368 / 29208 per site and right-hand side); oracle built with gcc -O2 "
+                    "-fopenmp, FP64 and its -DORACLE_FP32 instance"}
 
 
 def dist_init(torch):
@@ -480,6 +549,9 @@ def main():
     ap.add_argument("--solve-variants", action="store_true",
                     help="also the 4-system batched solve with every inner field in 16 bits and with "
                          "whole-lattice inner solves (comparisons; not in the default run)")
+    ap.add_argument("--cpu-table", action="store_true",
+                    help="only the CPU-baseline table: the oracle on 1 and all host threads, FP64 and FP32, "
+                         "for the staggered 8^4, Wilson 32^4, Brillouin 24^3x48 and 34^3x68 configurations")
     ap.add_argument("--full-batched-only", action="store_true",
                     help="only the full 48-system batched solve (--prec for one precision)")
     ap.add_argument("--lattice", default=None, help="Nx,Ny,Nz,Nt (a smaller case for profiling)")
@@ -504,6 +576,9 @@ def main():
         WORKLOAD = dict(WORKLOAD, op=args.op, mass=0.05 if args.op == "brillouin" else 0.0)
     if args.impl == "reference":
         return run_reference(args)
+    if args.cpu_table:
+        print(json.dumps(cpu_table()), flush=True)
+        return
     args.warmup = max(3, args.warmup)
 
     import torch
@@ -642,6 +717,11 @@ def main():
         extra["wilson_32x32x32x32_nv12_bf16"] = sweep_rate(dg, torch, dict(WORKLOAD, prec="bf16"), 200, 5)
         # the paper's own lattice (non-power-of-two extents) and the FP64 sweeps
         extra["wilson_34x34x34x68_nv12_f32"] = sweep_rate(dg, torch, dict(WORKLOAD, L=(34, 34, 34, 68)), 50, 3)
+        extra["staggered_34x34x34x68_nv12_f32"] = sweep_rate(dg, torch, dict(sw, L=(34, 34, 34, 68)), 50, 3)
+        extra["brillouin_34x34x34x68_nv12_f32"] = sweep_rate(dg, torch, dict(bw, L=(34, 34, 34, 68)), 10, 2)
+        # the staggered 8^4, Nv = 4 configuration: 2 MB, resident in L2 (latency-bound; no HBM grading)
+        c1 = dict(sw, L=(8, 8, 8, 8), Nv=4, links="haar", seed_links=1001, seed_source=2001)
+        extra["staggered_8x8x8x8_nv4_f32_l2_resident"] = sweep_rate(dg, torch, c1, 500, 20)
         extra["wilson_32x32x32x32_nv12_f64"] = sweep_rate(dg, torch, dict(WORKLOAD, prec="f64"), 20, 3)
         extra["staggered_32x32x32x32_nv12_f64"] = sweep_rate(dg, torch, dict(sw, prec="f64"), 20, 3)
         extra["brillouin_24x24x24x48_nv12_f64"] = sweep_rate(dg, torch, dict(bw, prec="f64"), 3, 1,

@@ -30,39 +30,61 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dirac_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_liboracle.so")
+_LIB32_PATH = os.path.join(_HERE, "_liboracle_f32.so")
 _lib = None
+_lib32 = None
 _lock = threading.Lock()
 
 OPS = {"staggered": 0, "wilson": 1, "brillouin": 2}
 
 
-def build(force: bool = False) -> str:
-    """Compile dirac_oracle.c into oracle/_liboracle.so with gcc + OpenMP."""
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+def build(force: bool = False, fp32: bool = False) -> str:
+    """Compile dirac_oracle.c into oracle/_liboracle.so with gcc + OpenMP (and,
+    with fp32, its single-precision instance _liboracle_f32.so, which only the
+    CPU-baseline timing uses)."""
+    path = _LIB32_PATH if fp32 else _LIB_PATH
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+        return path
+    tmp = path + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared"] + (["-DORACLE_FP32"] if fp32 else []) + \
+        ["-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
-def lib():
-    global _lib
+def _declare(L):
+    P = ctypes.c_void_p
+    L.oracle_apply.argtypes = [ctypes.c_int, ctypes.c_int, P, ctypes.c_int, ctypes.c_double,
+                               P, P, P, P, P, ctypes.c_long, ctypes.c_int]
+    L.oracle_brillouin_W.argtypes = [ctypes.c_int, P, P, P, ctypes.c_long, P]
+    L.oracle_force.argtypes = [ctypes.c_int, ctypes.c_int, P, ctypes.c_int, ctypes.c_double,
+                               P, P, P, P]
+    L.oracle_row_terms.argtypes = [ctypes.c_int, ctypes.c_int, P, ctypes.c_double, P,
+                                   ctypes.c_long, P, P]
+    L.oracle_gamma.argtypes = [ctypes.c_int, P]
+    L.oracle_set_threads.argtypes = [ctypes.c_int]
+    L.oracle_set_threads.restype = ctypes.c_int
+    return L
+
+
+def lib(fp32: bool = False):
+    global _lib, _lib32
     with _lock:
+        if fp32:
+            if _lib32 is None:
+                _lib32 = _declare(ctypes.CDLL(build(fp32=True)))
+            return _lib32
         if _lib is None:
-            _lib = ctypes.CDLL(build())
-            P = ctypes.c_void_p
-            _lib.oracle_apply.argtypes = [ctypes.c_int, ctypes.c_int, P, ctypes.c_int, ctypes.c_double,
-                                          P, P, P, P, P, ctypes.c_long, ctypes.c_int]
-            _lib.oracle_brillouin_W.argtypes = [ctypes.c_int, P, P, P, ctypes.c_long, P]
-            _lib.oracle_force.argtypes = [ctypes.c_int, ctypes.c_int, P, ctypes.c_int, ctypes.c_double,
-                                          P, P, P, P]
-            _lib.oracle_row_terms.argtypes = [ctypes.c_int, ctypes.c_int, P, ctypes.c_double, P,
-                                              ctypes.c_long, P, P]
-            _lib.oracle_gamma.argtypes = [ctypes.c_int, P]
+            _lib = _declare(ctypes.CDLL(build()))
         return _lib
+
+
+def set_threads(n: int, fp32: bool = False) -> int:
+    """OpenMP threads of the oracle's loops (n < 1: one per processor); returns
+    the number its next parallel loop uses."""
+    return int(lib(fp32).oracle_set_threads(int(n)))
 
 
 def _c128(a):
@@ -85,7 +107,8 @@ def gamma(mu: int) -> np.ndarray:
     return out
 
 
-def apply(op: str, V, psi, mass: float, sites=None, dagger: bool = False, W81=None) -> np.ndarray:
+def apply(op: str, V, psi, mass: float, sites=None, dagger: bool = False, W81=None,
+          fp32: bool = False) -> np.ndarray:
     """D psi (or D^dagger psi) in FP64.
 
     mass: staggered m, Wilson / Brillouin bare mass m0 (not kappa).
@@ -94,25 +117,28 @@ def apply(op: str, V, psi, mass: float, sites=None, dagger: bool = False, W81=No
     is [len(sites), Nv, (4,) Nc].
     W81: optional precomputed brillouin_W(V) (all sites) to avoid rebuilding
     W per row.
+    fp32: the single-precision instance (complex64 in and out), for timing only.
     """
-    V = _c128(V)
-    psi = _c128(psi)
+    cast = (lambda a: np.ascontiguousarray(a, dtype=np.complex64)) if fp32 else _c128
+    V = cast(V)
+    psi = cast(psi)
     L, Nc = _dims(V)
     Ns = 1 if op == "staggered" else 4
     vol = int(np.prod(L))
     Nv = psi.shape[4]
     blk = psi.shape[4:]
     Larr = np.array(L, dtype=np.int32)
+    odt = np.complex64 if fp32 else np.complex128
     if sites is None:
-        out = np.zeros((vol,) + blk, dtype=np.complex128)
+        out = np.zeros((vol,) + blk, dtype=odt)
         sp, ns = None, vol
     else:
         sp = np.ascontiguousarray(sites, dtype=np.int64)
         ns = len(sp)
-        out = np.zeros((ns,) + blk, dtype=np.complex128)
+        out = np.zeros((ns,) + blk, dtype=odt)
     if W81 is not None:
-        W81 = _c128(W81)
-    rc = lib().oracle_apply(OPS[op], Nc, _ptr(Larr), Nv, float(mass), _ptr(V), _ptr(W81),
+        W81 = cast(W81)
+    rc = lib(fp32).oracle_apply(OPS[op], Nc, _ptr(Larr), Nv, float(mass), _ptr(V), _ptr(W81),
                             _ptr(psi), _ptr(out), _ptr(sp), ns, 1 if dagger else 0)
     if rc:
         raise RuntimeError("oracle_apply failed")

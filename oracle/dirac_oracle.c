@@ -50,10 +50,23 @@
  */
 #include <complex.h>
 #include <math.h>
+#include <omp.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef ORACLE_FP32
+#include <tgmath.h>   /* conj, creal, cimag of float complex stay in float */
+#endif
 
+/* The oracle is FP64.  Compiled with -DORACLE_FP32 the same source gives a
+ * single-precision instance (fields, links and arithmetic in float), used only
+ * to time the CPU baseline in the paper's sp precision; the tests use FP64. */
+#ifdef ORACLE_FP32
+typedef float complex cplx;
+typedef float real_t;
+#else
 typedef double complex cplx;
+typedef double real_t;
+#endif
 
 enum { OP_STAGGERED = 0, OP_WILSON = 1, OP_BRILLOUIN = 2 };
 
@@ -435,7 +448,7 @@ static void apply_term(const ctx_t* c, const term_t* t, int dagger,
 }
 
 static void set_ctx(ctx_t* c, int op, int Nc, const int* L, int Nv, double mass,
-                    const double* V, const double* W)
+                    const real_t* V, const real_t* W)
 {
     init_gamma();
     c->op = op;
@@ -451,11 +464,19 @@ static void set_ctx(ctx_t* c, int op, int Nc, const int* L, int Nv, double mass,
 
 /* ---- public entry points ------------------------------------------------ */
 
+/* OpenMP threads of the parallel loops below (n < 1: one per processor);
+ * returns the number the next parallel region will use. */
+int oracle_set_threads(int n)
+{
+    omp_set_num_threads(n >= 1 ? n : omp_get_num_procs());
+    return omp_get_max_threads();
+}
+
 /* out = D psi (dagger = 0) or D^dagger psi (dagger = 1), at the listed output
  * sites (sites == NULL: all sites, out in canonical order); out is
  * [nsite][Nv][Ns][Nc].  W81 may be NULL for Brillouin (built per row). */
-int oracle_apply(int op, int Nc, const int* L, int Nv, double mass, const double* V,
-                 const double* W81, const double* psi, double* out,
+int oracle_apply(int op, int Nc, const int* L, int Nv, double mass, const real_t* V,
+                 const real_t* W81, const real_t* psi, real_t* out,
                  const long* sites, long nsites, int dagger)
 {
     if (Nc < 1 || Nc > MAX_NC) return 1;
@@ -506,8 +527,8 @@ int oracle_apply(int op, int Nc, const int* L, int Nv, double mass, const double
 }
 
 /* W_dir(y) for all 81 dir at the listed sites (sites == NULL: all), out [nsite][81][Nc][Nc] */
-int oracle_brillouin_W(int Nc, const int* L, const double* V, const long* sites, long nsites,
-                       double* out)
+int oracle_brillouin_W(int Nc, const int* L, const real_t* V, const long* sites, long nsites,
+                       real_t* out)
 {
     if (Nc < 1 || Nc > MAX_NC) return 1;
     ctx_t c;
@@ -627,8 +648,8 @@ static void brillouin_force(const ctx_t* c, const cplx* P, const cplx* Gv, cplx*
  * coef (S (x) C) with C = V contributes M^+ and one with C = V^+ contributes
  * M, with M of term_M.  Brillouin: through the paths of W (brillouin_force).
  * F is [site][mu][a][b]. */
-int oracle_force(int op, int Nc, const int* L, int Nv, double mass, const double* V,
-                 const double* psi, const double* g, double* F)
+int oracle_force(int op, int Nc, const int* L, int Nv, double mass, const real_t* V,
+                 const real_t* psi, const real_t* g, real_t* F)
 {
     if (Nc < 1 || Nc > MAX_NC) return 1;
     if (op == OP_BRILLOUIN) {
@@ -676,7 +697,7 @@ int oracle_force(int op, int Nc, const int* L, int Nv, double mass, const double
 }
 
 /* number of terms in one row (for the count pins) */
-int oracle_row_terms(int op, int Nc, const int* L, double mass, const double* V, long y,
+int oracle_row_terms(int op, int Nc, const int* L, double mass, const real_t* V, long y,
                      int* offsets /* [MAX_TERMS][4] or NULL */, int* spins /* or NULL */)
 {
     ctx_t c;
