@@ -152,9 +152,10 @@ def time_kernel(torch, fn, steps, warmup):
     return t0.elapsed_time(t1), [a.elapsed_time(b) for a, b in ev]
 
 
-def sweep_rate(dg, torch, w, steps, warmup, kernel=None):
+def sweep_rate(dg, torch, w, steps, warmup, kernel=None, compare_formats=False):
     """Time one sweep workload on the internal layout; returns a dict of rates.
-    kernel = (R, block, variant): that launch shape instead of the autotuner."""
+    kernel = (R, block, variant): that launch shape instead of the autotuner.
+    compare_formats: also time the link format the tuner did not keep."""
     V, psi = gen_inputs(w)
     D = dg.Dirac(w["op"], w["L"], w["Nv"], w["mass"], w["prec"])
     D.set_links(torch.from_numpy(V).cuda())
@@ -171,9 +172,37 @@ def sweep_rate(dg, torch, w, steps, warmup, kernel=None):
     byts = dg.bytes_per_site(w["op"], w["Nv"], w["prec"]) * vol
     cfg = D.kernel_config()
     order = D.site_order()
+    fmt = D.link_format()
+    byts = dg.bytes_per_site(w["op"], w["Nv"], w["prec"], link_format=fmt) * vol
+    out = {"gflops": flops / t / 1e9, "gbs": byts / t / 1e9, "ms": t * 1e3, "R": cfg[0], "block": cfg[1],
+           "variant": cfg[2], "site_order_tchunk": order, "link_format": fmt}
+    if compare_formats:
+        out["other_link_format"] = other_format_time(dg, torch, D, x, y, w, steps, warmup, fmt)
     D.close()
-    return {"gflops": flops / t / 1e9, "gbs": byts / t / 1e9, "ms": t * 1e3, "R": cfg[0], "block": cfg[1],
-            "variant": cfg[2], "site_order_tchunk": order}
+    return out
+
+
+def other_format_time(dg, torch, D, x, y, w, steps, warmup, fmt):
+    """The sweep in the link format the tuner did not keep (two-row links vs
+    nine entries for Wilson / staggered, 80 vs 40 stored W for Brillouin), in
+    the tuned launch shape if that shape reads both formats, else in variant 1
+    with two right-hand sides per thread, 64 sites per block, t-chunks of 8."""
+    other = 1 - fmt
+    try:
+        D.set_link_format(other)
+    except dg.DiracError as e:
+        return {"fmt": other, "unavailable": str(e)}
+    R, B, variant = D.kernel_config()
+    if not (variant == 1 or (w["op"] == "brillouin" and variant == 0)):
+        D.set_kernel_config(2, 64, 1)
+        D.set_site_order(min(8, w["L"][3]))
+    _, per = time_kernel(torch, lambda: D.apply(x, out=y), steps, warmup)
+    t = statistics.mean(per) * 1e-3
+    byts = dg.bytes_per_site(w["op"], w["Nv"], w["prec"], link_format=other) * int(np.prod(w["L"]))
+    res = {"fmt": other, "ms": t * 1e3, "gbs": byts / t / 1e9, "kernel": list(D.kernel_config()),
+           "site_order_tchunk": D.site_order()}
+    D.set_link_format(fmt)
+    return res
 
 
 class OracleSample:
@@ -627,7 +656,9 @@ def main():
     vol = int(np.prod(w["L"]))
     workload = "{}_apply_{}_nv{}_{}".format(op, "x".join(map(str, w["L"])), w["Nv"], w["prec"])
     flops_step = dg.flops_per_site_rhs(op) * vol * w["Nv"]
-    bytes_step = dg.bytes_per_site(op, w["Nv"], w["prec"]) * vol
+    link_fmt = D.link_format()
+    # the bytes the chosen link format moves (two-row links: two thirds of the link bytes)
+    bytes_step = dg.bytes_per_site(op, w["Nv"], w["prec"], link_format=link_fmt) * vol
     if bytes_step < 4 * 129e6:
         raise SystemExit("the timed step must stream more than the L2 (use a larger --lattice)")
 
@@ -676,6 +707,9 @@ def main():
             traffic = tf.get("dram_bytes_per_launch")
     cfg = D.kernel_config()
     site_order = D.site_order()
+    other_fmt = other_format_time(dg, torch, D, x, y, w, 200, 5, link_fmt) if not args.no_extra else None
+    D.set_kernel_config(*cfg)
+    D.set_site_order(site_order)
     line = {
         "metric": METRIC, "value": value, "unit": "Gflop/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -685,7 +719,7 @@ def main():
                    "source": "complex Gaussian N(0,1)", "layout": "internal blocked SoA (blocks of 32 sites)",
                    "l2": "no flush: each step streams {:.2f} GB > 129 MB L2".format(bytes_step / 1e9),
                    "kernel": {"rhs_per_thread": cfg[0], "block": cfg[1], "variant": cfg[2],
-                              "site_order_tchunk": site_order},
+                              "site_order_tchunk": site_order, "link_format": link_fmt},
                    "parallelism": f"replicas x{ws}"},
         "hbm_gbs": achieved,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -702,6 +736,7 @@ def main():
                 "path": "dirac_apply_host: pinned host field in, pinned host field out, "
                         "t-slab copies overlapped with pack / sweep / unpack"},
         "gpu_launches": args.steps,
+        "other_link_format": other_fmt,
         "paper_context": PAPER_CONTEXT,
     }
     D.close()
@@ -710,11 +745,13 @@ def main():
     if not args.no_extra:
         extra = {}
         sw = dict(WORKLOAD, op="staggered", mass=0.0)
-        extra["staggered_32x32x32x32_nv12_f32"] = sweep_rate(dg, torch, sw, 200, 5)
+        extra["staggered_32x32x32x32_nv12_f32"] = sweep_rate(dg, torch, sw, 200, 5, compare_formats=True)
         bw = dict(WORKLOAD, op="brillouin", L=(24, 24, 24, 48), mass=0.05, seed_links=1003, seed_source=2003)
-        extra["brillouin_24x24x24x48_nv12_f32"] = sweep_rate(dg, torch, bw, 20, 3)
-        extra["brillouin_24x24x24x48_nv12_bf16"] = sweep_rate(dg, torch, dict(bw, prec="bf16"), 20, 3)
-        extra["wilson_32x32x32x32_nv12_bf16"] = sweep_rate(dg, torch, dict(WORKLOAD, prec="bf16"), 200, 5)
+        extra["brillouin_24x24x24x48_nv12_f32"] = sweep_rate(dg, torch, bw, 20, 3, compare_formats=True)
+        extra["brillouin_24x24x24x48_nv12_bf16"] = sweep_rate(dg, torch, dict(bw, prec="bf16"), 20, 3,
+                                                              compare_formats=True)
+        extra["wilson_32x32x32x32_nv12_bf16"] = sweep_rate(dg, torch, dict(WORKLOAD, prec="bf16"), 200, 5,
+                                                           compare_formats=True)
         # the paper's own lattice (non-power-of-two extents) and the FP64 sweeps
         extra["wilson_34x34x34x68_nv12_f32"] = sweep_rate(dg, torch, dict(WORKLOAD, L=(34, 34, 34, 68)), 50, 3)
         extra["staggered_34x34x34x68_nv12_f32"] = sweep_rate(dg, torch, dict(sw, L=(34, 34, 34, 68)), 50, 3)

@@ -389,6 +389,35 @@ DIRAC_API dirac_status dirac_get_kernel_config(const dirac_handle* h, int* R, in
 DIRAC_API dirac_status dirac_set_site_order(dirac_handle* h, int tchunk);
 DIRAC_API dirac_status dirac_get_site_order(const dirac_handle* h, int* tchunk);
 
+/* Link format of the apply sweeps (gauge compression; Sec. 4, last
+ * paragraph, names it as a next step, and the caption of Tab. tab:off-axis
+ * gives W_{-dir}(x) = W_dir(x - dir)^+, which lets D_B store 40 of its 80 W).
+ *   fmt 0 (default): Wilson and staggered read all nine entries of each link;
+ *          Brillouin reads the 40 stored W, W_{-dir} as the adjoint of W_dir at
+ *          the neighbour x - dir.
+ *   fmt 1: Wilson and staggered (FP32, BF16, FP16 storage) read only the
+ *          first two rows of each link and rebuild the third as
+ *          U_2c = conj(U_0 x U_1)_c, which holds for special unitary links:
+ *          two thirds of the link bytes.  Selecting it checks the links in
+ *          FP64: max |U_2c - conj(U_0 x U_1)_c| must be <= 1e-6 (FP32) or
+ *          <= 1e-2 (16-bit storage), else DIRAC_ERR_INVALID_ARG and format 0
+ *          stays.  Brillouin (every precision) reads all 80 W stored at x
+ *          (W_{-dir}(x) precomputed, copied without rounding): twice the W
+ *          bytes, local reads only.
+ * Format 1 is read by the launch variants that support it (Wilson and
+ * staggered: variant 1; Brillouin: variants 0 and 1); other variants, the
+ * solvers' inner sweeps and the even-odd sweeps read the plain links.  The
+ * format-1 copy (Wilson/staggered: 4 x 6 complex per site; Brillouin: 80 x 9)
+ * is held by the handle and rebuilt by dirac_set_links; links that fail the
+ * check there switch the handle back to format 0 (dirac_get_link_format
+ * reports it).  Called before dirac_set_links, fmt 1 is recorded and built
+ * (and checked) there.  dirac_autotune times both formats and keeps the
+ * faster.  Results agree with format 0 to rounding (Brillouin: bit for bit).
+ * Errors: DIRAC_ERR_INVALID_ARG (fmt not 0 or 1, links not special unitary),
+ * DIRAC_ERR_UNSUPPORTED (two-row links of an FP64 handle). */
+DIRAC_API dirac_status dirac_set_link_format(dirac_handle* h, int fmt);
+DIRAC_API dirac_status dirac_get_link_format(const dirac_handle* h, int* fmt);
+
 /* Autotuner (the paper's "best of breed" selection, Sec. 4 and Sec. 6: time
  * every built variant on this machine and keep the winner): times each
  * supported (R, block, variant) of dirac_set_kernel_config, variants 0 and 1
@@ -396,6 +425,8 @@ DIRAC_API dirac_status dirac_get_site_order(const dirac_handle* h, int* tchunk);
  * workspace and keeps the fastest in the handle.  With the environment
  * variable DIRAC_TUNE_CACHE naming a writable file, results are cached per
  * (operator, precision, lattice, Nv, GPU name) and reused unless force != 0.
+ * It also times link format 1 (dirac_set_link_format) on the shapes that read
+ * it, when the links allow it, and keeps the faster format.
  * Synchronous.  R, block, variant, ms (host, may be NULL) receive the choice
  * and its median time per sweep in milliseconds (from the cache when reused). */
 DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int* R, int* block, int* variant, double* ms);

@@ -70,6 +70,8 @@ SIGNATURES = {
     "dirac_set_site_order": (I, [P, I]),
     "dirac_apply_host": (I, [P, P, P, I]),
     "dirac_get_site_order": (I, [P, ctypes.POINTER(I)]),
+    "dirac_set_link_format": (I, [P, I]),
+    "dirac_get_link_format": (I, [P, ctypes.POINTER(I)]),
     "dirac_set_preconditioner": (I, [P, I]),
     "dirac_set_residual_arithmetic": (I, [P, I]),
     "dirac_set_inner_fields": (I, [P, I]),
@@ -436,6 +438,17 @@ class Dirac:
         check(lib().dirac_get_site_order(self.h, ctypes.byref(t)), self.h, "dirac_get_site_order")
         return t.value
 
+    def set_link_format(self, fmt: int):
+        """Links the apply sweeps read: 0 the plain links (Brillouin: 40 stored W),
+        1 Wilson / staggered two-row links (special unitary links only),
+        Brillouin all 80 W per site; see dirac_set_link_format."""
+        check(lib().dirac_set_link_format(self.h, fmt), self.h, "dirac_set_link_format")
+
+    def link_format(self) -> int:
+        f = I()
+        check(lib().dirac_get_link_format(self.h, ctypes.byref(f)), self.h, "dirac_get_link_format")
+        return f.value
+
     def set_preconditioner(self, mode: int):
         """Inner solves: 1 even-odd Schur complement where it applies, 0 whole lattice;
         see dirac_set_preconditioner."""
@@ -533,9 +546,17 @@ def flops_per_site_rhs(op: str, Nc: int = 3) -> int:
     raise ValueError(op)
 
 
-def bytes_per_site(op: str, Nv: int, prec: str, Nc: int = 3) -> int:
-    """Algorithmic HBM bytes per site of one sweep: links once, in and out once."""
+def bytes_per_site(op: str, Nv: int, prec: str, Nc: int = 3, link_format: int = 0) -> int:
+    """Algorithmic HBM bytes per site of one sweep: links once, in and out once.
+    link_format 1 (dirac_set_link_format): Wilson / staggered read two rows of
+    each link, Brillouin all 80 W."""
     c = {"f64": 16, "f32": 8, "bf16": 4, "f16": 4}[prec]
     nlink = {"staggered": 4, "wilson": 4, "brillouin": 40}[op]
+    per_link = Nc * Nc
+    if link_format == 1:
+        if op == "brillouin":
+            nlink = 80
+        else:
+            per_link = (Nc - 1) * Nc
     ns = 1 if op == "staggered" else 4
-    return nlink * Nc * Nc * c + 2 * ns * Nc * Nv * c
+    return nlink * per_link * c + 2 * ns * Nc * Nv * c

@@ -14,19 +14,20 @@ namespace dirac {
 
 __constant__ BriDir c_bri_dirs[80];
 
-template <typename T, int R, bool DAG>
+// LF: 0 the 40 stored links, 1 all 80 directions stored at each site
+template <typename T, int R, bool DAG, int LF>
 __global__ void __launch_bounds__(256) k_brillouin(ApplyArgs a, int ngroups)
 {
     const long b = blockIdx.x;
     const int group = (int)(b % ngroups);
     const long p = (b / ngroups) * blockDim.x + threadIdx.x;
     if (p >= a.nsites) return;
-    brillouin_site<T, R, DAG>(a, slab_site(a, p), group, c_bri_dirs);
+    brillouin_site<T, R, DAG, LF>(a, slab_site(a, p), group, c_bri_dirs);
 }
 
 // V_GROUPS: blockDim = (sites, groups); block b covers a run of sites and a
 // chunk of gy right-hand-side groups
-template <typename T, int R, bool DAG>
+template <typename T, int R, bool DAG, int LF>
 __global__ void __launch_bounds__(192, 2) k_brillouin_groups(ApplyArgs a, int ngroups, int gy)
 {
     const int nchunks = (ngroups + gy - 1) / gy;
@@ -34,25 +35,31 @@ __global__ void __launch_bounds__(192, 2) k_brillouin_groups(ApplyArgs a, int ng
     const int group = (int)(b % nchunks) * gy + threadIdx.y;
     const long p = (b / nchunks) * blockDim.x + threadIdx.x;
     if (p >= a.nsites || group >= ngroups) return;
-    brillouin_site<T, R, DAG>(a, slab_site(a, p), group, c_bri_dirs);
+    brillouin_site<T, R, DAG, LF>(a, slab_site(a, p), group, c_bri_dirs);
 }
 
-template <typename T, int R>
-static cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
+template <typename T, int R, int LF>
+static cudaError_t go_lf(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
 {
     const int block = c.block;
     const int ngroups = (a.Nv + R - 1) / R;
     if (c.variant == V_GROUPS) {
         const int gy = groups_per_block(block, ngroups);
         const long nb = ((a.nsites + block - 1) / block) * (long)((ngroups + gy - 1) / gy);
-        if (dag) k_brillouin_groups<T, R, true><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
-        else k_brillouin_groups<T, R, false><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+        if (dag) k_brillouin_groups<T, R, true, LF><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+        else k_brillouin_groups<T, R, false, LF><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
         return cudaGetLastError();
     }
     const long nblk = ((a.nsites + block - 1) / block) * (long)ngroups;
-    if (dag) k_brillouin<T, R, true><<<(unsigned)nblk, block, 0, st>>>(a, ngroups);
-    else k_brillouin<T, R, false><<<(unsigned)nblk, block, 0, st>>>(a, ngroups);
+    if (dag) k_brillouin<T, R, true, LF><<<(unsigned)nblk, block, 0, st>>>(a, ngroups);
+    else k_brillouin<T, R, false, LF><<<(unsigned)nblk, block, 0, st>>>(a, ngroups);
     return cudaGetLastError();
+}
+
+template <typename T, int R>
+static cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
+{
+    return c.fmt == 1 ? go_lf<T, R, 1>(dag, a, c, st) : go_lf<T, R, 0>(dag, a, c, st);
 }
 
 template <typename T>

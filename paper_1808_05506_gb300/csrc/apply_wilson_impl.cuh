@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(256) k_wilson_pipe(ApplyArgs a, int ngroups)
 
 // V_GROUPS: blockDim = (sites, groups); block b covers a run of sites and a
 // chunk of gy right-hand-side groups
-template <typename T, int R, bool DAG, int MODE>
+// LF: link format (0 nine entries per link, 1 two rows, reconstructed)
+template <typename T, int R, bool DAG, int MODE, int LF>
 __global__ void __launch_bounds__(192, 2) k_wilson_groups(ApplyArgs a, int ngroups, int gy)
 {
     const int nchunks = (ngroups + gy - 1) / gy;
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(192, 2) k_wilson_groups(ApplyArgs a, int ngrou
     const int group = (int)(b % nchunks) * gy + threadIdx.y;
     const long p = (b / nchunks) * blockDim.x + threadIdx.x;
     if (p >= a.nsites || group >= ngroups) return;
-    wilson_site<T, R, DAG, MODE>(a, slab_site(a, p), group);
+    wilson_site<T, R, DAG, MODE, LF>(a, slab_site(a, p), group);
 }
 
 template <typename T, int R>
@@ -93,10 +94,15 @@ cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
         // whole groups of R right-hand sides: the specialised bodies
         const bool dv = sizeof(T) == 8 ? a.diag_v != nullptr : a.diag_vf != nullptr;
         const int mode = (a.Nv % R != 0 || (a.diag_v != nullptr && !dv)) ? 0 : (dv ? 2 : 1);
-        auto launch = [&](auto m) {
+        auto launch_lf = [&](auto m, auto lf) {
             constexpr int M = decltype(m)::value;
-            if (dag) k_wilson_groups<T, R, true, M><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
-            else k_wilson_groups<T, R, false, M><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+            constexpr int LF = decltype(lf)::value;
+            if (dag) k_wilson_groups<T, R, true, M, LF><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+            else k_wilson_groups<T, R, false, M, LF><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+        };
+        auto launch = [&](auto m) {
+            if (c.fmt == 1) launch_lf(m, std::integral_constant<int, 1>{});
+            else launch_lf(m, std::integral_constant<int, 0>{});
         };
         if (mode == 1) launch(std::integral_constant<int, 1>{});
         else if (mode == 2) launch(std::integral_constant<int, 2>{});

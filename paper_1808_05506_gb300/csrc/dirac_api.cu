@@ -128,6 +128,15 @@ dirac_status dirac_handle::run_apply(bool dagger, void* out, const void* in, int
                                      double diag_value, const void* link_ptr, int p, LaunchCfg c,
                                      const double* diag_v, int t0, int nt, const float* diag_vf)
 {
+    // link format 1 (dirac_set_link_format) for the storage links, where the
+    // launch variant reads it; every other call reads the plain links
+    const int f = c.fmt < 0 ? link_fmt : c.fmt;
+    if (f == 1 && link_ptr == links && p == prec && links_alt && link_format_supported(op, p, c.variant)) {
+        link_ptr = links_alt;
+        c.fmt = 1;
+    } else {
+        c.fmt = 0;
+    }
     ApplyArgs a = args(out, in, nv, diag_value);
     a.links = link_ptr;
     a.diag_v = diag_v;
@@ -246,6 +255,7 @@ dirac_handle::~dirac_handle()
     release(links64b);
     release(links_df);
     release(links32);
+    release(links_alt);
     release(ws_in);
     release(ws_out);
     free_solver_workspace();
@@ -334,10 +344,51 @@ dirac_status dirac_set_links(dirac_handle* h, const void* V, dirac_prec V_prec, 
             if (st) return st;
         }
     }
+    if (h->link_fmt == 1) {
+        // rebuilt in place (same address); links that do not allow format 1
+        // (two-row links of links that are not special unitary) fall back to
+        // format 0, which gives the same operator
+        if (h->build_link_alt() != DIRAC_OK) {
+            h->release_after_sync(h->links_alt);
+            h->link_fmt = 0;
+        }
+    }
     st = h->cuda(cudaStreamSynchronize(h->stream), "dirac_set_links");
     if (st) return st;
     h->have_links = true;
     return DIRAC_OK;
+}
+
+// format 1 of the storage links (links_alt) from the current links: Brillouin,
+// all 80 directions per site; Wilson and staggered, the first two rows of each
+// link, after checking in FP64 that the links are special unitary to the
+// precision of the storage (the third row is rebuilt from the first two)
+dirac_status dirac_handle::build_link_alt()
+{
+    dirac_status st;
+    const size_t nsite = nblk_of((size_t)g.vol) * 32;
+    if (op == OP_BRILLOUIN) {
+        if (!links_alt && (st = alloc(&links_alt, nsite * 80 * 9 * cbytes(prec), "80-direction W"))) return st;
+        return cuda(launch_brillouin_w80(prec, g, links, links_alt, stream), "80-direction W");
+    }
+    if (prec == P_F64)
+        return fail(DIRAC_ERR_UNSUPPORTED, "dirac_set_link_format: two-row links are built for FP32 and 16-bit storage");
+    void* d = nullptr;
+    if ((st = alloc(&d, sizeof(double), "SU(3) check"))) return st;
+    double dev = 0.0;
+    st = cuda(launch_su3_deviation(g, links64, static_cast<double*>(d), stream), "SU(3) check");
+    if (!st) st = cuda(cudaMemcpyAsync(&dev, d, sizeof(double), cudaMemcpyDeviceToHost, stream), "SU(3) check");
+    if (!st) st = cuda(cudaStreamSynchronize(stream), "SU(3) check");
+    release(d);
+    if (st) return st;
+    const double tol = prec == P_F32 ? 1e-6 : 1e-2;
+    if (!(dev <= tol))
+        return fail(DIRAC_ERR_INVALID_ARG,
+                    "dirac_set_link_format: two-row links need special unitary links; max |U_2c - conj(U_0 x U_1)_c| "
+                    "= %.3g > %.0e",
+                    dev, tol);
+    if (!links_alt && (st = alloc(&links_alt, nsite * 4 * 6 * cbytes(prec), "two-row links"))) return st;
+    return cuda(launch_links_2row(prec, g, links, links_alt, stream), "two-row links");
 }
 
 // the operator's links in FP64 and in the sweeps' blocked layout (the FP64 copies
@@ -492,6 +543,38 @@ dirac_status dirac_set_kernel_config(dirac_handle* h, int R, int block, int vari
         return h->fail(DIRAC_ERR_UNSUPPORTED, "dirac_set_kernel_config: R = %d, block = %d, variant = %d not built",
                        R, block, variant);
     h->cfg = LaunchCfg{R, block, variant, h->cfg.order};
+    return DIRAC_OK;
+}
+
+dirac_status dirac_set_link_format(dirac_handle* h, int fmt)
+{
+    if (!h) return DIRAC_ERR_INVALID_ARG;
+    if (fmt != 0 && fmt != 1)
+        return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_set_link_format: format %d is not 0 or 1", fmt);
+    if (fmt == 0) {
+        h->link_fmt = 0;
+        h->release_after_sync(h->links_alt);
+        return DIRAC_OK;
+    }
+    if (h->op != OP_BRILLOUIN && h->prec == P_F64)
+        return h->fail(DIRAC_ERR_UNSUPPORTED, "dirac_set_link_format: two-row links are built for FP32 and 16-bit storage");
+    if (h->have_links) {
+        dirac_status st = h->build_link_alt();
+        if (!st) st = h->cuda(cudaStreamSynchronize(h->stream), "dirac_set_link_format");
+        if (st) {
+            h->release_after_sync(h->links_alt);
+            h->link_fmt = 0;
+            return st;
+        }
+    }
+    h->link_fmt = 1;
+    return DIRAC_OK;
+}
+
+dirac_status dirac_get_link_format(const dirac_handle* h, int* fmt)
+{
+    if (!h || !fmt) return DIRAC_ERR_INVALID_ARG;
+    *fmt = h->link_fmt;
     return DIRAC_OK;
 }
 

@@ -378,6 +378,31 @@ DEV_INLINE void load_link(const void* base, size_t vol, int m, long s, cx<typena
     for (int e = 0; e < 9; ++e) U[e] = ld_one<T>(base, blk_index(vol, 9, m, e, s));
 }
 
+// Two-row links (gauge compression): only rows 0 and 1 are stored (planes
+// e = 0..5 of a layout with 6 planes per link); for a special unitary U the
+// third row is the complex conjugate of the cross product of the first two,
+// U_2c = conj(U_0a U_1b - U_0b U_1a) for (a, b, c) cyclic.
+template <typename A> HD void reconstruct_row2(cx<A>* U)
+{
+    U[6] = conj(cmul(U[1], U[5]) - cmul(U[2], U[4]));
+    U[7] = conj(cmul(U[2], U[3]) - cmul(U[0], U[5]));
+    U[8] = conj(cmul(U[0], U[4]) - cmul(U[1], U[3]));
+}
+template <typename T, bool NA>
+DEV_INLINE void load_link_2row(const void* base, size_t vol, int m, long s, cx<typename Store<T>::A>* U)
+{
+#pragma unroll
+    for (int e = 0; e < 6; ++e) U[e] = ld_one_p<T, NA>(base, blk_index(vol, 6, m, e, s));
+    reconstruct_row2(U);
+}
+// link m at site s in link format LF: 0 all nine entries, 1 two rows
+template <typename T, bool NA, int LF>
+DEV_INLINE void load_link_f(const void* base, size_t vol, int m, long s, cx<typename Store<T>::A>* U)
+{
+    if constexpr (LF == 1) load_link_2row<T, NA>(base, vol, m, s, U);
+    else load_link_p<T, NA>(base, vol, m, s, U);
+}
+
 // ---- packed FP32 pairs: one fma.rn.f32x2 does the (re, im) halves of a
 // complex update, halving the issue slots of complex arithmetic.  Used by the
 // Brillouin sweep, which is issue-bound; the Wilson and staggered sweeps keep

@@ -30,6 +30,9 @@ struct dirac_handle {
     void* links32 = nullptr;  // FP32 V_mu, blocked layout, for the split inner solve (lazy)
     void* links64b = nullptr; // FP64 links of the operator (V or W) in the blocked layout of the
                               // sweeps, for the solver's FP64 residual (lazy; F64 handles use links)
+    void* links_alt = nullptr;  // link format 1 (dirac_set_link_format): Wilson / staggered two-row
+                                // links [4][6][site], Brillouin all 80 W [80][9][site] (blocked)
+    int link_fmt = 0;           // the format the apply sweeps read where their variant supports it
     bool have_links = false;
     int* dev_err = nullptr;   // device error word written by kernels whose bounded waits run out
 
@@ -61,6 +64,7 @@ struct dirac_handle {
     dirac_status ensure_links64b(const void** out);
     dirac_status ensure_links_df(const void** out);
     dirac_status ensure_links32(const void** out);
+    dirac_status build_link_alt();
     dirac::ApplyArgs args(void* out, const void* in, int nv, double diag_value) const;
     dirac_status run_apply(bool dagger, void* out, const void* in, int nv, double diag_value,
                            const void* link_ptr, int p, dirac::LaunchCfg c, const double* diag_v = nullptr,

@@ -40,7 +40,18 @@ struct LaunchCfg {
     int block;     // V_DIRECT, V_PIPE3: threads per block; V_GROUPS: sites per block
     int variant;   // Variant
     int order = 0; // V_DIRECT, V_GROUPS: site order of the grid (site_of t-chunk, 0 lexicographic)
+    int fmt = -1;  // link format of the sweep (link_format_supported): 0 the plain links
+                   // (Brillouin: 40 stored W); 1 Wilson / staggered two-row links,
+                   // Brillouin all 80 W stored per site; -1 the handle's format
 };
+
+// whether a launch variant reads link format 1: Wilson and staggered
+// V_GROUPS with FP32 / 16-bit storage, Brillouin V_DIRECT and V_GROUPS
+inline bool link_format_supported(int op, int prec, int variant)
+{
+    if (op == OP_BRILLOUIN) return variant == V_DIRECT || variant == V_GROUPS;
+    return prec != P_F64 && variant == V_GROUPS;
+}
 
 // threads per block of V_GROUPS: block sites x gy groups with block * gy <= 192
 inline int groups_per_block(int block, int ngroups)
@@ -51,6 +62,15 @@ inline int groups_per_block(int block, int ngroups)
 
 bool apply_config_supported(int op, int prec, int R, int block, int variant, const Geom& g);
 size_t wilson_pipe_smem(int prec, int R, int block, int stages);
+
+// two-row links [4][site/32][6][32] (rows 0, 1 of the storage links) and the
+// largest deviation from special unitarity max |U_2c - conj(U_0 x U_1)_c|
+// of the FP64 links V64 [4][9][site] (into *dev, a device double)
+cudaError_t launch_links_2row(int prec, const Geom& g, const void* links, void* out, cudaStream_t st);
+cudaError_t launch_su3_deviation(const Geom& g, const void* V64, double* dev, cudaStream_t st);
+// Brillouin: all 80 directions per site [80][site/32][9][32] from the 40 stored
+// ones: planes 0..39 copied, plane 40 + j holds W_{-d_j}(x) = W_{d_j}(x - d_j)^+
+cudaError_t launch_brillouin_w80(int prec, const Geom& g, const void* links, void* out, cudaStream_t st);
 
 // out = D in (or D^+ in) on internal-layout fields
 cudaError_t launch_apply(int op, int prec, bool dagger, const ApplyArgs& a, LaunchCfg cfg,

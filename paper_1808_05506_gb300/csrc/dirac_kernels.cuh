@@ -98,13 +98,14 @@ HD void wilson_reconstruct(const cx<A>* w, cx<A>* acc)
 // one hop: acc_r += (1 + S gamma_MU) U psi_r(nbr),  U = V_MU(lsite) or its adjoint (BACK);
 // NA: the loads bypass L1 (data this SM will not read again soon)
 // FULL: every group holds R right-hand sides (Nv % R == 0), no clamping
-template <typename T, int R, int MU, int S, bool BACK, bool NA = false, bool FULL = false>
+// LF: link format (0 nine entries per link, 1 two rows, reconstructed)
+template <typename T, int R, int MU, int S, bool BACK, bool NA = false, bool FULL = false, int LF = 0>
 DEV_INLINE void wilson_hop(const ApplyArgs& a, long nbr, long lsite, int v0,
                            cx<typename Store<T>::A> (&acc)[R][12])
 {
     using A = typename Store<T>::A;
     cx<A> U[9];
-    load_link_p<T, NA>(a.links, a.g.vol, MU, lsite, U);
+    load_link_f<T, NA, LF>(a.links, a.g.vol, MU, lsite, U);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         // a partial last group recomputes the last right-hand side instead of
@@ -133,7 +134,7 @@ template <typename A> DEV_INLINE A diag_mode(const ApplyArgs& a, int v, int mode
     return diag_of<A>(a, v);
 }
 
-template <typename T, int R, bool DAG, int MODE = 0>
+template <typename T, int R, bool DAG, int MODE = 0, int LF = 0>
 DEV_INLINE void wilson_site(const ApplyArgs& a, long s, int group)
 {
     constexpr bool FULL = MODE != 0;
@@ -150,14 +151,14 @@ DEV_INLINE void wilson_site(const ApplyArgs& a, long s, int group)
     // forward hop carries (1 - gamma), backward (1 + gamma); the adjoint swaps them
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
-    wilson_hop<T, R, 0, SF, false, false, FULL>(a, s + fwd[0], s, v0, acc);
-    wilson_hop<T, R, 0, SB, true, false, FULL>(a, s + bwd[0], s + bwd[0], v0, acc);
-    wilson_hop<T, R, 1, SF, false, false, FULL>(a, s + fwd[1], s, v0, acc);
-    wilson_hop<T, R, 1, SB, true, false, FULL>(a, s + bwd[1], s + bwd[1], v0, acc);
-    wilson_hop<T, R, 2, SF, false, false, FULL>(a, s + fwd[2], s, v0, acc);
-    wilson_hop<T, R, 2, SB, true, false, FULL>(a, s + bwd[2], s + bwd[2], v0, acc);
-    wilson_hop<T, R, 3, SF, false, false, FULL>(a, s + fwd[3], s, v0, acc);
-    wilson_hop<T, R, 3, SB, true, false, FULL>(a, s + bwd[3], s + bwd[3], v0, acc);
+    wilson_hop<T, R, 0, SF, false, false, FULL, LF>(a, s + fwd[0], s, v0, acc);
+    wilson_hop<T, R, 0, SB, true, false, FULL, LF>(a, s + bwd[0], s + bwd[0], v0, acc);
+    wilson_hop<T, R, 1, SF, false, false, FULL, LF>(a, s + fwd[1], s, v0, acc);
+    wilson_hop<T, R, 1, SB, true, false, FULL, LF>(a, s + bwd[1], s + bwd[1], v0, acc);
+    wilson_hop<T, R, 2, SF, false, false, FULL, LF>(a, s + fwd[2], s, v0, acc);
+    wilson_hop<T, R, 2, SB, true, false, FULL, LF>(a, s + bwd[2], s + bwd[2], v0, acc);
+    wilson_hop<T, R, 3, SF, false, false, FULL, LF>(a, s + fwd[3], s, v0, acc);
+    wilson_hop<T, R, 3, SB, true, false, FULL, LF>(a, s + bwd[3], s + bwd[3], v0, acc);
     const A mh = (A)(-0.5);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -550,8 +551,8 @@ DEV_INLINE void wilson_site_pipe(const ApplyArgs& a, long s, int group, char* sm
 }
 
 // ---------------------------------------------------------------- staggered
-// MODE as in wilson_site
-template <typename T, int R, bool DAG, int MODE = 0>
+// MODE and LF as in wilson_site
+template <typename T, int R, bool DAG, int MODE = 0, int LF = 0>
 DEV_INLINE void staggered_site(const ApplyArgs& a, long s, int group)
 {
     constexpr bool FAST = MODE != 0;
@@ -571,8 +572,8 @@ DEV_INLINE void staggered_site(const ApplyArgs& a, long s, int group)
         const A eta = (par & 1) ? A(-1) : A(1);
         par += x[mu];
         cx<A> Uf[9], Ub[9];
-        load_link<T>(a.links, a.g.vol, mu, s, Uf);
-        load_link<T>(a.links, a.g.vol, mu, s + bwd[mu], Ub);
+        load_link_f<T, false, LF>(a.links, a.g.vol, mu, s, Uf);
+        load_link_f<T, false, LF>(a.links, a.g.vol, mu, s + bwd[mu], Ub);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int v = FAST ? v0 + r : min(v0 + r, a.Nv - 1);   // partial group: recompute, store guarded
@@ -702,8 +703,10 @@ DEV_INLINE void bri_pair_acc(const BriDirA<A>& m, const cx<A>* av, const cx<A>* 
 // out = (m0 + 15/8) psi + sum over the 40 pairs (d, -d) of the stored
 // directions: the spin matrices of d and -d differ only in the sign of the
 // rho part, so both colour products are formed first and one spin matrix
-// application serves the pair
-template <typename T, int R, bool DAG>
+// application serves the pair.
+// LF 0: 40 stored links, W_{-d}(x) = W_d(x - d)^+ read at the neighbour x - d;
+// LF 1: all 80 stored at x, W_{-d}(x) in plane 40 + rep (local reads)
+template <typename T, int R, bool DAG, int LF = 0>
 DEV_INLINE void brillouin_site(const ApplyArgs& a, long s, int group, const BriDir* dirs)
 {
     using A = typename Store<T>::A;
@@ -728,7 +731,8 @@ DEV_INLINE void brillouin_site(const ApplyArgs& a, long s, int group, const BriD
         }
         cx<A> Wp[9], Wm[9];
         load_link<T>(a.links, a.g.vol, D.rep, s, Wp);    // W_d(x)
-        load_link<T>(a.links, a.g.vol, D.rep, nm, Wm);   // W_{-d}(x) = W_d(x - d)^+
+        if constexpr (LF == 1) load_link<T>(a.links, a.g.vol, 40 + D.rep, s, Wm);   // W_{-d}(x)
+        else load_link<T>(a.links, a.g.vol, D.rep, nm, Wm);   // W_{-d}(x) = W_d(x - d)^+
         const BriDirA<A> m = bri_coeffs<A, DAG>(D);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -747,8 +751,13 @@ DEV_INLINE void brillouin_site(const ApplyArgs& a, long s, int group, const BriD
             for (int sp = 0; sp < 4; ++sp) {
 #pragma unroll
                 for (int i = 0; i < 3; ++i) bv[3 * sp + i] = cx<A>{A(0), A(0)};
-                if constexpr (sizeof(A) == 4) mat_dag_vec_acc2(Wm, p + 3 * sp, bv + 3 * sp);
-                else mat_dag_vec_acc(Wm, p + 3 * sp, bv + 3 * sp);
+                if constexpr (LF == 1) {
+                    if constexpr (sizeof(A) == 4) mat_vec_acc2(Wm, p + 3 * sp, bv + 3 * sp);
+                    else mat_vec_acc(Wm, p + 3 * sp, bv + 3 * sp);
+                } else {
+                    if constexpr (sizeof(A) == 4) mat_dag_vec_acc2(Wm, p + 3 * sp, bv + 3 * sp);
+                    else mat_dag_vec_acc(Wm, p + 3 * sp, bv + 3 * sp);
+                }
             }
             bri_pair_acc(m, av, bv, acc[r]);
         }

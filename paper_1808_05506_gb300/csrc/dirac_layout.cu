@@ -361,3 +361,134 @@ cudaError_t launch_build_W(const Geom& g, const void* V64, void* tmp81, void* W6
 }
 
 }  // namespace dirac
+
+// ---------------------------------------------------------------- link formats
+namespace dirac {
+
+// two-row links: planes e = 0..5 of each storage link, in a layout with 6 planes
+template <typename T>
+__global__ void k_links_2row(long vol, long n, const void* __restrict__ src, void* dst)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;   // (mu, e < 6, site), site fastest
+    if (i >= n) return;
+    const long s = i % vol;
+    const long me = i / vol;
+    const int mu = (int)(me / 6), e = (int)(me % 6);
+    st_one<T>(dst, blk_index((size_t)vol, 6, mu, e, s), ld_one<T>(src, blk_index((size_t)vol, 9, mu, e, s)));
+}
+
+cudaError_t launch_links_2row(int prec, const Geom& g, const void* links, void* out, cudaStream_t st)
+{
+    const long n = g.vol * 4L * 6;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    switch (prec) {
+    case P_F32: k_links_2row<float><<<nb, 256, 0, st>>>(g.vol, n, links, out); break;
+    case P_BF16: k_links_2row<__nv_bfloat16><<<nb, 256, 0, st>>>(g.vol, n, links, out); break;
+    case P_F16: k_links_2row<__half><<<nb, 256, 0, st>>>(g.vol, n, links, out); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// max over the links of |U_2c - conj(U_0 x U_1)_c| in FP64 (non-negative
+// doubles order like their bit patterns, so the maximum is an integer atomic)
+__global__ void k_su3_deviation(long vol, const double2* __restrict__ V64, unsigned long long* dev)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;   // (mu, site), site fastest
+    double m = 0.0;
+    if (i < 4 * vol) {
+        const long s = i % vol;
+        const int mu = (int)(i / vol);
+        cx<double> U[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            const double2 v = V64[((size_t)mu * 9 + e) * vol + s];
+            U[e] = cx<double>{v.x, v.y};
+        }
+        cx<double> R[9];
+#pragma unroll
+        for (int e = 0; e < 6; ++e) R[e] = U[e];
+        reconstruct_row2(R);
+#pragma unroll
+        for (int c = 6; c < 9; ++c) {
+            const cx<double> d = R[c] - U[c];
+            m = fmax(m, sqrt(d.re * d.re + d.im * d.im));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(dev, (unsigned long long)__double_as_longlong(m));
+}
+
+cudaError_t launch_su3_deviation(const Geom& g, const void* V64, double* dev, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(dev, 0, sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const long n = 4 * g.vol;
+    k_su3_deviation<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g.vol, (const double2*)V64,
+                                                                 (unsigned long long*)dev);
+    return cudaGetLastError();
+}
+
+struct RepDirs {
+    signed char d[40][4];
+};
+
+// all 80 Brillouin directions per site: plane j < 40 is the stored W_{d_j}(x),
+// plane 40 + j is W_{-d_j}(x) = W_{d_j}(x - d_j)^+ (Tab. tab:off-axis caption),
+// both in the storage precision (a copy and a conjugate transpose: no rounding)
+template <typename T>
+__global__ void k_brillouin_w80(Geom g, RepDirs R, long n, const void* __restrict__ src, void* dst)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;   // (plane, e, site), site fastest
+    if (i >= n) return;
+    const long s = i % g.vol;
+    const long pe = i / g.vol;
+    const int j = (int)(pe / 9), e = (int)(pe % 9);
+    using A = typename Store<T>::A;
+    cx<A> v;
+    if (j < 40) {
+        v = ld_one<T>(src, blk_index((size_t)g.vol, 9, j, e, s));
+    } else {
+        const int rep = j - 40;
+        long r = s, sn = 0;
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const int L = g.L[mu];
+            const int x = (int)(r % L);
+            r /= L;
+            const int xm = (x - R.d[rep][mu] + L) % L;
+            sn += (long)xm * g.stride[mu];
+        }
+        const int a = e / 3, b = e % 3;   // (W^+)_ab = conj(W_ba)
+        v = conj(ld_one<T>(src, blk_index((size_t)g.vol, 9, rep, 3 * b + a, sn)));
+    }
+    st_one<T>(dst, blk_index((size_t)g.vol, 9, j, e, s), v);
+}
+
+cudaError_t launch_brillouin_w80(int prec, const Geom& g, const void* links, void* out, cudaStream_t st)
+{
+    BriDir dirs[80];
+    int reps[40];
+    brillouin_tables(dirs, reps);
+    RepDirs R;
+    for (int r = 0; r < 40; ++r) {
+        const int c = reps[r];
+        R.d[r][0] = (signed char)(c % 3 - 1);
+        R.d[r][1] = (signed char)((c / 3) % 3 - 1);
+        R.d[r][2] = (signed char)((c / 9) % 3 - 1);
+        R.d[r][3] = (signed char)((c / 27) % 3 - 1);
+    }
+    const long n = g.vol * 80L * 9;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    switch (prec) {
+    case P_F64: k_brillouin_w80<double><<<nb, 256, 0, st>>>(g, R, n, links, out); break;
+    case P_F32: k_brillouin_w80<float><<<nb, 256, 0, st>>>(g, R, n, links, out); break;
+    case P_BF16: k_brillouin_w80<__nv_bfloat16><<<nb, 256, 0, st>>>(g, R, n, links, out); break;
+    case P_F16: k_brillouin_w80<__half><<<nb, 256, 0, st>>>(g, R, n, links, out); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace dirac

@@ -322,9 +322,12 @@ static dirac_status eo_split_sweep(dirac_handle* h, SolverWS* w, int kind, int p
 static dirac_status apply_inner(dirac_handle* h, SolverWS* w, bool dag, void* out, const void* in,
                                 const double* diag_v)
 {
-    if (!w->eo)
-        return h->run_apply(dag, out, in, w->W, h->diag, h->links, w->prec, h->cfg, diag_v, 0, 0,
+    if (!w->eo) {
+        LaunchCfg c0 = h->cfg;
+        c0.fmt = 0;   // the captured graphs read the plain links
+        return h->run_apply(dag, out, in, w->W, h->diag, h->links, w->prec, c0, diag_v, 0, 0,
                             diag_v ? w->diag_vf : nullptr);
+    }
     dirac_status st;
     if (w->split) {
         if (!dag) {
@@ -552,7 +555,8 @@ static dirac_status fp64_residual(dirac_handle* h, SolverWS* w, const double* di
     } else {
         const void* L64 = nullptr;
         if ((st = h->ensure_links64b(&L64))) return st;
-        const LaunchCfg cfg64 = default_config(h->op, P_F64, W);
+        LaunchCfg cfg64 = default_config(h->op, P_F64, W);
+        cfg64.fmt = 0;
         if ((st = h->run_apply(false, w->r64, w->x64, W, h->diag, L64, P_F64, cfg64, diag_v))) return st;
         if ((st = h->cuda(blas_residual64(n, W, w->b64, w->r64, w->r64, w->part, w->rr64, S), "solve: residual")))
             return st;

@@ -32,7 +32,9 @@ static std::string tune_key(const dirac_handle* h)
     return buf;
 }
 
-static bool cache_lookup(const std::string& key, int* R, int* B, int* Pp, int* T, double* ms)
+// an entry: "<key> R<R> B<block> P<variant> T<order> F<link format> <ms>"
+// (lines written without F read as format 0)
+static bool cache_lookup(const std::string& key, int* R, int* B, int* Pp, int* T, double* ms, int* F = nullptr)
 {
     const char* path = getenv("DIRAC_TUNE_CACHE");
     if (!path || !*path) return false;
@@ -44,15 +46,16 @@ static bool cache_lookup(const std::string& key, int* R, int* B, int* Pp, int* T
     while (fgets(line, sizeof(line), f)) {
         const size_t kl = key.size();
         if (strncmp(line, key.c_str(), kl) == 0 && line[kl] == ' ') {
-            int r, b, tc;
+            int r, b, tc, pp, fm = 0;
             double t;
-            int pp;
-            if (sscanf(line + kl, " R%d B%d P%d T%d %lf", &r, &b, &pp, &tc, &t) == 5) {
+            if (sscanf(line + kl, " R%d B%d P%d T%d F%d %lf", &r, &b, &pp, &tc, &fm, &t) == 6 ||
+                (fm = 0, sscanf(line + kl, " R%d B%d P%d T%d %lf", &r, &b, &pp, &tc, &t) == 5)) {
                 *R = r;
                 *B = b;
                 *Pp = pp;
                 *T = tc;
                 *ms = t;
+                if (F) *F = fm;
                 found = true;   // the last entry wins
             }
         }
@@ -61,14 +64,14 @@ static bool cache_lookup(const std::string& key, int* R, int* B, int* Pp, int* T
     return found;
 }
 
-static void cache_store(const std::string& key, int R, int B, int Pp, int T, double ms)
+static void cache_store(const std::string& key, int R, int B, int Pp, int T, double ms, int F = 0)
 {
     const char* path = getenv("DIRAC_TUNE_CACHE");
     if (!path || !*path) return;
     std::lock_guard<std::mutex> lk(g_cache_mu);
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s R%d B%d P%d T%d %.6f\n", key.c_str(), R, B, Pp, T, ms);
+    fprintf(f, "%s R%d B%d P%d T%d F%d %.6f\n", key.c_str(), R, B, Pp, T, F, ms);
     fclose(f);
 }
 
@@ -164,11 +167,13 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
     if (!h) return DIRAC_ERR_INVALID_ARG;
     if (!h->have_links) return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_autotune: call dirac_set_links first");
     const std::string key = tune_key(h);
-    int R = 0, B = 0, Pp = 0, Tc = 0;
+    int R = 0, B = 0, Pp = 0, Tc = 0, Fm = 0;
     double best = 0.0;
-    if (!force && cache_lookup(key, &R, &B, &Pp, &Tc, &best) &&
+    if (!force && cache_lookup(key, &R, &B, &Pp, &Tc, &best, &Fm) &&
         apply_config_supported(h->op, h->prec, R, B, Pp, h->g) && Tc >= 0 && Tc <= h->g.L[3]) {
         h->cfg = LaunchCfg{R, B, Pp, Tc};
+        // the cached link format, if these links allow it
+        if (dirac_set_link_format(h, Fm) != DIRAC_OK) dirac_set_link_format(h, 0);
     } else {
         dirac_status st;
         if ((st = h->ensure_workspace())) return st;
@@ -182,64 +187,87 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
             cudaEventDestroy(e0);
             return st;
         }
+        // median of 5 timed calls after 2 warm-up calls; false if the shape
+        // cannot run here or a kernel recorded a failure (never picked)
+        auto time_cfg = [&](const LaunchCfg& c, double* med) -> bool {
+            std::vector<float> t;
+            cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream);
+            for (int rep = 0; rep < 7 && st == DIRAC_OK; ++rep) {
+                cudaEventRecord(e0, h->stream);
+                const dirac_status ls = h->run_apply(false, h->ws_out, h->ws_in, h->Nv, h->diag, h->links, h->prec, c);
+                if (ls != DIRAC_OK) {
+                    cudaGetLastError();
+                    return false;
+                }
+                cudaEventRecord(e1, h->stream);
+                st = h->cuda(cudaEventSynchronize(e1), "autotune");
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep >= 2) t.push_back(ms);   // two warm-up calls
+            }
+            if (st) return false;
+            int kerr = 0;
+            cudaMemcpy(&kerr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+            if (kerr) {
+                cudaMemset(h->dev_err, 0, sizeof(int));
+                return false;
+            }
+            std::sort(t.begin(), t.end());
+            *med = t[t.size() / 2];
+            const char* tr = getenv("DIRAC_TRACE");
+            if (tr && *tr && *tr != '0')
+                fprintf(stderr, "[dirac] autotune %s R=%d block=%d variant=%d order=%d format=%d: %.4f ms\n",
+                        key.c_str(), c.R, c.block, c.variant, c.order, c.fmt, *med);
+            return true;
+        };
         best = 1e30;
         LaunchCfg win = h->cfg;
+        win.fmt = 0;
         const int variants[] = {V_DIRECT, V_GROUPS, V_TMARCH, V_PIPE3, V_XROW};
-        for (int r : Rs) {
-            if (r > h->Nv && r != Rs.front()) continue;
-            for (int b : blocks)
-            for (int pp : variants)
-            for (int oi = 0; oi < 2; ++oi) {
-                if (!apply_config_supported(h->op, h->prec, r, b, pp, h->g)) continue;
-                // site order: lexicographic, or t-chunks of 8 slices (variants 0 and 1)
-                const int tc = oi == 0 ? 0 : std::min(8, h->g.L[3]);
-                if (oi == 1 && pp != V_DIRECT && pp != V_GROUPS) continue;
-                LaunchCfg c{r, b, pp, tc};
-                std::vector<float> t;
-                cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream);
-                bool launched = true;
-                for (int rep = 0; rep < 7 && st == DIRAC_OK; ++rep) {
-                    cudaEventRecord(e0, h->stream);
-                    const dirac_status ls =
-                        h->run_apply(false, h->ws_out, h->ws_in, h->Nv, h->diag, h->links, h->prec, c);
-                    if (ls != DIRAC_OK) {
-                        // this launch shape cannot run here (e.g. no tensor-map support): skip it
-                        cudaGetLastError();
-                        launched = false;
-                        break;
+        // link format 0 (the plain links) over every built launch shape, then
+        // link format 1 (two-row links / 80 stored W) over the shapes that read
+        // it, where the links allow it
+        const int saved_fmt = h->link_fmt;
+        bool have_alt = h->links_alt != nullptr;
+        if (!have_alt && (h->op == OP_BRILLOUIN || h->prec != P_F64)) {
+            have_alt = h->build_link_alt() == DIRAC_OK;
+            if (!have_alt) h->release_after_sync(h->links_alt);
+            h->err.clear();
+        }
+        for (int fm = 0; fm < (have_alt ? 2 : 1) && st == DIRAC_OK; ++fm)
+            for (int r : Rs) {
+                if (r > h->Nv && r != Rs.front()) continue;
+                for (int b : blocks)
+                for (int pp : variants)
+                for (int oi = 0; oi < 2; ++oi) {
+                    if (!apply_config_supported(h->op, h->prec, r, b, pp, h->g)) continue;
+                    if (fm == 1 && !link_format_supported(h->op, h->prec, pp)) continue;
+                    // site order: lexicographic, or t-chunks of 8 slices (variants 0 and 1)
+                    const int tc = oi == 0 ? 0 : std::min(8, h->g.L[3]);
+                    if (oi == 1 && pp != V_DIRECT && pp != V_GROUPS) continue;
+                    LaunchCfg c{r, b, pp, tc, fm};
+                    double med = 0.0;
+                    if (!time_cfg(c, &med)) {
+                        if (st) break;
+                        continue;
                     }
-                    cudaEventRecord(e1, h->stream);
-                    st = h->cuda(cudaEventSynchronize(e1), "autotune");
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (rep >= 2) t.push_back(ms);   // two warm-up calls
+                    if (med < best) {
+                        best = med;
+                        win = c;
+                    }
                 }
                 if (st) break;
-                if (!launched) continue;
-                int kerr = 0;
-                cudaMemcpy(&kerr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
-                if (kerr) {   // a kernel recorded a failure in this variant: never pick it
-                    cudaMemset(h->dev_err, 0, sizeof(int));
-                    continue;
-                }
-                std::sort(t.begin(), t.end());
-                const double med = t[t.size() / 2];
-                const char* tr = getenv("DIRAC_TRACE");
-                if (tr && *tr && *tr != '0')
-                    fprintf(stderr, "[dirac] autotune %s R=%d block=%d variant=%d order=%d: %.4f ms\n", key.c_str(),
-                            r, b, pp, tc, med);
-                if (med < best) {
-                    best = med;
-                    win = c;
-                }
             }
-            if (st) break;
-        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        if (st) return st;
-        h->cfg = win;
-        cache_store(key, win.R, win.block, win.variant, win.order, best);
+        if (st) {
+            h->link_fmt = saved_fmt;
+            return st;
+        }
+        h->cfg = LaunchCfg{win.R, win.block, win.variant, win.order};
+        h->link_fmt = win.fmt == 1 ? 1 : 0;
+        if (h->link_fmt == 0) h->release_after_sync(h->links_alt);
+        cache_store(key, win.R, win.block, win.variant, win.order, best, h->link_fmt);
     }
     dirac_status est = tune_even_odd(h, force);
     if (est) return est;

@@ -64,6 +64,8 @@ def test_null_handle_calls(dg):
     assert dg.dirac_apply(None, None, None, 0) == dg.ERR_INVALID_ARG
     assert dg.dirac_set_preconditioner(None, 1) == dg.ERR_INVALID_ARG
     assert dg.dirac_get_preconditioner(None, None) == dg.ERR_INVALID_ARG
+    assert dg.dirac_set_link_format(None, 1) == dg.ERR_INVALID_ARG
+    assert dg.dirac_get_link_format(None, None) == dg.ERR_INVALID_ARG
     assert dg.dirac_set_residual_arithmetic(None, 1) == dg.ERR_INVALID_ARG
     assert dg.dirac_get_residual_arithmetic(None, None) == dg.ERR_INVALID_ARG
     assert dg.dirac_set_inner_fields(None, 1) == dg.ERR_INVALID_ARG

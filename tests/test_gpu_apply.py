@@ -323,6 +323,103 @@ def test_brillouin_full_size_sampled(dg):
     assert rel_l2(got[sites], want, rhs_axis=1) <= TOL["f32"]
 
 
+@pytest.mark.parametrize("op,mass", [("wilson", 0.1237), ("staggered", 0.031)])
+@pytest.mark.parametrize("prec", ["f32", "bf16", "f16"])
+def test_two_row_links(dg, op, mass, prec):
+    """Link format 1 for Wilson and staggered (gauge compression: the first
+    two rows of each Haar link stored, the third rebuilt as the conjugate
+    cross product): parity with the oracle on a ragged volume in every launch
+    shape that reads it, D and D^+; links that are not special unitary are
+    refused and format 0 stays."""
+    L, Nv = (6, 4, 6, 5), 5
+    V, psi = inputs(op, L, Nv, "f32", 300)
+    Vr, pr = rounded_for_oracle(V, psi, prec)
+    D = dg.Dirac(op, L, Nv, mass, prec)
+    D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
+    D.set_link_format(1)
+    assert D.link_format() == 1
+    xi = D.pack(torch.from_numpy(psi.astype(np.complex64)).cuda())
+    Rs = (1, 2, 4, 6) if op == "staggered" else (1, 2, 3, 4)
+    for dag in (False, True):
+        want = oracle.apply(op, Vr, pr, m0_of(op, mass), dagger=dag)
+        for R in Rs:
+            for block in (32, 64):
+                if not dg.config_supported(op, prec, R, block, 1, L):
+                    continue
+                D.set_kernel_config(R, block, 1)
+                yi = D.new_internal()
+                yi.fill_(0xFF)
+                D.apply(xi, out=yi, dagger=dag)
+                got = D.unpack(yi).cpu().numpy().astype(np.complex128)
+                assert rel_l2(got, want) <= TOL[prec], (R, block, dag)
+    # Gaussian matrices are not special unitary: refused, format 0 stays
+    G = synth.complex_gaussian(synth.lattice_shape(L) + (4, 3, 3), 301)
+    D.set_link_format(0)
+    D.set_links(torch.from_numpy(G.astype(np.complex64)).cuda())
+    with pytest.raises(dg.DiracError) as e:
+        D.set_link_format(1)
+    assert e.value.status == dg.ERR_INVALID_ARG and "special unitary" in str(e.value)
+    assert D.link_format() == 0
+    # recorded before the links: built at set_links; links that fail the check switch back to 0
+    D2 = dg.Dirac(op, L, Nv, mass, prec)
+    D2.set_link_format(1)
+    D2.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
+    assert D2.link_format() == 1
+    D2.set_links(torch.from_numpy(G.astype(np.complex64)).cuda())
+    assert D2.link_format() == 0
+    D.close()
+    D2.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_brillouin_80_stored_links(dg, prec):
+    """Brillouin link format 1 (all 80 W stored per site, W_{-d}(x) copied
+    from W_d(x - d)^+ without rounding): bit for bit the 40-link sweep in
+    variants 0 and 1, D and D^+, and parity with the oracle."""
+    L, Nv = (4, 6, 2, 5), 3
+    V, psi = inputs("brillouin", L, Nv, prec, 310, kind="near_identity")
+    cdt = np.complex128 if prec == "f64" else np.complex64
+    D = dg.Dirac("brillouin", L, Nv, 0.07, prec)
+    D.set_links(torch.from_numpy(V.astype(cdt)).cuda())
+    xi = D.pack(torch.from_numpy(psi.astype(cdt)).cuda())
+    for variant in (0, 1):
+        D.set_kernel_config(2, 64, variant)
+        for dag in (False, True):
+            D.set_link_format(0)
+            ref = D.apply(xi, out=D.new_internal().zero_(), dagger=dag).clone()
+            D.set_link_format(1)
+            got = D.apply(xi, out=D.new_internal().zero_(), dagger=dag)
+            assert torch.equal(got, ref), (variant, dag)
+    if prec != "bf16":
+        y = D.unpack(got).cpu().numpy().astype(np.complex128)
+        want = oracle.apply("brillouin", V, psi, 0.07, dagger=True)
+        assert rel_l2(y, want) <= TOL[prec]
+    D.close()
+
+
+def test_autotune_link_format(dg, tmp_path, monkeypatch):
+    """The tuner times both link formats and records the winner; the tuned
+    handle reproduces the sweep, and a second handle takes the format from the
+    cache."""
+    monkeypatch.setenv("DIRAC_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    L, Nv = (8, 8, 4, 8), 4
+    V, psi = inputs("wilson", L, Nv, "f32", 311)
+    D = dg.Dirac("wilson", L, Nv, 0.12, "f32")
+    D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
+    D.autotune(force=True)
+    f = D.link_format()
+    assert f in (0, 1)
+    assert " F%d " % f in (tmp_path / "tune.txt").read_text()
+    got = D.apply(torch.from_numpy(psi.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
+    assert rel_l2(got, oracle.apply("wilson", V, psi, oracle.kappa_to_m0(0.12))) <= TOL["f32"]
+    D2 = dg.Dirac("wilson", L, Nv, 0.12, "f32")
+    D2.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
+    D2.autotune()
+    assert D2.link_format() == f and D2.kernel_config() == D.kernel_config()
+    D.close()
+    D2.close()
+
+
 def test_error_paths(dg):
     D = dg.Dirac("wilson", (4, 4, 4, 4), 2, 0.12, "f32")
     x = D.new_canonical()
