@@ -729,7 +729,9 @@ def main():
                      "peak_kind": f"{peak_kind} copy bandwidth",
                      "kernel": "k_{}{}<{},R={}>".format(op, {0: "", 1: "_groups", 2: "_march", 3: "_pipe", 5: "_xrow"}[cfg[2]],
                                                       w["prec"], cfg[0]),
-                     "algorithmic_bytes_per_launch": bytes_step},
+                     "algorithmic_bytes_per_launch": bytes_step,
+                     "link_format": link_fmt,
+                     "bytes_per_launch_nine_entry_links": dg.bytes_per_site(op, w["Nv"], w["prec"]) * vol},
         "clocks": clk.summary(),
         "e2e": {"value": flops_step / (e2e_ms * 1e-3) / 1e9, "unit": "Gflop/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -310,18 +310,20 @@ DIRAC_API dirac_status dirac_apply_static(dirac_handle* h, void* out, const void
 DIRAC_API dirac_status dirac_set_preconditioner(dirac_handle* h, int mode);
 DIRAC_API dirac_status dirac_get_preconditioner(const dirac_handle* h, int* mode);
 
-/* Fields of the even-odd inner solves of 16-bit Wilson handles.
+/* Fields of the inner solves of 16-bit handles (Wilson with even-odd inner
+ * solves, Brillouin with its whole-lattice inner solve).
  *   mode 0: every inner field in the handle's 16-bit precision.
- *   mode 1 (split, the default): the search directions p and s = S^+ r (and the adjoint
- *          sweep's intermediate) in 16 bits; the solution e, the residual r,
- *          the products t = S p and the links in FP32.  Because t is formed
- *          exactly (to FP32) from the 16-bit p that also updates e, the
- *          recursive residual stays the true one to FP32 accuracy, so an
- *          inner solve reaches FP32-level reductions (the rounding of p only
- *          perturbs the search directions) while half of its vector traffic
- *          and the sweeps' direction inputs stay 16-bit.
- * Other handles (FP32, FP64, staggered, Brillouin, whole-lattice inner
- * solves) ignore the mode.  The stats field split_fields reports it.
+ *   mode 1 (split, the default): the search directions p and s = A^+ r (and
+ *          the Wilson adjoint sweep's intermediate) in 16 bits; the solution
+ *          e, the residual r, the products t = A p and the links (Brillouin:
+ *          the 40 stored W) in FP32.  Because t is formed exactly (to FP32)
+ *          from the 16-bit p that also updates e, the recursive residual stays
+ *          the true one to FP32 accuracy, so an inner solve reaches FP32-level
+ *          reductions (the rounding of p only perturbs the search directions)
+ *          while half of its vector traffic and the sweeps' direction inputs
+ *          stay 16-bit.
+ * Other handles (FP32, FP64, staggered, Wilson whole-lattice inner solves)
+ * ignore the mode.  The stats field split_fields reports it.
  * Measured (4 Wilson systems on 32^3 x 64, 24 slots, to 1e-10): split BF16
  * 5.26 s and FP16 5.20 s, against 7.27 s / 6.48 s with all fields in 16 bits
  * and 5.61 s for FP32 storage; the split solve takes the FP32 solve's

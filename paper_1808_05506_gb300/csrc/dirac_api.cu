@@ -333,6 +333,12 @@ dirac_status dirac_set_links(dirac_handle* h, const void* V, dirac_prec V_prec, 
         if ((st = h->build_W64())) return st;
         st = h->cuda(launch_convert_links(h->prec, h->g, 40, h->W64, h->links, h->stream), "W conversion");
         if (st) return st;
+        // the FP32 copy of the split inner solve is refreshed in place (a
+        // captured solver graph holds its address)
+        if (h->links32 && h->links32 != h->links) {
+            st = h->cuda(launch_convert_links(P_F32, h->g, 40, h->W64, h->links32, h->stream), "FP32 W");
+            if (st) return st;
+        }
         if (h->prec != P_F64) h->release_after_sync(h->W64);   // rebuilt on demand by the solver
     } else {
         st = h->cuda(launch_convert_links(h->prec, h->g, 4, h->links64, h->links, h->stream), "links conversion");
@@ -434,15 +440,18 @@ dirac_status dirac_handle::ensure_links_df(const void** out)
 
 dirac_status dirac_handle::ensure_links32(const void** out)
 {
-    if (prec == P_F32 && op != OP_BRILLOUIN) {
+    if (prec == P_F32) {
         *out = links;
         return DIRAC_OK;
     }
-    if (op == OP_BRILLOUIN) return fail(DIRAC_ERR_UNSUPPORTED, "FP32 link copy: Wilson and staggered only");
     if (!links32) {
+        // Brillouin: the 40 stored W in FP32 (from the FP64 W, which the solver builds first)
+        const int nmat = op == OP_BRILLOUIN ? 40 : 4;
+        const void* src = op == OP_BRILLOUIN ? W64 : links64;
+        if (!src) return fail(DIRAC_ERR_INVALID_ARG, "FP32 link copy: no FP64 links");
         dirac_status st;
-        if ((st = alloc(&links32, nblk_of((size_t)g.vol) * 32 * 9 * 4 * 8, "FP32 links (blocked)"))) return st;
-        if ((st = cuda(launch_convert_links(P_F32, g, 4, links64, links32, stream), "FP32 links (blocked)"))) {
+        if ((st = alloc(&links32, nblk_of((size_t)g.vol) * 32 * 9 * nmat * 8, "FP32 links (blocked)"))) return st;
+        if ((st = cuda(launch_convert_links(P_F32, g, nmat, src, links32, stream), "FP32 links (blocked)"))) {
             release(links32);
             return st;
         }

@@ -82,6 +82,12 @@ cudaError_t launch_apply_wilson(int prec, bool dagger, const ApplyArgs& a, Launc
 cudaError_t launch_apply_brillouin(int prec, bool dagger, const ApplyArgs& a, LaunchCfg cfg,
                                    cudaStream_t st);
 
+// Brillouin sweeps of the split inner solve (apply_brillouin_split.cuh):
+// dag = false t(F32) = D p(16), dag = true s(16) = D^+ r(F32), FP32 W; prepare
+// uploads the direction table (once per device, before any stream capture)
+cudaError_t brillouin_split_prepare(int prec16, cudaStream_t st);
+cudaError_t launch_brillouin_split(int prec16, bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st);
+
 // the 80 Brillouin directions and the dir81 code of each of the 40 stored ones
 void brillouin_tables(BriDir dirs[80], int rep_dir81[40]);
 cudaError_t upload_brillouin_table(cudaStream_t st);

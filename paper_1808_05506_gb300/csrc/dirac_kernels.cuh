@@ -23,6 +23,8 @@
 // B_4 = 1; gamma5 = diag(1, 1, -1, -1).
 #pragma once
 
+#include <type_traits>
+
 #include "dirac_common.cuh"
 
 namespace dirac {
@@ -705,10 +707,15 @@ DEV_INLINE void bri_pair_acc(const BriDirA<A>& m, const cx<A>* av, const cx<A>* 
 // rho part, so both colour products are formed first and one spin matrix
 // application serves the pair.
 // LF 0: 40 stored links, W_{-d}(x) = W_d(x - d)^+ read at the neighbour x - d;
-// LF 1: all 80 stored at x, W_{-d}(x) in plane 40 + rep (local reads)
-template <typename T, int R, bool DAG, int LF = 0>
+// LF 1: all 80 stored at x, W_{-d}(x) in plane 40 + rep (local reads).
+// T is the storage type of the links; TI, TO those of the input and output
+// fields (the split inner solve reads 16-bit directions and writes FP32
+// products, or the reverse), all with the same arithmetic type.
+template <typename T, int R, bool DAG, int LF = 0, typename TI = T, typename TO = T>
 DEV_INLINE void brillouin_site(const ApplyArgs& a, long s, int group, const BriDir* dirs)
 {
+    static_assert(std::is_same<typename Store<T>::A, typename Store<TI>::A>::value &&
+                  std::is_same<typename Store<T>::A, typename Store<TO>::A>::value, "one arithmetic type");
     using A = typename Store<T>::A;
     long fwd[4], bwd[4];
     int x[4];
@@ -738,7 +745,7 @@ DEV_INLINE void brillouin_site(const ApplyArgs& a, long s, int group, const BriD
         for (int r = 0; r < R; ++r) {
             const int v = min(v0 + r, a.Nv - 1);   // partial group: recompute, store guarded
             cx<A> p[12], av[12], bv[12];
-            load_spinor<T, 12>(a.in, a.g.vol, v, np, p);
+            load_spinor<TI, 12>(a.in, a.g.vol, v, np, p);
 #pragma unroll
             for (int sp = 0; sp < 4; ++sp) {
 #pragma unroll
@@ -746,7 +753,7 @@ DEV_INLINE void brillouin_site(const ApplyArgs& a, long s, int group, const BriD
                 if constexpr (sizeof(A) == 4) mat_vec_acc2(Wp, p + 3 * sp, av + 3 * sp);
                 else mat_vec_acc(Wp, p + 3 * sp, av + 3 * sp);
             }
-            load_spinor<T, 12>(a.in, a.g.vol, v, nm, p);
+            load_spinor<TI, 12>(a.in, a.g.vol, v, nm, p);
 #pragma unroll
             for (int sp = 0; sp < 4; ++sp) {
 #pragma unroll
@@ -767,13 +774,13 @@ DEV_INLINE void brillouin_site(const ApplyArgs& a, long s, int group, const BriD
         const int v = min(v0 + r, a.Nv - 1);
         const A dg = diag_of<A>(a, v);
         cx<A> p[12];
-        load_spinor<T, 12>(a.in, a.g.vol, v, s, p);
+        load_spinor<TI, 12>(a.in, a.g.vol, v, s, p);
 #pragma unroll
         for (int i = 0; i < 12; ++i) {
             p[i].re = fma(dg, p[i].re, acc[r][i].re);
             p[i].im = fma(dg, p[i].im, acc[r][i].im);
         }
-        if (v0 + r < a.Nv) store_spinor<T, 12>(a.out, a.g.vol, v0 + r, s, p);
+        if (v0 + r < a.Nv) store_spinor<TO, 12>(a.out, a.g.vol, v0 + r, s, p);
     }
 }
 

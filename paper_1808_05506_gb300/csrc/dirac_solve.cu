@@ -159,6 +159,8 @@ struct SolverWS {
     LaunchCfg g_cfg{0, 0, 0};
     LaunchCfg g_eo_cfg{0, 0, 0};
     const void* g_links = nullptr;
+    const void* g_alt = nullptr;
+    int g_fmt = 0;
     const double* g_diag = nullptr;
     double g_dval = 0.0;
 };
@@ -214,7 +216,7 @@ static dirac_status ensure_solver_ws(dirac_handle* h, bool eo, bool split, Solve
     // e, r, t, tmp, re, ro in pa; s, p, tmp2 in pd
     void** inner[] = {&w->e, &w->r, &w->t, &w->s, &w->p, &w->tmp, &w->re, &w->ro, &w->tmp2};
     const bool in_pa[] = {true, true, true, false, false, true, true, true, false};
-    const int ninner = split ? 9 : (eo ? 8 : 5);
+    const int ninner = split && eo ? 9 : (eo ? 8 : 5);
     size_t inner_bytes = 0;
     for (int i = 0; i < ninner; ++i) {
         const size_t fb = in_pa[i] ? fa : fd;
@@ -242,6 +244,8 @@ static dirac_status ensure_solver_ws(dirac_handle* h, bool eo, bool split, Solve
     w->eoc = w->scal + (size_t)nslots * h->Nv + 1 + ((size_t)h->Nv + 1) / 2;
     if ((st = h->alloc(&pp, ((size_t)h->Nv + 2) * sizeof(int), "solver flags"))) return st;
     w->iflags = (int*)pp;
+    if (split && !eo && (st = h->cuda(brillouin_split_prepare(w->pd, h->stream), "solver: direction table")))
+        return st;
     if ((st = h->cuda(cudaStreamCreateWithFlags(&w->cs, cudaStreamNonBlocking), "solver stream"))) return st;
     if ((st = h->cuda(cudaEventCreateWithFlags(&w->ev, cudaEventDisableTiming), "solver event"))) return st;
     h->sw_bytes = 3 * f64 + inner_bytes;
@@ -323,10 +327,28 @@ static dirac_status apply_inner(dirac_handle* h, SolverWS* w, bool dag, void* ou
                                 const double* diag_v)
 {
     if (!w->eo) {
+        // the handle's launch shape and link format (a captured graph is
+        // rebuilt when either changes, and the format-1 links keep their
+        // address across dirac_set_links)
         LaunchCfg c0 = h->cfg;
-        c0.fmt = 0;   // the captured graphs read the plain links
-        return h->run_apply(dag, out, in, w->W, h->diag, h->links, w->prec, c0, diag_v, 0, 0,
-                            diag_v ? w->diag_vf : nullptr);
+        if (!w->split)
+            return h->run_apply(dag, out, in, w->W, h->diag, h->links, w->prec, c0, diag_v, 0, 0,
+                                diag_v ? w->diag_vf : nullptr);
+        c0.fmt = 0;   // the FP32 W copy of the split solve holds the 40 stored directions
+        // split Brillouin fields: t(F32) = D p(16), s(16) = D^+ r(F32) with FP32 W
+        const void* L32 = nullptr;
+        dirac_status st;
+        if ((st = h->ensure_links32(&L32))) return st;
+        ApplyArgs a = h->args(out, in, w->W, h->diag);
+        a.links = L32;
+        a.diag_v = diag_v;
+        a.diag_vf = diag_v ? w->diag_vf : nullptr;
+        a.tc = (c0.variant == V_DIRECT || c0.variant == V_GROUPS) ? c0.order : 0;
+        if (a.tc > 0) {
+            a.fdc = make_fdiv((uint32_t)(h->g.L[2] * a.tc));
+            a.fdt = make_fdiv((uint32_t)a.tc);
+        }
+        return h->cuda(launch_brillouin_split(w->pd, dag, a, c0, h->stream), "solve: split Brillouin sweep");
     }
     dirac_status st;
     if (w->split) {
@@ -389,7 +411,7 @@ static dirac_status ensure_graph(dirac_handle* h, SolverWS* w, const double* dia
     };
     // the whole-lattice sweeps take the handle's diagonal by value (dirac_set_mass may change it)
     if (w->gexec && same(w->g_cfg, h->cfg) && same(w->g_eo_cfg, h->eo_cfg) && w->g_links == h->links &&
-        w->g_diag == diag_v && w->g_dval == h->diag)
+        w->g_alt == h->links_alt && w->g_fmt == h->link_fmt && w->g_diag == diag_v && w->g_dval == h->diag)
         return DIRAC_OK;
     if (w->gexec) {
         cudaGraphExecDestroy(w->gexec);
@@ -413,6 +435,8 @@ static dirac_status ensure_graph(dirac_handle* h, SolverWS* w, const double* dia
     w->g_cfg = h->cfg;
     w->g_eo_cfg = h->eo_cfg;
     w->g_links = h->links;
+    w->g_alt = h->links_alt;
+    w->g_fmt = h->link_fmt;
     w->g_diag = diag_v;
     w->g_dval = h->diag;
     return DIRAC_OK;
@@ -492,7 +516,7 @@ static dirac_status refine_step(dirac_handle* h, SolverWS* w, const double* diag
                                 const std::vector<double>& rr64, int max_inner, double inner_tol,
                                 dirac_solve_stats* S_)
 {
-    const int W = w->W, P = w->prec;
+    const int W = w->W;
     const size_t n = (size_t)nsc_of(h->op) * nblk_of((size_t)h->g.vol) * 32;
     cudaStream_t S = h->stream;
     dirac_status st;
@@ -509,13 +533,15 @@ static dirac_status refine_step(dirac_handle* h, SolverWS* w, const double* diag
         return st;
     bool bd = false;
     if (!w->eo) {
-        if ((st = h->cuda(blas_convert(P_F64, P, nsc_of(h->op), h->g.vol, W, w->r64, w->scale, w->r, w->part,
+        // r_hat and e in the precision of the inner residual (FP32 with split fields)
+        if ((st = h->cuda(blas_convert(P_F64, w->pa, nsc_of(h->op), h->g.vol, W, w->r64, w->scale, w->r, w->part,
                                        w->rr0, S), "solve: r_hat")))
             return st;
         if ((st = inner_cgls(h, w, diag_v, max_inner, inner_tol, S_, &bd))) return st;
         // x += (|r| / sqrt(n)) e in FP64 (the update is kept even after a breakdown:
         // the next FP64 residual decides)
-        return h->cuda(blas_axpy_to64(P, nsc_of(h->op), h->g.vol, W, w->coef, w->e, w->x64, S), "solve: x update");
+        return h->cuda(blas_axpy_to64(w->pa, nsc_of(h->op), h->g.vol, W, w->coef, w->e, w->x64, S),
+                       "solve: x update");
     }
     // even-odd: r_hat -> (r_e, r_o); the Schur right-hand side r = r_o - H_oe r_e / a
     if ((st = upload_eo_coef(h, w))) return st;
@@ -624,11 +650,12 @@ static double default_inner_tol(const SolverWS* w)
     return w->pd == P_F16 ? 2e-3 : 1e-2;
 }
 
-// whether the even-odd inner solve keeps split fields: asked for, Wilson
-// (CGLS), 16-bit storage
+// whether the inner solve keeps split fields: asked for, 16-bit storage, and
+// the Wilson even-odd (CGLS) or the Brillouin whole-lattice inner solve
 static bool use_split(const dirac_handle* h, bool eo)
 {
-    return eo && h->inner_fields == 1 && h->op == OP_WILSON && (h->prec == P_BF16 || h->prec == P_F16);
+    return h->inner_fields == 1 && (h->prec == P_BF16 || h->prec == P_F16) &&
+           ((eo && h->op == OP_WILSON) || (!eo && h->op == OP_BRILLOUIN));
 }
 
 static dirac_status check_solver_args(dirac_handle* h, double tol, int max_outer, int max_inner, double inner_tol,
