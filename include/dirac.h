@@ -316,7 +316,7 @@ DIRAC_API dirac_status dirac_get_preconditioner(const dirac_handle* h, int* mode
  *   mode 1 (split, the default): the search directions p and s = A^+ r (and
  *          the Wilson adjoint sweep's intermediate) in 16 bits; the solution
  *          e, the residual r, the products t = A p and the links (Brillouin:
- *          the 40 stored W) in FP32.  Because t is formed exactly (to FP32)
+ *          all 80 W per site, as in link format 1) in FP32.  Because t is formed exactly (to FP32)
  *          from the 16-bit p that also updates e, the recursive residual stays
  *          the true one to FP32 accuracy, so an inner solve reaches FP32-level
  *          reductions (the rounding of p only perturbs the search directions)

@@ -1,6 +1,6 @@
 // Brillouin sweeps of the split inner solve (Sec. 5, Eqs. def_bril, def_der,
-// def_lap at c_SW = 0): FP32 links W and FP32 arithmetic, with one of the two
-// fields in 16 bits -- t(F32) = D p(16) for the search direction p, and
+// def_lap at c_SW = 0): FP32 links W (all 80 directions stored per site, link
+// format 1) and FP32 arithmetic, with one of the two fields in 16 bits -- t(F32) = D p(16) for the search direction p, and
 // s(16) = D^+ r(F32) for the residual r.  The product t is exact to FP32 for
 // the 16-bit p that also updates the solution, so the recursive residual of
 // the inner CGLS stays the true one.  Included by one translation unit per
@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(256) k_bri_split(ApplyArgs a, int ngroups)
     const int group = (int)(b % ngroups);
     const long p = (b / ngroups) * blockDim.x + threadIdx.x;
     if (p >= a.nsites) return;
-    brillouin_site<float, R, DAG, 0, TI, TO>(a, slab_site(a, p), group, c_split_dirs);
+    brillouin_site<float, R, DAG, 1, TI, TO>(a, slab_site(a, p), group, c_split_dirs);
 }
 
 template <typename TI, typename TO, int R, bool DAG>
@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(192, 2) k_bri_split_groups(ApplyArgs a, int ng
     const int group = (int)(b % nchunks) * gy + threadIdx.y;
     const long p = (b / nchunks) * blockDim.x + threadIdx.x;
     if (p >= a.nsites || group >= ngroups) return;
-    brillouin_site<float, R, DAG, 0, TI, TO>(a, slab_site(a, p), group, c_split_dirs);
+    brillouin_site<float, R, DAG, 1, TI, TO>(a, slab_site(a, p), group, c_split_dirs);
 }
 
 static cudaError_t split_table(cudaStream_t st)
@@ -73,11 +73,12 @@ static cudaError_t split_go(const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
 }
 
 // dag = false: a.in 16-bit (H), a.out FP32; dag = true: a.in FP32, a.out 16-bit;
-// a.links FP32 W (40 stored directions); R = 2 for c.R >= 2, else 1
+// a.links FP32 W, 80 directions per site; R = min(c.R, 3)
 template <typename H>
 static cudaError_t split_launch(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
 {
-    if (c.R >= 2) return dag ? split_go<float, H, 2, true>(a, c, st) : split_go<H, float, 2, false>(a, c, st);
+    if (c.R >= 3) return dag ? split_go<float, H, 3, true>(a, c, st) : split_go<H, float, 3, false>(a, c, st);
+    if (c.R == 2) return dag ? split_go<float, H, 2, true>(a, c, st) : split_go<H, float, 2, false>(a, c, st);
     return dag ? split_go<float, H, 1, true>(a, c, st) : split_go<H, float, 1, false>(a, c, st);
 }
 

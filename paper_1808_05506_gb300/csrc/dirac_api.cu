@@ -335,10 +335,7 @@ dirac_status dirac_set_links(dirac_handle* h, const void* V, dirac_prec V_prec, 
         if (st) return st;
         // the FP32 copy of the split inner solve is refreshed in place (a
         // captured solver graph holds its address)
-        if (h->links32 && h->links32 != h->links) {
-            st = h->cuda(launch_convert_links(P_F32, h->g, 40, h->W64, h->links32, h->stream), "FP32 W");
-            if (st) return st;
-        }
+        if (h->links32 && h->links32 != h->links && (st = h->refresh_links32())) return st;
         if (h->prec != P_F64) h->release_after_sync(h->W64);   // rebuilt on demand by the solver
     } else {
         st = h->cuda(launch_convert_links(h->prec, h->g, 4, h->links64, h->links, h->stream), "links conversion");
@@ -445,19 +442,31 @@ dirac_status dirac_handle::ensure_links32(const void** out)
         return DIRAC_OK;
     }
     if (!links32) {
-        // Brillouin: the 40 stored W in FP32 (from the FP64 W, which the solver builds first)
-        const int nmat = op == OP_BRILLOUIN ? 40 : 4;
+        // Brillouin: all 80 W per site in FP32 (link format 1), from the FP64 W,
+        // which the solver builds first
         const void* src = op == OP_BRILLOUIN ? W64 : links64;
         if (!src) return fail(DIRAC_ERR_INVALID_ARG, "FP32 link copy: no FP64 links");
         dirac_status st;
+        const size_t nmat = op == OP_BRILLOUIN ? 80 : 4;
         if ((st = alloc(&links32, nblk_of((size_t)g.vol) * 32 * 9 * nmat * 8, "FP32 links (blocked)"))) return st;
-        if ((st = cuda(launch_convert_links(P_F32, g, nmat, src, links32, stream), "FP32 links (blocked)"))) {
+        if ((st = refresh_links32())) {
             release(links32);
             return st;
         }
     }
     *out = links32;
     return DIRAC_OK;
+}
+
+// the FP32 link copy of the split inner solve from the FP64 links (Brillouin:
+// W64 into planes 0..39, then planes 40..79 = W_{-d}(x) in place)
+dirac_status dirac_handle::refresh_links32()
+{
+    if (op != OP_BRILLOUIN)
+        return cuda(launch_convert_links(P_F32, g, 4, links64, links32, stream), "FP32 links (blocked)");
+    dirac_status st;
+    if ((st = cuda(launch_convert_links(P_F32, g, 40, W64, links32, stream), "FP32 W (blocked)"))) return st;
+    return cuda(launch_brillouin_w80(P_F32, g, links32, links32, stream), "FP32 W, 80 directions");
 }
 
 dirac_status dirac_handle::build_W64()

@@ -27,7 +27,8 @@ struct dirac_handle {
     void* links64 = nullptr;  // FP64 V_mu [4][9][site]
     void* W64 = nullptr;      // FP64 W [40][9][site] (Brillouin; kept for F64 handles, lazy otherwise)
     void* links_df = nullptr; // the same in double-float storage (dirac_df.cuh), for the residual (lazy)
-    void* links32 = nullptr;  // FP32 V_mu, blocked layout, for the split inner solve (lazy)
+    void* links32 = nullptr;  // FP32 links of the split inner solve, blocked layout (lazy):
+                              // V_mu, or all 80 Brillouin W per site
     void* links64b = nullptr; // FP64 links of the operator (V or W) in the blocked layout of the
                               // sweeps, for the solver's FP64 residual (lazy; F64 handles use links)
     void* links_alt = nullptr;  // link format 1 (dirac_set_link_format): Wilson / staggered two-row
@@ -64,6 +65,7 @@ struct dirac_handle {
     dirac_status ensure_links64b(const void** out);
     dirac_status ensure_links_df(const void** out);
     dirac_status ensure_links32(const void** out);
+    dirac_status refresh_links32();
     dirac_status build_link_alt();
     dirac::ApplyArgs args(void* out, const void* in, int nv, double diag_value) const;
     dirac_status run_apply(bool dagger, void* out, const void* in, int nv, double diag_value,

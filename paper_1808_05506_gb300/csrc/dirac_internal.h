@@ -70,6 +70,7 @@ cudaError_t launch_links_2row(int prec, const Geom& g, const void* links, void* 
 cudaError_t launch_su3_deviation(const Geom& g, const void* V64, double* dev, cudaStream_t st);
 // Brillouin: all 80 directions per site [80][site/32][9][32] from the 40 stored
 // ones: planes 0..39 copied, plane 40 + j holds W_{-d_j}(x) = W_{d_j}(x - d_j)^+
+// (in place when out == links: an 80-plane array whose planes 0..39 are set)
 cudaError_t launch_brillouin_w80(int prec, const Geom& g, const void* links, void* out, cudaStream_t st);
 
 // out = D in (or D^+ in) on internal-layout fields

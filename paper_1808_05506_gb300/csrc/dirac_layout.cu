@@ -437,14 +437,16 @@ struct RepDirs {
 // all 80 Brillouin directions per site: plane j < 40 is the stored W_{d_j}(x),
 // plane 40 + j is W_{-d_j}(x) = W_{d_j}(x - d_j)^+ (Tab. tab:off-axis caption),
 // both in the storage precision (a copy and a conjugate transpose: no rounding)
+// planes j0..79 (j0 = 40 when src and dst are the same array: only the
+// adjoint planes are written, read from the stored ones)
 template <typename T>
-__global__ void k_brillouin_w80(Geom g, RepDirs R, long n, const void* __restrict__ src, void* dst)
+__global__ void k_brillouin_w80(Geom g, RepDirs R, int j0, long n, const void* __restrict__ src, void* dst)
 {
-    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;   // (plane, e, site), site fastest
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;   // (plane - j0, e, site), site fastest
     if (i >= n) return;
     const long s = i % g.vol;
     const long pe = i / g.vol;
-    const int j = (int)(pe / 9), e = (int)(pe % 9);
+    const int j = j0 + (int)(pe / 9), e = (int)(pe % 9);
     using A = typename Store<T>::A;
     cx<A> v;
     if (j < 40) {
@@ -479,13 +481,14 @@ cudaError_t launch_brillouin_w80(int prec, const Geom& g, const void* links, voi
         R.d[r][2] = (signed char)((c / 9) % 3 - 1);
         R.d[r][3] = (signed char)((c / 27) % 3 - 1);
     }
-    const long n = g.vol * 80L * 9;
+    const int j0 = links == out ? 40 : 0;
+    const long n = g.vol * (80L - j0) * 9;
     const unsigned nb = (unsigned)((n + 255) / 256);
     switch (prec) {
-    case P_F64: k_brillouin_w80<double><<<nb, 256, 0, st>>>(g, R, n, links, out); break;
-    case P_F32: k_brillouin_w80<float><<<nb, 256, 0, st>>>(g, R, n, links, out); break;
-    case P_BF16: k_brillouin_w80<__nv_bfloat16><<<nb, 256, 0, st>>>(g, R, n, links, out); break;
-    case P_F16: k_brillouin_w80<__half><<<nb, 256, 0, st>>>(g, R, n, links, out); break;
+    case P_F64: k_brillouin_w80<double><<<nb, 256, 0, st>>>(g, R, j0, n, links, out); break;
+    case P_F32: k_brillouin_w80<float><<<nb, 256, 0, st>>>(g, R, j0, n, links, out); break;
+    case P_BF16: k_brillouin_w80<__nv_bfloat16><<<nb, 256, 0, st>>>(g, R, j0, n, links, out); break;
+    case P_F16: k_brillouin_w80<__half><<<nb, 256, 0, st>>>(g, R, j0, n, links, out); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -334,7 +334,7 @@ static dirac_status apply_inner(dirac_handle* h, SolverWS* w, bool dag, void* ou
         if (!w->split)
             return h->run_apply(dag, out, in, w->W, h->diag, h->links, w->prec, c0, diag_v, 0, 0,
                                 diag_v ? w->diag_vf : nullptr);
-        c0.fmt = 0;   // the FP32 W copy of the split solve holds the 40 stored directions
+        // the FP32 W copy of the split solve holds all 80 directions (format 1)
         // split Brillouin fields: t(F32) = D p(16), s(16) = D^+ r(F32) with FP32 W
         const void* L32 = nullptr;
         dirac_status st;
