@@ -154,20 +154,24 @@ cudaError_t upload_brillouin_table(cudaStream_t st)
     return e;
 }
 
-// double-float residual sweep (dirac_df.cuh): one thread per (site, right-hand side)
-__global__ void __launch_bounds__(128) k_brillouin_df(ApplyArgs a)
+// double-float residual sweep (dirac_df.cuh): one thread per (site, right-hand
+// side), the DF_COLS right-hand sides of a block sharing its W through L1
+__global__ void __launch_bounds__(DF_SITES * DF_COLS) k_brillouin_df(ApplyArgs a)
 {
-    const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.nsites) return;
-    brillouin_site<f64df, 1, false>(a, slab_site(a, p), (int)blockIdx.y, c_bri_dirs);
+    const int ncb = (a.Nv + DF_COLS - 1) / DF_COLS;
+    const long b = blockIdx.x;
+    const int v = (int)(b % ncb) * DF_COLS + threadIdx.y;
+    const long p = (b / ncb) * DF_SITES + threadIdx.x;
+    if (p >= a.nsites || v >= a.Nv) return;
+    brillouin_site<f64df, 1, false>(a, slab_site(a, p), v, c_bri_dirs);
 }
 
 cudaError_t launch_brillouin_df(const ApplyArgs& a, cudaStream_t st)
 {
     cudaError_t e = upload_brillouin_table(st);
     if (e != cudaSuccess) return e;
-    const dim3 grid((unsigned)((a.nsites + 127) / 128), (unsigned)a.Nv);
-    k_brillouin_df<<<grid, 128, 0, st>>>(a);
+    const long nb = ((a.nsites + DF_SITES - 1) / DF_SITES) * (long)((a.Nv + DF_COLS - 1) / DF_COLS);
+    k_brillouin_df<<<(unsigned)nb, dim3(DF_SITES, DF_COLS), 0, st>>>(a);
     return cudaGetLastError();
 }
 

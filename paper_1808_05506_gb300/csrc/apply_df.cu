@@ -4,24 +4,30 @@
 
 namespace dirac {
 
-// one thread per (site, right-hand side): blockIdx.y is the right-hand side
+// one thread per (site, right-hand side); blockDim = (DF_SITES, DF_COLS): the
+// DF_COLS right-hand sides of a block (one warp each) read the same links, so
+// each link comes from L2 once per block and from L1 for the other warps
 template <int OP>
-__global__ void __launch_bounds__(128) k_apply_df(ApplyArgs a)
+__global__ void __launch_bounds__(DF_SITES * DF_COLS) k_apply_df(ApplyArgs a)
 {
-    const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.nsites) return;
+    const int ncb = (a.Nv + DF_COLS - 1) / DF_COLS;
+    const long b = blockIdx.x;
+    const int v = (int)(b % ncb) * DF_COLS + threadIdx.y;
+    const long p = (b / ncb) * DF_SITES + threadIdx.x;
+    if (p >= a.nsites || v >= a.Nv) return;
     const long s = slab_site(a, p);
-    if constexpr (OP == OP_WILSON) wilson_site<f64df, 1, false, 0>(a, s, (int)blockIdx.y);
-    else staggered_site<f64df, 1, false, 0>(a, s, (int)blockIdx.y);
+    if constexpr (OP == OP_WILSON) wilson_site<f64df, 1, false, 0>(a, s, v);
+    else staggered_site<f64df, 1, false, 0>(a, s, v);
 }
 
 cudaError_t launch_apply_df(int op, const ApplyArgs& a, cudaStream_t st)
 {
     if (a.nsites == 0 || a.Nv == 0) return cudaSuccess;
     if (op == OP_BRILLOUIN) return launch_brillouin_df(a, st);
-    const dim3 grid((unsigned)((a.nsites + 127) / 128), (unsigned)a.Nv);
-    if (op == OP_WILSON) k_apply_df<OP_WILSON><<<grid, 128, 0, st>>>(a);
-    else if (op == OP_STAGGERED) k_apply_df<OP_STAGGERED><<<grid, 128, 0, st>>>(a);
+    const long nb = ((a.nsites + DF_SITES - 1) / DF_SITES) * (long)((a.Nv + DF_COLS - 1) / DF_COLS);
+    const dim3 block(DF_SITES, DF_COLS);
+    if (op == OP_WILSON) k_apply_df<OP_WILSON><<<(unsigned)nb, block, 0, st>>>(a);
+    else if (op == OP_STAGGERED) k_apply_df<OP_STAGGERED><<<(unsigned)nb, block, 0, st>>>(a);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

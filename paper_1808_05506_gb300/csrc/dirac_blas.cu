@@ -422,6 +422,12 @@ cudaError_t blas_norm2(int prec, size_t n, int Nv, const void* x, double* part, 
     return cudaGetLastError();
 }
 
+cudaError_t blas_reduce_partials(const double* part, long nparts, int Nv, double* out, cudaStream_t st)
+{
+    k_reduce_partials<<<Nv, BT, 0, st>>>(part, (int)nparts, out, 0);
+    return cudaGetLastError();
+}
+
 cudaError_t blas_dot(int prec, size_t n, int Nv, const void* x, const void* y, double* part,
                      double* out_re, double* out_im, cudaStream_t st)
 {

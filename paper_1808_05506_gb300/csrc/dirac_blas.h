@@ -22,6 +22,8 @@ cudaError_t blas_cgls_step(int prec, size_t n, int Nv, const double* alpha, void
 // split inner solve); n = complex numbers per right-hand side
 cudaError_t blas_cgls_step_split(int prec16, size_t n, int Nv, const double* alpha, void* e, const void* p, void* r,
                                  const void* t, double* part, double* rr, cudaStream_t st);
+// out_v = sum of the nparts partials part[v * nparts + i] (fixed order)
+cudaError_t blas_reduce_partials(const double* part, long nparts, int Nv, double* out, cudaStream_t st);
 // p = s + beta_v p
 cudaError_t blas_xpay(int prec, size_t n, int Nv, const void* s, const double* beta, void* p, cudaStream_t st);
 // dst = scale_v src within one storage type (scale NULL: 1); nrm2_v = |dst_v|^2

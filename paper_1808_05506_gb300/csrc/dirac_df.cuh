@@ -148,6 +148,11 @@ template <> DEV_INLINE void st_one<f64df>(void* base, size_t i, cx<dfl> c)
 }
 template <> DEV_INLINE void st_vec<f64df>(void* base, size_t i, const cx<dfl>* c) { st_one<f64df>(base, i, c[0]); }
 
+// launch shape of the double-float sweeps: blocks of DF_SITES sites x DF_COLS
+// right-hand sides (one warp per right-hand side)
+constexpr int DF_SITES = 32;
+constexpr int DF_COLS = 4;
+
 // the double-float residual sweep: out = D in (no adjoint), direct variant,
 // one right-hand side per thread; in, out and links in f64df storage
 cudaError_t launch_apply_df(int op, const ApplyArgs& a, cudaStream_t st);

@@ -40,7 +40,22 @@ struct EoArgs {
     const void* coef;  // arithmetic type: alpha[Nv] then beta[Nv]
     int tc;            // site order of the half lattice (site_of)
     FDiv fdc, fdt;
+    // optional |out_v|^2 (of the stored values), fused into the sweep: one FP64
+    // partial per warp and column, npart[v * nwarp + warp] (null: not formed);
+    // nwarp = eo_norm_slots(vh, block), set by the launcher
+    double* npart = nullptr;
+    long nwarp = 0;
 };
+
+// partials per column of the fused norm of a sweep with `block` half sites per block
+inline long eo_norm_slots(long vh, int block) { return ((vh + block - 1) / block) * (block / 32); }
+
+// a value as the storage type T holds it (16-bit types round)
+template <typename T> DEV_INLINE cx<typename Store<T>::A> stored_value(cx<typename Store<T>::A> c)
+{
+    if constexpr (sizeof(T) == 2) return unpack2(pack2(c, (T*)nullptr), (T*)nullptr);
+    else return c;
+}
 
 // site of parity a.par with half-site index h
 HD long eo_site(const EoArgs& a, long h)
@@ -78,8 +93,9 @@ DEV_INLINE void eo_wilson_hop(const EoArgs& a, long hn, long lsite, int v0, cx<t
 // out = alpha in2 + beta (H in) at one site; H = -1/2 sum_mu [(1 - gamma_mu)
 // V_mu(x) psi(x + mu) + (1 + gamma_mu) V_mu(x - mu)^+ psi(x - mu)], the
 // adjoint swapping the two projectors.  R divides Nv.
+// q[r] = |out|^2 at this site of column v0 + r (when a.npart is set)
 template <typename TL, typename TI, typename TI2, typename TO, int R, bool DAG>
-DEV_INLINE void wilson_eo_site(const EoArgs& a, long h, int group)
+DEV_INLINE void wilson_eo_site(const EoArgs& a, long h, int group, typename Store<TI>::A (&q)[R])
 {
     using A = typename Store<TI>::A;
     const long s = eo_site(a, h);
@@ -120,13 +136,22 @@ DEV_INLINE void wilson_eo_site(const EoArgs& a, long h, int group)
             for (int i = 0; i < 12; ++i) o[i] = cx<A>{be * acc[r][i].re, be * acc[r][i].im};
         }
         store_spinor<TO, 12>(a.out, a.vh, v, h, o);
+        if (a.npart) {
+            A n2 = A(0);
+#pragma unroll
+            for (int i = 0; i < 12; ++i) {
+                const cx<A> c = stored_value<TO>(o[i]);
+                n2 = fma(c.re, c.re, fma(c.im, c.im, n2));
+            }
+            q[r] = n2;
+        }
     }
 }
 
 // out = alpha in2 + beta (H in) at one site; H = 1/2 sum_mu eta_mu(x)
 // [V_mu(x) psi(x + mu) - V_mu(x - mu)^+ psi(x - mu)], H^+ = -H.  R divides Nv.
 template <typename TL, typename TI, typename TI2, typename TO, int R, bool DAG>
-DEV_INLINE void staggered_eo_site(const EoArgs& a, long h, int group)
+DEV_INLINE void staggered_eo_site(const EoArgs& a, long h, int group, typename Store<TI>::A (&q)[R])
 {
     using A = typename Store<TI>::A;
     const long s = eo_site(a, h);
@@ -181,23 +206,52 @@ DEV_INLINE void staggered_eo_site(const EoArgs& a, long h, int group)
             for (int c = 0; c < 3; ++c) o[c] = cx<A>{be * acc[r][c].re, be * acc[r][c].im};
         }
         store_spinor<TO, 3>(a.out, a.vh, v, h, o);
+        if (a.npart) {
+            A n2 = A(0);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const cx<A> z = stored_value<TO>(o[c]);
+                n2 = fma(z.re, z.re, fma(z.im, z.im, n2));
+            }
+            q[r] = n2;
+        }
     }
 }
 
 // blockDim = (half sites, gy groups); block b covers a run of half sites (in
 // the site order of the half lattice) and gy groups of R right-hand sides
 
+// With a.npart the norms of the outputs are summed per warp (the 32 lanes of
+// a warp share threadIdx.y, since blockDim.x >= 32): each site's |out_v|^2 in
+// the arithmetic type (at most 24 squares), the warp's sum in FP64, one
+// partial per warp and column; a fixed-order second pass adds the partials.
 template <int OP, typename TL, typename TI, typename TI2, typename TO, int R, bool DAG>
 __global__ void __launch_bounds__(192, 2) k_eo(EoArgs a, int ngroups, int gy)
 {
+    using A = typename Store<TI>::A;
     const int nchunks = (ngroups + gy - 1) / gy;
     const long b = blockIdx.x;
     const int group = (int)(b % nchunks) * gy + threadIdx.y;
+    if (group >= ngroups) return;   // a whole warp
     const long p = (b / nchunks) * blockDim.x + threadIdx.x;
-    if (p >= a.vh || group >= ngroups) return;
-    const long h = site_of(a.gh, p, a.tc, a.g.L[3], a.fdc, a.fdt);
-    if constexpr (OP == OP_WILSON) wilson_eo_site<TL, TI, TI2, TO, R, DAG>(a, h, group);
-    else staggered_eo_site<TL, TI, TI2, TO, R, DAG>(a, h, group);
+    A q[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) q[r] = A(0);
+    if (p < a.vh) {
+        const long h = site_of(a.gh, p, a.tc, a.g.L[3], a.fdc, a.fdt);
+        if constexpr (OP == OP_WILSON) wilson_eo_site<TL, TI, TI2, TO, R, DAG>(a, h, group, q);
+        else staggered_eo_site<TL, TI, TI2, TO, R, DAG>(a, h, group, q);
+    }
+    if (a.npart) {
+        const long wi = (b / nchunks) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            double d = (double)q[r];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            if ((threadIdx.x & 31) == 0) a.npart[(size_t)(group * R + r) * a.nwarp + wi] = d;
+        }
+    }
 }
 
 // block: half sites per block (32, 64 or 128), times gy = min(192 / block,
@@ -209,7 +263,9 @@ cudaError_t eo_go_typed(const EoArgs& a, int block, cudaStream_t st)
     const int ngroups = a.Nv / R;
     const int gy = groups_per_block(block, ngroups);
     const long nb = ((a.vh + block - 1) / block) * (long)((ngroups + gy - 1) / gy);
-    k_eo<OP, TL, TI, TI2, TO, R, DAG><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+    EoArgs b = a;
+    b.nwarp = eo_norm_slots(a.vh, block);
+    k_eo<OP, TL, TI, TI2, TO, R, DAG><<<(unsigned)nb, dim3(block, gy), 0, st>>>(b, ngroups, gy);
     return cudaGetLastError();
 }
 

@@ -146,6 +146,7 @@ struct SolverWS {
     void* xdf = nullptr;                                      // x in double-float storage (lazy)
     size_t n = 0;                                             // complex numbers per rhs of the inner fields
     double* part = nullptr;                                   // reduction partials
+    double* npart = nullptr;                                  // eo: fused-norm partials (W x eo_norm_slots)
     double* scal = nullptr;                                   // per-rhs scalar slots
     int* iflags = nullptr;                                    // active[W], breakdown, nactive
     double *bb, *rr64, *scale, *coef, *rr0, *rr, *gamma, *gnew, *delta, *alpha, *beta, *diag_v, *dim, *itol2;
@@ -178,6 +179,8 @@ void dirac_handle::free_solver_workspace()
                      &w->tmp2};
     for (void** q : ptrs) release(*q);
     void* pp = w->part;
+    release(pp);
+    pp = w->npart;
     release(pp);
     pp = w->scal;
     release(pp);
@@ -232,6 +235,13 @@ static dirac_status ensure_solver_ws(dirac_handle* h, bool eo, bool split, Solve
     void* pp = nullptr;
     if ((st = h->alloc(&pp, 2 * blas_partials(nfull, h->Nv) * sizeof(double), "solver partials"))) return st;
     w->part = (double*)pp;
+    if (eo) {
+        // one partial per warp and column for every launch shape of the even-odd sweeps (32..128 half sites)
+        const long vh = h->g.vol / 2;
+        if ((st = h->alloc(&pp, (size_t)h->Nv * (size_t)((vh + 31) / 32 + 4) * sizeof(double), "solver norm partials")))
+            return st;
+        w->npart = (double*)pp;
+    }
     const int nslots = 13;
     const size_t nscal = (size_t)nslots * h->Nv + 1 + ((size_t)h->Nv + 1) / 2 + (size_t)EO_NSETS * 2 * h->Nv;
     if ((st = h->alloc(&pp, nscal * sizeof(double), "solver scalars"))) return st;
@@ -297,70 +307,97 @@ static LaunchCfg eo_cfg_of(const dirac_handle* h, const SolverWS* w)
 // one even-odd sweep with every field in precision w->pa (the links of that
 // precision: the handle's, or the FP32 copy of the split solve)
 static dirac_status eo_sweep(dirac_handle* h, SolverWS* w, bool dag, int par, void* out, const void* in,
-                             const void* in2, int set)
+                             const void* in2, int set, double* nrm = nullptr)
 {
     const LaunchCfg c = eo_cfg_of(h, w);
     const void* L = h->links;
     dirac_status st;
     if (w->split && (st = h->ensure_links32(&L))) return st;
-    const EoArgs a = make_eo_args(h->g, w->W, par, in, in2, out, L, eo_coef(w, set), c.order);
-    return h->cuda(launch_eo(h->op, w->pa, dag, a, c, h->stream), "solve: even-odd sweep");
+    EoArgs a = make_eo_args(h->g, w->W, par, in, in2, out, L, eo_coef(w, set), c.order);
+    if (nrm) a.npart = w->npart;
+    if ((st = h->cuda(launch_eo(h->op, w->pa, dag, a, c, h->stream), "solve: even-odd sweep"))) return st;
+    if (!nrm) return DIRAC_OK;
+    return h->cuda(blas_reduce_partials(w->npart, eo_norm_slots(a.vh, c.block), w->W, nrm, h->stream),
+                   "solve: fused norm");
 }
 
-// one sweep of the split solve (EO_SPLIT_*)
+// one sweep of the split solve (EO_SPLIT_*); nrm: |out_v|^2 fused into the sweep
 static dirac_status eo_split_sweep(dirac_handle* h, SolverWS* w, int kind, int par, void* out, const void* in,
-                                   const void* in2, int set)
+                                   const void* in2, int set, double* nrm = nullptr)
 {
     const LaunchCfg c = eo_cfg_of(h, w);
     const void* L = nullptr;
     dirac_status st;
     if ((st = h->ensure_links32(&L))) return st;
-    const EoArgs a = make_eo_args(h->g, w->W, par, in, in2, out, L, eo_coef(w, set), c.order);
-    return h->cuda(launch_eo_wilson_split(w->pd, kind, a, c, h->stream), "solve: even-odd sweep");
+    EoArgs a = make_eo_args(h->g, w->W, par, in, in2, out, L, eo_coef(w, set), c.order);
+    if (nrm) a.npart = w->npart;
+    if ((st = h->cuda(launch_eo_wilson_split(w->pd, kind, a, c, h->stream), "solve: even-odd sweep"))) return st;
+    if (!nrm) return DIRAC_OK;
+    return h->cuda(blas_reduce_partials(w->npart, eo_norm_slots(a.vh, c.block), w->W, nrm, h->stream),
+                   "solve: fused norm");
+}
+
+// out = D in (or D^+ in) on the whole lattice (the inner operator without the
+// even-odd split)
+static dirac_status apply_inner_whole(dirac_handle* h, SolverWS* w, bool dag, void* out, const void* in,
+                                      const double* diag_v)
+{
+    // the handle's launch shape and link format (a captured graph is
+    // rebuilt when either changes, and the format-1 links keep their
+    // address across dirac_set_links)
+    LaunchCfg c0 = h->cfg;
+    if (!w->split)
+        return h->run_apply(dag, out, in, w->W, h->diag, h->links, w->prec, c0, diag_v, 0, 0,
+                            diag_v ? w->diag_vf : nullptr);
+    // split Brillouin fields: t(F32) = D p(16), s(16) = D^+ r(F32) with the
+    // FP32 W copy of the split solve, all 80 directions per site (format 1)
+    const void* L32 = nullptr;
+    dirac_status st;
+    if ((st = h->ensure_links32(&L32))) return st;
+    ApplyArgs a = h->args(out, in, w->W, h->diag);
+    a.links = L32;
+    a.diag_v = diag_v;
+    a.diag_vf = diag_v ? w->diag_vf : nullptr;
+    a.tc = (c0.variant == V_DIRECT || c0.variant == V_GROUPS) ? c0.order : 0;
+    if (a.tc > 0) {
+        a.fdc = make_fdiv((uint32_t)(h->g.L[2] * a.tc));
+        a.fdt = make_fdiv((uint32_t)a.tc);
+    }
+    return h->cuda(launch_brillouin_split(w->pd, dag, a, c0, h->stream), "solve: split Brillouin sweep");
+}
+
+// the Schur complement S (or S^+) on the odd half fields: two half sweeps;
+// nrm: |out_v|^2 fused into the second
+static dirac_status apply_inner_eo(dirac_handle* h, SolverWS* w, bool dag, void* out, const void* in, double* nrm)
+{
+    dirac_status st;
+    if (w->split) {
+        if (!dag) {
+            if ((st = eo_split_sweep(h, w, EO_SPLIT_HP, 0, w->tmp, in, nullptr, EO_HOP))) return st;
+            return eo_split_sweep(h, w, EO_SPLIT_SP, 1, out, w->tmp, in, EO_S, nrm);
+        }
+        if ((st = eo_split_sweep(h, w, EO_SPLIT_HR, 0, w->tmp2, in, nullptr, EO_HOP))) return st;
+        return eo_split_sweep(h, w, EO_SPLIT_SR, 1, out, w->tmp2, in, EO_S, nrm);
+    }
+    if ((st = eo_sweep(h, w, dag, 0, w->tmp, in, nullptr, EO_HOP))) return st;   // H_eo in
+    return eo_sweep(h, w, dag, 1, out, w->tmp, in, EO_S, nrm);                    // a in - H_oe (.) / a
 }
 
 // out = A in (or A^+ in), A the operator of the inner solve: D on the whole
 // lattice, or the Schur complement S on the odd half fields.  Split fields:
 // A p reads p in 16 bits and writes t in FP32; A^+ r reads r in FP32 and
-// writes s in 16 bits.
+// writes s in 16 bits.  nrm (optional): |out_v|^2 per right-hand side, fused
+// into the second half sweep on the even-odd path, a separate pass on the
+// whole lattice.
 static dirac_status apply_inner(dirac_handle* h, SolverWS* w, bool dag, void* out, const void* in,
-                                const double* diag_v)
+                                const double* diag_v, double* nrm = nullptr)
 {
     if (!w->eo) {
-        // the handle's launch shape and link format (a captured graph is
-        // rebuilt when either changes, and the format-1 links keep their
-        // address across dirac_set_links)
-        LaunchCfg c0 = h->cfg;
-        if (!w->split)
-            return h->run_apply(dag, out, in, w->W, h->diag, h->links, w->prec, c0, diag_v, 0, 0,
-                                diag_v ? w->diag_vf : nullptr);
-        // the FP32 W copy of the split solve holds all 80 directions (format 1)
-        // split Brillouin fields: t(F32) = D p(16), s(16) = D^+ r(F32) with FP32 W
-        const void* L32 = nullptr;
-        dirac_status st;
-        if ((st = h->ensure_links32(&L32))) return st;
-        ApplyArgs a = h->args(out, in, w->W, h->diag);
-        a.links = L32;
-        a.diag_v = diag_v;
-        a.diag_vf = diag_v ? w->diag_vf : nullptr;
-        a.tc = (c0.variant == V_DIRECT || c0.variant == V_GROUPS) ? c0.order : 0;
-        if (a.tc > 0) {
-            a.fdc = make_fdiv((uint32_t)(h->g.L[2] * a.tc));
-            a.fdt = make_fdiv((uint32_t)a.tc);
-        }
-        return h->cuda(launch_brillouin_split(w->pd, dag, a, c0, h->stream), "solve: split Brillouin sweep");
+        dirac_status st = apply_inner_whole(h, w, dag, out, in, diag_v);
+        if (st || !nrm) return st;
+        return h->cuda(blas_norm2(dag ? w->pd : w->pa, w->n, w->W, out, w->part, nrm, h->stream), "solve: norm");
     }
-    dirac_status st;
-    if (w->split) {
-        if (!dag) {
-            if ((st = eo_split_sweep(h, w, EO_SPLIT_HP, 0, w->tmp, in, nullptr, EO_HOP))) return st;
-            return eo_split_sweep(h, w, EO_SPLIT_SP, 1, out, w->tmp, in, EO_S);
-        }
-        if ((st = eo_split_sweep(h, w, EO_SPLIT_HR, 0, w->tmp2, in, nullptr, EO_HOP))) return st;
-        return eo_split_sweep(h, w, EO_SPLIT_SR, 1, out, w->tmp2, in, EO_S);
-    }
-    if ((st = eo_sweep(h, w, dag, 0, w->tmp, in, nullptr, EO_HOP))) return st;   // H_eo in
-    return eo_sweep(h, w, dag, 1, out, w->tmp, in, EO_S);                         // a in - H_oe (.) / a
+    return apply_inner_eo(h, w, dag, out, in, nrm);
 }
 
 // one inner iteration over all W right-hand sides (kernel launches only, so it
@@ -375,7 +412,7 @@ static dirac_status enqueue_iteration(dirac_handle* h, SolverWS* w, const double
     int* nactive = w->iflags + W + 1;
     const unsigned sb = (unsigned)((W + 127) / 128);
     dirac_status st;
-    if ((st = apply_inner(h, w, false, w->t, w->p, diag_v))) return st;
+    if ((st = apply_inner(h, w, false, w->t, w->p, diag_v, w->cg ? nullptr : w->delta))) return st;
     if (w->cg) {
         // t = A p, delta = <p, t>, e += alpha p, r -= alpha t, gamma' = |r|^2, p = r + beta p
         if ((st = h->cuda(blas_dot(P, n, W, w->p, w->t, w->part, w->delta, w->dim, S), "solve: <p, t>")))
@@ -388,15 +425,14 @@ static dirac_status enqueue_iteration(dirac_handle* h, SolverWS* w, const double
         if ((st = h->cuda(blas_xpay(P, n, W, w->r, w->beta, w->p, S), "solve: p = r + beta p"))) return st;
     } else {
         // t = A p (pa), delta = |t|^2, e += alpha p, r -= alpha t (pa; p in pd),
-        // s = A^+ r (pd), gamma' = |s|^2, p = s + beta p (pd)
-        if ((st = h->cuda(blas_norm2(w->pa, n, W, w->t, w->part, w->delta, S), "solve: |t|"))) return st;
+        // s = A^+ r (pd), gamma' = |s|^2, p = s + beta p (pd); the norms of t
+        // and s come with the sweeps that write them
         k_cgls_alpha<<<sb, 128, 0, S>>>(W, w->gamma, w->delta, active, w->alpha, breakdown);
         const cudaError_t ce =
             w->split ? blas_cgls_step_split(w->pd, n, W, w->alpha, w->e, w->p, w->r, w->t, w->part, w->rr, S)
                      : blas_cgls_step(P, n, W, w->alpha, w->e, w->p, w->r, w->t, w->part, w->rr, S);
         if ((st = h->cuda(ce, "solve: step"))) return st;
-        if ((st = apply_inner(h, w, true, w->s, w->r, diag_v))) return st;
-        if ((st = h->cuda(blas_norm2(w->pd, n, W, w->s, w->part, w->gnew, S), "solve: |s|"))) return st;
+        if ((st = apply_inner(h, w, true, w->s, w->r, diag_v, w->gnew))) return st;
         k_cgls_beta<<<sb, 128, 0, S>>>(W, w->gnew, w->gamma, active, w->beta);
         if ((st = h->cuda(blas_xpay(w->pd, n, W, w->s, w->beta, w->p, S), "solve: p = s + beta p"))) return st;
     }

@@ -110,12 +110,13 @@ static double eo_vs_whole(int op, const int* L, int Nv, bool dag, int tc, unsign
             if (seen[h] != 1) return 1e30;
         for (long h = 0; h < vh; ++h)
             for (int gi = 0; gi < Nv / R; ++gi) {
+                A q[R];
                 if (op == OP_WILSON) {
-                    if (dag) wilson_eo_site<T, T, T, T, R, true>(e, h, gi);
-                    else wilson_eo_site<T, T, T, T, R, false>(e, h, gi);
+                    if (dag) wilson_eo_site<T, T, T, T, R, true>(e, h, gi, q);
+                    else wilson_eo_site<T, T, T, T, R, false>(e, h, gi, q);
                 } else {
-                    if (dag) staggered_eo_site<T, T, T, T, R, true>(e, h, gi);
-                    else staggered_eo_site<T, T, T, T, R, false>(e, h, gi);
+                    if (dag) staggered_eo_site<T, T, T, T, R, true>(e, h, gi, q);
+                    else staggered_eo_site<T, T, T, T, R, false>(e, h, gi, q);
                 }
             }
     }
@@ -133,8 +134,9 @@ static double eo_vs_whole(int op, const int* L, int Nv, bool dag, int tc, unsign
 
 // ---- 2. split-field sweeps vs the FP32 sweep on the 16-bit values
 template <typename H>
-static double split_vs_uniform(unsigned seed)
+static double split_vs_uniform(unsigned seed, double* norm_err)
 {
+    *norm_err = 0.0;
     const Geom g = make_geom(4, 4, 2, 6);
     const long vh = g.vol / 2;
     const int Nv = 4;
@@ -173,16 +175,28 @@ static double split_vs_uniform(unsigned seed)
         default: m.in = p16.data(); m.in2 = r32.data(); m.out = o16.data(); u.in = p32.data(); u.in2 = r32.data(); break;
         }
         u.out = ref32.data();
+        // the fused norm of the stored output (the sweep only tests npart for null)
+        std::vector<double> flag(1);
+        m.npart = flag.data();
         for (long h = 0; h < vh; ++h)
             for (int gi = 0; gi < Nv / R; ++gi) {
+                float q[R], qu[R];
                 switch (kind) {
-                case EO_SPLIT_HP: wilson_eo_site<float, H, float, float, R, false>(m, h, gi); break;
-                case EO_SPLIT_SP: wilson_eo_site<float, float, H, float, R, false>(m, h, gi); break;
-                case EO_SPLIT_HR: wilson_eo_site<float, float, float, H, R, true>(m, h, gi); break;
-                default: wilson_eo_site<float, H, float, H, R, true>(m, h, gi); break;
+                case EO_SPLIT_HP: wilson_eo_site<float, H, float, float, R, false>(m, h, gi, q); break;
+                case EO_SPLIT_SP: wilson_eo_site<float, float, H, float, R, false>(m, h, gi, q); break;
+                case EO_SPLIT_HR: wilson_eo_site<float, float, float, H, R, true>(m, h, gi, q); break;
+                default: wilson_eo_site<float, H, float, H, R, true>(m, h, gi, q); break;
                 }
-                if (dag) wilson_eo_site<float, float, float, float, R, true>(u, h, gi);
-                else wilson_eo_site<float, float, float, float, R, false>(u, h, gi);
+                if (dag) wilson_eo_site<float, float, float, float, R, true>(u, h, gi, qu);
+                else wilson_eo_site<float, float, float, float, R, false>(u, h, gi, qu);
+                for (int r = 0; r < R; ++r) {
+                    cx<float> o[12];
+                    if (kind < 2) load_spinor<float, 12>(out32.data(), vh, gi * R + r, h, o);
+                    else load_spinor<H, 12>(o16.data(), vh, gi * R + r, h, o);
+                    double n2 = 0.0;
+                    for (int k = 0; k < 12; ++k) n2 += (double)o[k].re * o[k].re + (double)o[k].im * o[k].im;
+                    *norm_err = std::fmax(*norm_err, std::fabs(q[r] - n2) / std::fmax(n2, 1e-30));
+                }
             }
         for (int v = 0; v < Nv; ++v)
             for (long h = 0; h < vh; ++h) {
@@ -298,8 +312,11 @@ int main()
                 expect(eo_vs_whole<double, 12, 1>(OP_WILSON, L, 2, dag, tc, 4) == 0.0, what);
                 expect(eo_vs_whole<double, 3, 2>(OP_STAGGERED, L, 2, dag, tc, 5) == 0.0, what);
             }
-    expect(split_vs_uniform<__nv_bfloat16>(6) == 0.0, "split sweeps (BF16) = FP32 sweep on the BF16 values");
-    expect(split_vs_uniform<__half>(7) == 0.0, "split sweeps (FP16) = FP32 sweep on the FP16 values");
+    double ne16 = 0.0, neh = 0.0;
+    expect(split_vs_uniform<__nv_bfloat16>(6, &ne16) == 0.0, "split sweeps (BF16) = FP32 sweep on the BF16 values");
+    expect(split_vs_uniform<__half>(7, &neh) == 0.0, "split sweeps (FP16) = FP32 sweep on the FP16 values");
+    printf("fused output norms vs FP64 norms of the stored values: %.2e %.2e\n", ne16, neh);
+    expect(ne16 < 1e-6 && neh < 1e-6, "fused |out|^2 per site = the norm of the stored output (FP32 sum of 24 squares)");
     expect(split_step_mapping() == 0, "split CGLS step element mapping");
     const int L1[4] = {4, 4, 4, 4}, L2[4] = {3, 4, 5, 2}, L3[4] = {4, 2, 4, 6}, L4[4] = {4, 4, 2, 4};
     const double dw = df_vs_f64<12>(OP_WILSON, L1, 2, 4.1, 8), dw2 = df_vs_f64<12>(OP_WILSON, L2, 3, 4.17, 9);
