@@ -587,6 +587,8 @@ def main():
     ap.add_argument("--prec", default=None, choices=["f32", "bf16", "f16", "f64"])
     ap.add_argument("--kernel", default=None,
                     help="R,block,variant[,tchunk]: fixed launch shape (and site order) instead of the autotuner")
+    ap.add_argument("--link-format", type=int, default=None, choices=[0, 1],
+                    help="with --kernel: the link format (dirac_set_link_format) instead of the default 0")
     ap.add_argument("--op", default="wilson", choices=["wilson", "staggered", "brillouin"],
                     help="operator of the timed sweep (the default workload is Wilson; the others are for profiling)")
     ap.add_argument("--batched-solve-only", action="store_true",
@@ -648,6 +650,8 @@ def main():
         D.set_kernel_config(*k[:3])
         if len(k) > 3:
             D.set_site_order(k[3])
+        if args.link_format is not None:
+            D.set_link_format(args.link_format)
     else:
         D.autotune()                   # best of the built launch shapes on this GPU
     xin = torch.from_numpy(psi).cuda()
