@@ -155,8 +155,8 @@ DIRAC_API dirac_status dirac_apply(dirac_handle* h, void* out, const void* in, d
  *             overlap, pageable memory works with copies that block the
  *             calling thread; they must not overlap (INVALID_ARG), device
  *             pointers are rejected (INVALID_ARG).
- * Launch shape: the handle's kernel configuration when it is variant 0, 1, 2
- * or 5 (the ones that can sweep a t-slab), else variant 1 with the same R.
+ * Launch shape: the handle's kernel configuration when it is variant 0, 1, 2,
+ * 5 or 6 (the ones that can sweep a t-slab), else variant 1 with the same R.
  * Holds two staging buffers per direction of one slab each (allocated on
  * the first call, kept in the handle) and the handle's apply workspace.
  * Requires dirac_set_links first.  Asynchronous: out is complete when the
@@ -354,8 +354,8 @@ DIRAC_API dirac_status dirac_get_residual_arithmetic(const dirac_handle* h, int*
  *            or 6 for staggered); each link is loaded once per thread and
  *            applied to its R right-hand sides from registers
  *   block    threads per block (variants 0 and 3; a multiple of 32, 32..256;
- *            variant 5: 32..192) or sites per block (variants 1 and 2: 32 or
- *            64, variant 2 also 128)
+ *            variant 5: 32..192) or sites per block (variants 1, 2 and 6: 32
+ *            or 64, variant 2 also 128)
  *   variant  0: the right-hand-side groups of a site run in consecutive blocks;
  *            1: the groups of the same sites share one block, so that each link
  *               comes from L2 once per block and is reused through L1;
@@ -371,13 +371,18 @@ DIRAC_API dirac_status dirac_get_residual_arithmetic(const dirac_handle* h, int*
  *               consecutive sites of the (x, y, z) volume: the x hops are
  *               exchanged between lanes by warp shuffles instead of loaded;
  *               needs Lx to divide 32 and Lx * Ly * Lz divisible by 32;
- *               block / 32 right-hand-side groups share a block.
+ *               block / 32 right-hand-side groups share a block;
+ *            6: (Wilson, FP32/BF16/FP16, R <= 2, same lattice rule as 5)
+ *               variant 1 with the x hops done last by lane exchange: each
+ *               site's own spinor, loaded once, serves the diagonal term and
+ *               both x hops, so two of the nine spinor loads and one of the
+ *               eight link loads per site disappear; 32 or 64 sites per block.
  * UNSUPPORTED for other values. */
 DIRAC_API dirac_status dirac_set_kernel_config(dirac_handle* h, int R, int block, int variant);
 
 DIRAC_API dirac_status dirac_get_kernel_config(const dirac_handle* h, int* R, int* block, int* variant);
 
-/* Site order of the sweeps of variants 0 and 1 (no counterpart in the paper,
+/* Site order of the sweeps of variants 0, 1 and 6 (no counterpart in the paper,
  * whose KNL code walks the lattice in its storage order): the order in which
  * consecutive thread blocks take the sites.
  *   tchunk = 0    lexicographic (x fastest, then y, z, t);
@@ -406,9 +411,10 @@ DIRAC_API dirac_status dirac_get_site_order(const dirac_handle* h, int* tchunk);
  *          stays.  Brillouin (every precision) reads all 80 W stored at x
  *          (W_{-dir}(x) precomputed, copied without rounding): twice the W
  *          bytes, local reads only.
- * Format 1 is read by the launch variants that support it (Wilson and
- * staggered: variant 1; Brillouin: variants 0 and 1); other variants, the
- * solvers' inner sweeps and the even-odd sweeps read the plain links.  The
+ * Format 1 is read by the launch variants that support it (Wilson: variants
+ * 1 and 6; staggered: variant 1; Brillouin: variants 0 and 1) in the apply
+ * and in the whole-lattice inner sweeps of the solvers; other variants and
+ * the even-odd sweeps read the plain links.  The
  * format-1 copy (Wilson/staggered: 4 x 6 complex per site; Brillouin: 80 x 9)
  * is held by the handle and rebuilt by dirac_set_links; links that fail the
  * check there switch the handle back to format 0 (dirac_get_link_format

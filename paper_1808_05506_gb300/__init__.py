@@ -499,18 +499,18 @@ class Dirac:
         return R.value, B.value, Pp.value
 
 
-VARIANTS = {"staggered": (0, 1), "wilson": (0, 1, 2, 3, 5), "brillouin": (0, 1)}
+VARIANTS = {"staggered": (0, 1), "wilson": (0, 1, 2, 3, 5, 6), "brillouin": (0, 1)}
 
 
 def config_supported(op: str, prec: str, R: int, block: int, variant: int, L=None) -> bool:
     """The rule dirac_set_kernel_config applies (without a handle); L = (Nx, Ny, Nz, Nt)
-    is needed for variant 5."""
+    is needed for variants 5 and 6."""
     if block < 32 or block > 256 or block % 32:
         return False
     if variant == 4:
         return False   # not used
-    if variant == 5:
-        if op != "wilson" or prec == "f64" or not 1 <= R <= 2 or block > 192 or L is None:
+    if variant in (5, 6):
+        if op != "wilson" or prec == "f64" or not 1 <= R <= 2 or block > (192 if variant == 5 else 64) or L is None:
             return False
         return 32 % L[0] == 0 and (L[0] * L[1] * L[2]) % 32 == 0
     if op == "staggered" and R not in (1, 2, 4, 6):

@@ -81,6 +81,19 @@ __global__ void __launch_bounds__(192, 2) k_wilson_groups(ApplyArgs a, int ngrou
     wilson_site<T, R, DAG, MODE, LF>(a, slab_site(a, p), group);
 }
 
+// V_XLAST: V_GROUPS with the x hops last, by lane exchange (wilson_site_xlast);
+// the host checked that every warp holds whole x-rows
+template <typename T, int R, bool DAG, int MODE, int LF>
+__global__ void __launch_bounds__(192, 2) k_wilson_xlast(ApplyArgs a, int ngroups, int gy)
+{
+    const int nchunks = (ngroups + gy - 1) / gy;
+    const long b = blockIdx.x;
+    const int group = (int)(b % nchunks) * gy + threadIdx.y;
+    const long p = (b / nchunks) * blockDim.x + threadIdx.x;
+    if (p >= a.nsites || group >= ngroups) return;   // whole warps
+    wilson_site_xlast<T, R, DAG, MODE, LF>(a, slab_site(a, p), threadIdx.x & 31, group);
+}
+
 template <typename T, int R>
 cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
 {
@@ -110,6 +123,26 @@ cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
         return cudaGetLastError();
     }
     if constexpr (R <= 2) {
+    if (c.variant == V_XLAST) {
+        const int gy = groups_per_block(block, ngroups);
+        const long nb = ((a.nsites + block - 1) / block) * (long)((ngroups + gy - 1) / gy);
+        const bool dv = a.diag_vf != nullptr;
+        const int mode = (a.Nv % R != 0 || (a.diag_v != nullptr && !dv)) ? 0 : (dv ? 2 : 1);
+        auto launch_lf = [&](auto m, auto lf) {
+            constexpr int M = decltype(m)::value;
+            constexpr int LF = decltype(lf)::value;
+            if (dag) k_wilson_xlast<T, R, true, M, LF><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+            else k_wilson_xlast<T, R, false, M, LF><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+        };
+        auto launch = [&](auto m) {
+            if (c.fmt == 1) launch_lf(m, std::integral_constant<int, 1>{});
+            else launch_lf(m, std::integral_constant<int, 0>{});
+        };
+        if (mode == 1) launch(std::integral_constant<int, 1>{});
+        else if (mode == 2) launch(std::integral_constant<int, 2>{});
+        else launch(std::integral_constant<int, 0>{});
+        return cudaGetLastError();
+    }
     if (c.variant == V_XROW) {
         // the host checked 32 % Lx == 0 and vol3 % 32 == 0: every warp is full
         const int gy = min(c.block / 32, ngroups);

@@ -147,7 +147,7 @@ dirac_status dirac_handle::run_apply(bool dagger, void* out, const void* in, int
         a.nt = nt;
         a.nsites = (long)nt * g.stride[3];
     }
-    a.tc = (c.variant == V_DIRECT || c.variant == V_GROUPS) ? c.order : 0;
+    a.tc = (c.variant == V_DIRECT || c.variant == V_GROUPS || c.variant == V_XLAST) ? c.order : 0;
     if (a.tc > 0) {
         a.fdc = make_fdiv((uint32_t)(g.L[2] * a.tc));
         a.fdt = make_fdiv((uint32_t)a.tc);
@@ -698,6 +698,9 @@ bool apply_config_supported(int op, int prec, int R, int block, int variant, con
     if (block < 32 || block > 256 || block % 32) return false;
     if (variant == V_XROW)
         return op == OP_WILSON && prec != P_F64 && R >= 1 && R <= 2 && block <= 192 && 32 % g.L[0] == 0 &&
+               g.stride[3] % 32 == 0;
+    if (variant == V_XLAST)
+        return op == OP_WILSON && prec != P_F64 && R >= 1 && R <= 2 && block <= 64 && 32 % g.L[0] == 0 &&
                g.stride[3] % 32 == 0;
     const bool Rok = (op == OP_STAGGERED) ? (R == 1 || R == 2 || R == 4 || R == 6) : (R >= 1 && R <= 4);
     if (!Rok) return false;

@@ -29,10 +29,13 @@ enum Variant {
                     // 8 consecutive t-slices with the t hops carried in registers
     V_PIPE3 = 3,    // Wilson: V_DIRECT with a 3-stage cp.async pipeline in shared memory
     // 4 is not used (a variant with bulk-copied tiles, retired with the blocked layout)
-    V_XROW = 5      // Wilson (FP32/BF16/FP16), Lx dividing 32: a warp holds 32 consecutive sites
+    V_XROW = 5,     // Wilson (FP32/BF16/FP16), Lx dividing 32: a warp holds 32 consecutive sites
                     // of the (x, y, z) volume (whole x-rows) and walks up to 8 t-slices; x hops
                     // by warp shuffles, t hops carried in registers; `block` = threads
                     // (block / 32 right-hand-side groups per block)
+    V_XLAST = 6     // Wilson (FP32/BF16/FP16, R <= 2), Lx dividing 32 and 32 dividing Lx Ly Lz:
+                    // V_GROUPS with the x hops last, by lane exchange of the site's own spinor
+                    // (wilson_site_xlast); `block` = sites per block (32 or 64)
 };
 
 struct LaunchCfg {
@@ -46,11 +49,12 @@ struct LaunchCfg {
 };
 
 // whether a launch variant reads link format 1: Wilson and staggered
-// V_GROUPS with FP32 / 16-bit storage, Brillouin V_DIRECT and V_GROUPS
+// V_GROUPS (Wilson also V_XLAST) with FP32 / 16-bit storage, Brillouin
+// V_DIRECT and V_GROUPS
 inline bool link_format_supported(int op, int prec, int variant)
 {
     if (op == OP_BRILLOUIN) return variant == V_DIRECT || variant == V_GROUPS;
-    return prec != P_F64 && variant == V_GROUPS;
+    return prec != P_F64 && (variant == V_GROUPS || (op == OP_WILSON && variant == V_XLAST));
 }
 
 // threads per block of V_GROUPS: block sites x gy groups with block * gy <= 192

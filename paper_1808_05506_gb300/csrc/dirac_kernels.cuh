@@ -179,6 +179,76 @@ DEV_INLINE void wilson_site(const ApplyArgs& a, long s, int group)
     }
 }
 
+// ---------------------------------------------------------------- Wilson, x hops last
+// wilson_site with the 32 lanes of a warp on whole x-rows (Lx divides 32 and
+// every warp starts at a multiple of 32 sites of its plane): the y, z and t
+// hops load their spinors as usual; then, per right-hand side, the site's own
+// spinor -- loaded once -- serves the diagonal term and both x hops.  Lane x
+// forms (1 + SF gamma_1) psi(x), the forward projection, and sends it to
+// lane x - 1; it forms U_x(x)^+ (1 + SB gamma_1) psi(x) with its own link, the
+// backward hop of site x + 1, and sends it to lane x + 1.  Two of the nine
+// spinor loads per site and one of the eight link loads disappear.  Every
+// lane of the warp must call this with the same group.
+// lane: the thread's lane in its warp; the warp's 32 consecutive work items
+// start at a multiple of 32, so lane = x mod Lx and the row occupies the lanes
+// lane - x .. lane - x + Lx - 1
+template <typename T, int R, bool DAG, int MODE = 0, int LF = 0>
+DEV_INLINE void wilson_site_xlast(const ApplyArgs& a, long s, int lane, int group)
+{
+    constexpr bool FULL = MODE != 0;
+    using A = typename Store<T>::A;
+    long fwd[4], bwd[4];
+    int x[4];
+    site_offsets(a.g, s, fwd, bwd, x);
+    const int Lx = a.g.L[0];
+    const int lane_f = lane - x[0] + (x[0] + 1 == Lx ? 0 : x[0] + 1);   // site x + 1
+    const int lane_b = lane - x[0] + (x[0] == 0 ? Lx - 1 : x[0] - 1);   // site x - 1
+    const int v0 = group * R;
+    cx<A> acc[R][12];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int i = 0; i < 12; ++i) acc[r][i] = cx<A>{A(0), A(0)};
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int SB = -SF;
+    wilson_hop<T, R, 1, SF, false, false, FULL, LF>(a, s + fwd[1], s, v0, acc);
+    wilson_hop<T, R, 1, SB, true, false, FULL, LF>(a, s + bwd[1], s + bwd[1], v0, acc);
+    wilson_hop<T, R, 2, SF, false, false, FULL, LF>(a, s + fwd[2], s, v0, acc);
+    wilson_hop<T, R, 2, SB, true, false, FULL, LF>(a, s + bwd[2], s + bwd[2], v0, acc);
+    wilson_hop<T, R, 3, SF, false, false, FULL, LF>(a, s + fwd[3], s, v0, acc);
+    wilson_hop<T, R, 3, SB, true, false, FULL, LF>(a, s + bwd[3], s + bwd[3], v0, acc);
+    cx<A> U[9];
+    load_link_f<T, false, LF>(a.links, a.g.vol, 0, s, U);
+    const A mh = (A)(-0.5);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int v = FULL ? v0 + r : min(v0 + r, a.Nv - 1);
+        cx<A> pc[12], h[6], w[6], q[6];
+        load_spinor<T, 12>(a.in, a.g.vol, v, s, pc);
+        wilson_project<0, SF>(pc, h);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) q[i] = shfl_cx(h[i], lane_f);
+        mat_vec(U, q, w);
+        mat_vec(U, q + 3, w + 3);
+        wilson_reconstruct<0, SF>(w, acc[r]);
+        wilson_project<0, SB>(pc, h);
+        mat_dag_vec(U, h, w);
+        mat_dag_vec(U, h + 3, w + 3);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) q[i] = shfl_cx(w[i], lane_b);
+        wilson_reconstruct<0, SB>(q, acc[r]);
+        const A dg = diag_mode<A>(a, v, MODE);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            cx<A> o;
+            o.re = fma(mh, acc[r][i].re, dg * pc[i].re);
+            o.im = fma(mh, acc[r][i].im, dg * pc[i].im);
+            pc[i] = o;
+        }
+        if (FULL || v0 + r < a.Nv) store_spinor<T, 12>(a.out, a.g.vol, v0 + r, s, pc);
+    }
+}
+
 // ---------------------------------------------------------------- Wilson, t-march
 // One thread owns the site column (x, y, z) for the slices t0 <= t < t1 and
 // one group of R right-hand sides.  Along t each spinor and each t-link is

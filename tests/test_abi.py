@@ -200,6 +200,14 @@ def test_config_rule(dg):
     assert not dg.config_supported("wilson", "f64", 1, 64, 5, (32, 32, 32, 32))
     assert not dg.config_supported("wilson", "f32", 1, 256, 5, (32, 32, 32, 32))
     assert not dg.config_supported("staggered", "f32", 1, 64, 5, (32, 32, 32, 32))
+    # x hops last: the same lattice rule, 32 or 64 sites per block
+    assert dg.config_supported("wilson", "f32", 2, 64, 6, (32, 32, 32, 32))
+    assert dg.config_supported("wilson", "f16", 1, 32, 6, (8, 4, 2, 3))
+    assert not dg.config_supported("wilson", "f32", 2, 128, 6, (32, 32, 32, 32))
+    assert not dg.config_supported("wilson", "f32", 3, 64, 6, (32, 32, 32, 32))
+    assert not dg.config_supported("wilson", "f32", 2, 64, 6, (24, 24, 24, 48))
+    assert not dg.config_supported("wilson", "f64", 1, 64, 6, (32, 32, 32, 32))
+    assert not dg.config_supported("brillouin", "f32", 1, 64, 6, (32, 32, 32, 32))
 
 
 def test_binding_rejects_mismatched_tensors(dg, monkeypatch):

@@ -141,6 +141,36 @@ def test_wilson_xrow_shapes(dg, prec):
                     assert rel_l2(got, want) <= TOL[prec], (L, Nv, R, block, dagger)
 
 
+@pytest.mark.parametrize("prec", ["f32", "bf16", "f16"])
+def test_wilson_xlast_shapes(dg, prec):
+    """Variant 6 (x hops last, by lane exchange of the site's own spinor):
+    rows of 32, 16, 8 and 4 sites (one to eight rows per warp, rows of one
+    warp in different planes when Lx Ly is not a multiple of 32), Nv that
+    leaves a partial group, both link formats, D and D^+."""
+    for L, Nv in (((32, 2, 2, 3), 3), ((16, 2, 3, 5), 5), ((8, 2, 2, 10), 4), ((4, 4, 2, 3), 2)):
+        V, psi = inputs("wilson", L, Nv, "f32", 275)
+        Vr, pr = rounded_for_oracle(V, psi, prec)
+        D = dg.Dirac("wilson", L, Nv, 0.121, prec)
+        D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
+        xi = D.pack(torch.from_numpy(psi.astype(np.complex64)).cuda())
+        for dag in (False, True):
+            want = oracle.apply("wilson", Vr, pr, oracle.kappa_to_m0(0.121), dagger=dag)
+            for fmt in (0, 1):
+                D.set_link_format(fmt)
+                for R in (1, 2):
+                    for block in (32, 64):
+                        assert dg.config_supported("wilson", prec, R, block, 6, L)
+                        for tc in (0, 2):
+                            D.set_kernel_config(R, block, 6)
+                            D.set_site_order(tc)
+                            yi = D.new_internal()
+                            yi.fill_(0xFF)
+                            D.apply(xi, out=yi, dagger=dag)
+                            got = D.unpack(yi).cpu().numpy().astype(np.complex128)
+                            assert rel_l2(got, want) <= TOL[prec], (L, Nv, fmt, R, block, tc, dag)
+        D.close()
+
+
 @pytest.mark.parametrize("op,mass", [("wilson", 0.124), ("staggered", 0.05), ("brillouin", 0.2)])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_apply_host_matches_device_apply(dg, op, mass, prec):
@@ -166,10 +196,11 @@ def test_apply_host_matches_device_apply(dg, op, mass, prec):
         D.close()
 
 
-@pytest.mark.parametrize("variant", [0, 2, 5, 3])
+@pytest.mark.parametrize("variant", [0, 2, 5, 6, 3])
 def test_apply_host_launch_variants(dg, variant):
-    """The slab sweeps of the t-march (2) and x-row (5) Wilson variants, and a
-    configuration that cannot sweep a slab (3: replaced by variant 1)."""
+    """The slab sweeps of the t-march (2), x-row (5) and x-last (6) Wilson
+    variants, and a configuration that cannot sweep a slab (3: replaced by
+    variant 1)."""
     L, Nv = (8, 4, 2, 10), 5
     V, psi = inputs("wilson", L, Nv, "f32", 291)
     D = dg.Dirac("wilson", L, Nv, 0.122, "f32")

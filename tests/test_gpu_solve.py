@@ -199,6 +199,34 @@ def test_brillouin_split_inner_fields(dg, prec):
         assert oracle_residual("brillouin", V, xi, bi, m).max() <= 1e-10
 
 
+@pytest.mark.parametrize("op,masses", [("wilson", [0.120, 0.1225, 0.124]), ("brillouin", [0.05, 0.1, 0.2])])
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+def test_solve_link_format_1(dg, op, masses, prec):
+    """Single and batched solves with link format 1 (Wilson two-row links in
+    the whole-lattice inner sweeps, Brillouin 80 stored W), the per-column
+    diagonal of the batched sweep included, certified by the oracle."""
+    L = (4, 4, 2, 4)
+    V = links_for(prec, synth.gauge_links(L, 3, "near_identity", 390))
+    b = synth.spinor(L, 3, 4, 3, 391)
+    D = dg.Dirac(op, L, 3, masses[0], prec)
+    D.set_preconditioner(0)          # whole-lattice inner solves: the sweeps that read format 1
+    D.set_kernel_config(2, 64, 1)
+    D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
+    D.set_link_format(1)
+    m0 = oracle.kappa_to_m0 if op == "wilson" else (lambda m: m)
+    x, res, st, status = D.solve(torch.from_numpy(b).cuda(), tol=1e-10, max_outer=60, max_inner=3000)
+    assert status == dg.OK, (res, st)
+    assert oracle_residual(op, V, x.cpu().numpy(), b, m0(masses[0])).max() <= 1e-10
+    bs = [synth.spinor(L, nv, 4, 3, 392 + i) for i, nv in enumerate([2, 1, 3])]
+    xs, res, sys_stats, tot, status = D.solve_batched([torch.from_numpy(bi).cuda() for bi in bs], masses,
+                                                      tol=1e-10, max_outer=60, max_inner=3000)
+    assert status == dg.OK, (sys_stats, tot)
+    assert D.link_format() == 1
+    for bi, xi, m in zip(bs, xs, masses):
+        assert oracle_residual(op, V, xi.cpu().numpy(), bi, m0(m)).max() <= 1e-10
+    D.close()
+
+
 def test_solve_after_set_mass_and_set_links(dg):
     """A second solve on the same handle after dirac_set_mass, and after
     dirac_set_links with new links, solves the current operator: the captured
