@@ -372,11 +372,12 @@ DIRAC_API dirac_status dirac_get_residual_arithmetic(const dirac_handle* h, int*
  *               exchanged between lanes by warp shuffles instead of loaded;
  *               needs Lx to divide 32 and Lx * Ly * Lz divisible by 32;
  *               block / 32 right-hand-side groups share a block;
- *            6: (Wilson, FP32/BF16/FP16, R <= 2, same lattice rule as 5)
- *               variant 1 with the x hops done last by lane exchange: each
- *               site's own spinor, loaded once, serves the diagonal term and
- *               both x hops, so two of the nine spinor loads and one of the
- *               eight link loads per site disappear; 32 or 64 sites per block.
+ *            6: (Wilson with R <= 2, and staggered; FP32/BF16/FP16; the
+ *               lattice rule of variant 5) variant 1 with the x hops done
+ *               last by lane exchange: each site's own spinor, loaded once,
+ *               serves the diagonal term and both x hops, so two of the nine
+ *               spinor loads and one of the eight link loads per site
+ *               disappear; 32 or 64 sites per block.
  * UNSUPPORTED for other values. */
 DIRAC_API dirac_status dirac_set_kernel_config(dirac_handle* h, int R, int block, int variant);
 
@@ -411,8 +412,8 @@ DIRAC_API dirac_status dirac_get_site_order(const dirac_handle* h, int* tchunk);
  *          stays.  Brillouin (every precision) reads all 80 W stored at x
  *          (W_{-dir}(x) precomputed, copied without rounding): twice the W
  *          bytes, local reads only.
- * Format 1 is read by the launch variants that support it (Wilson: variants
- * 1 and 6; staggered: variant 1; Brillouin: variants 0 and 1) in the apply
+ * Format 1 is read by the launch variants that support it (Wilson and
+ * staggered: variants 1 and 6; Brillouin: variants 0 and 1) in the apply
  * and in the whole-lattice inner sweeps of the solvers; other variants and
  * the even-odd sweeps read the plain links.  The
  * format-1 copy (Wilson/staggered: 4 x 6 complex per site; Brillouin: 80 x 9)

@@ -499,7 +499,7 @@ class Dirac:
         return R.value, B.value, Pp.value
 
 
-VARIANTS = {"staggered": (0, 1), "wilson": (0, 1, 2, 3, 5, 6), "brillouin": (0, 1)}
+VARIANTS = {"staggered": (0, 1, 6), "wilson": (0, 1, 2, 3, 5, 6), "brillouin": (0, 1)}
 
 
 def config_supported(op: str, prec: str, R: int, block: int, variant: int, L=None) -> bool:
@@ -510,7 +510,12 @@ def config_supported(op: str, prec: str, R: int, block: int, variant: int, L=Non
     if variant == 4:
         return False   # not used
     if variant in (5, 6):
-        if op != "wilson" or prec == "f64" or not 1 <= R <= 2 or block > (192 if variant == 5 else 64) or L is None:
+        if prec == "f64" or block > (192 if variant == 5 else 64) or L is None:
+            return False
+        if op == "wilson":
+            if not 1 <= R <= 2:
+                return False
+        elif not (op == "staggered" and variant == 6 and R in (1, 2, 4, 6)):
             return False
         return 32 % L[0] == 0 and (L[0] * L[1] * L[2]) % 32 == 0
     if op == "staggered" and R not in (1, 2, 4, 6):

@@ -4,6 +4,8 @@
 // from registers, and every output element is written once.  Consecutive
 // blocks cover the right-hand-side groups of the same sites, so the other
 // groups find the links in L2.
+#include <type_traits>
+
 #include "dirac_internal.h"
 
 namespace dirac {
@@ -32,11 +34,46 @@ __global__ void __launch_bounds__(192, 2) k_staggered_groups(ApplyArgs a, int ng
     staggered_site<T, R, DAG, MODE, LF>(a, slab_site(a, p), group);
 }
 
+// V_XLAST: V_GROUPS with the x hops last, by lane exchange (staggered_site_xlast);
+// the host checked that every warp holds whole x-rows
+template <typename T, int R, bool DAG, int MODE, int LF>
+__global__ void __launch_bounds__(192, 2) k_staggered_xlast(ApplyArgs a, int ngroups, int gy)
+{
+    const int nchunks = (ngroups + gy - 1) / gy;
+    const long b = blockIdx.x;
+    const int group = (int)(b % nchunks) * gy + threadIdx.y;
+    const long p = (b / nchunks) * blockDim.x + threadIdx.x;
+    if (p >= a.nsites || group >= ngroups) return;   // whole warps
+    staggered_site_xlast<T, R, DAG, MODE, LF>(a, slab_site(a, p), threadIdx.x & 31, group);
+}
+
 template <typename T, int R>
 static cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
 {
     const int block = c.block;
     const int ngroups = (a.Nv + R - 1) / R;
+    if constexpr (sizeof(T) != 8) {
+    if (c.variant == V_XLAST) {
+        const int gy = groups_per_block(block, ngroups);
+        const long nb = ((a.nsites + block - 1) / block) * (long)((ngroups + gy - 1) / gy);
+        const bool dv = a.diag_vf != nullptr;
+        const int mode = (a.Nv % R != 0 || (a.diag_v != nullptr && !dv)) ? 0 : (dv ? 2 : 1);
+        auto launch_lf = [&](auto m, auto lf) {
+            constexpr int M = decltype(m)::value;
+            constexpr int LF = decltype(lf)::value;
+            if (dag) k_staggered_xlast<T, R, true, M, LF><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+            else k_staggered_xlast<T, R, false, M, LF><<<(unsigned)nb, dim3(block, gy), 0, st>>>(a, ngroups, gy);
+        };
+        auto launch = [&](auto m) {
+            if (c.fmt == 1) launch_lf(m, std::integral_constant<int, 1>{});
+            else launch_lf(m, std::integral_constant<int, 0>{});
+        };
+        if (mode == 1) launch(std::integral_constant<int, 1>{});
+        else if (mode == 2) launch(std::integral_constant<int, 2>{});
+        else launch(std::integral_constant<int, 0>{});
+        return cudaGetLastError();
+    }
+    }
     if (c.variant == V_GROUPS) {
         const int gy = groups_per_block(block, ngroups);
         const long nb = ((a.nsites + block - 1) / block) * (long)((ngroups + gy - 1) / gy);
@@ -69,7 +106,7 @@ static cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st
 template <typename T>
 static cudaError_t go_T(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
 {
-    if (c.variant != V_DIRECT && c.variant != V_GROUPS) return cudaErrorInvalidValue;
+    if (c.variant != V_DIRECT && c.variant != V_GROUPS && c.variant != V_XLAST) return cudaErrorInvalidValue;
     switch (c.R) {
     case 1: return go<T, 1>(dag, a, c, st);
     case 2: return go<T, 2>(dag, a, c, st);

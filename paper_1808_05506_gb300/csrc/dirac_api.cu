@@ -700,8 +700,8 @@ bool apply_config_supported(int op, int prec, int R, int block, int variant, con
         return op == OP_WILSON && prec != P_F64 && R >= 1 && R <= 2 && block <= 192 && 32 % g.L[0] == 0 &&
                g.stride[3] % 32 == 0;
     if (variant == V_XLAST)
-        return op == OP_WILSON && prec != P_F64 && R >= 1 && R <= 2 && block <= 64 && 32 % g.L[0] == 0 &&
-               g.stride[3] % 32 == 0;
+        return prec != P_F64 && block <= 64 && 32 % g.L[0] == 0 && g.stride[3] % 32 == 0 &&
+               ((op == OP_WILSON && R >= 1 && R <= 2) || (op == OP_STAGGERED && (R == 1 || R == 2 || R == 4 || R == 6)));
     const bool Rok = (op == OP_STAGGERED) ? (R == 1 || R == 2 || R == 4 || R == 6) : (R >= 1 && R <= 4);
     if (!Rok) return false;
     if (variant == V_DIRECT) return true;

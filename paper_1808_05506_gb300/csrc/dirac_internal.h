@@ -33,9 +33,10 @@ enum Variant {
                     // of the (x, y, z) volume (whole x-rows) and walks up to 8 t-slices; x hops
                     // by warp shuffles, t hops carried in registers; `block` = threads
                     // (block / 32 right-hand-side groups per block)
-    V_XLAST = 6     // Wilson (FP32/BF16/FP16, R <= 2), Lx dividing 32 and 32 dividing Lx Ly Lz:
-                    // V_GROUPS with the x hops last, by lane exchange of the site's own spinor
-                    // (wilson_site_xlast); `block` = sites per block (32 or 64)
+    V_XLAST = 6     // Wilson (R <= 2) and staggered, FP32/BF16/FP16, Lx dividing 32 and 32
+                    // dividing Lx Ly Lz: V_GROUPS with the x hops last, by lane exchange of the
+                    // site's own spinor (wilson_site_xlast, staggered_site_xlast); `block` =
+                    // sites per block (32 or 64)
 };
 
 struct LaunchCfg {
@@ -49,12 +50,12 @@ struct LaunchCfg {
 };
 
 // whether a launch variant reads link format 1: Wilson and staggered
-// V_GROUPS (Wilson also V_XLAST) with FP32 / 16-bit storage, Brillouin
-// V_DIRECT and V_GROUPS
+// V_GROUPS and V_XLAST with FP32 / 16-bit storage, Brillouin V_DIRECT and
+// V_GROUPS
 inline bool link_format_supported(int op, int prec, int variant)
 {
     if (op == OP_BRILLOUIN) return variant == V_DIRECT || variant == V_GROUPS;
-    return prec != P_F64 && (variant == V_GROUPS || (op == OP_WILSON && variant == V_XLAST));
+    return prec != P_F64 && (variant == V_GROUPS || variant == V_XLAST);
 }
 
 // threads per block of V_GROUPS: block sites x gy groups with block * gy <= 192

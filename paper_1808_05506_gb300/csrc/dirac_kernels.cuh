@@ -680,6 +680,81 @@ DEV_INLINE void staggered_site(const ApplyArgs& a, long s, int group)
     }
 }
 
+// staggered_site with the x hops last, by lane exchange of the site's own
+// spinor (the warp layout of wilson_site_xlast: whole x-rows per warp, lane
+// the thread's lane): lane x sends psi(x) to lane x - 1 for its forward hop
+// and V_x(x)^+ psi(x) to lane x + 1 for its backward hop (eta_0 = 1)
+template <typename T, int R, bool DAG, int MODE = 0, int LF = 0>
+DEV_INLINE void staggered_site_xlast(const ApplyArgs& a, long s, int lane, int group)
+{
+    constexpr bool FAST = MODE != 0;
+    using A = typename Store<T>::A;
+    long fwd[4], bwd[4];
+    int x[4];
+    site_offsets(a.g, s, fwd, bwd, x);
+    const int Lx = a.g.L[0];
+    const int lane_f = lane - x[0] + (x[0] + 1 == Lx ? 0 : x[0] + 1);   // site x + 1
+    const int lane_b = lane - x[0] + (x[0] == 0 ? Lx - 1 : x[0] - 1);   // site x - 1
+    const int v0 = group * R;
+    cx<A> acc[R][3];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) acc[r][i] = cx<A>{A(0), A(0)};
+    int par = x[0];  // x_0 + ... + x_{mu-1}, from mu = 1 on
+#pragma unroll
+    for (int mu = 1; mu < 4; ++mu) {
+        const A eta = (par & 1) ? A(-1) : A(1);
+        par += x[mu];
+        cx<A> Uf[9], Ub[9];
+        load_link_f<T, false, LF>(a.links, a.g.vol, mu, s, Uf);
+        load_link_f<T, false, LF>(a.links, a.g.vol, mu, s + bwd[mu], Ub);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int v = FAST ? v0 + r : min(v0 + r, a.Nv - 1);
+            cx<A> pf[3], pb[3], w[3] = {}, wb[3] = {};
+            load_spinor<T, 3>(a.in, a.g.vol, v, s + fwd[mu], pf);
+            load_spinor<T, 3>(a.in, a.g.vol, v, s + bwd[mu], pb);
+            mat_vec(Uf, pf, w);
+            mat_dag_vec(Ub, pb, wb);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                cx<A> d = w[c] - wb[c];
+                acc[r][c].re = fma(eta, d.re, acc[r][c].re);
+                acc[r][c].im = fma(eta, d.im, acc[r][c].im);
+            }
+        }
+    }
+    cx<A> U[9];
+    load_link_f<T, false, LF>(a.links, a.g.vol, 0, s, U);
+    const A hf = DAG ? A(-0.5) : A(0.5);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int v = FAST ? v0 + r : min(v0 + r, a.Nv - 1);
+        cx<A> p[3], q[3], w[3], wb[3];
+        load_spinor<T, 3>(a.in, a.g.vol, v, s, p);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) q[c] = shfl_cx(p[c], lane_f);
+        mat_vec(U, q, w);          // V_x(x) psi(x + 1)
+        mat_dag_vec(U, p, q);      // V_x(x)^+ psi(x): the backward hop of site x + 1
+#pragma unroll
+        for (int c = 0; c < 3; ++c) wb[c] = shfl_cx(q[c], lane_b);
+        const A dg = diag_mode<A>(a, v, MODE);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const cx<A> d = w[c] - wb[c];
+            cx<A> t;
+            t.re = acc[r][c].re + d.re;
+            t.im = acc[r][c].im + d.im;
+            cx<A> o;
+            o.re = fma(hf, t.re, dg * p[c].re);
+            o.im = fma(hf, t.im, dg * p[c].im);
+            p[c] = o;
+        }
+        if (FAST || v0 + r < a.Nv) store_spinor<T, 3>(a.out, a.g.vol, v0 + r, s, p);
+    }
+}
+
 // ---------------------------------------------------------------- Brillouin
 // The 80 off-centre directions, each with its spin matrix
 //   M = rho_k (dir . gamma) - lambda_k / 2 = [[a, rho Q], [rho Q^+, a]],

@@ -208,6 +208,9 @@ def test_config_rule(dg):
     assert not dg.config_supported("wilson", "f32", 2, 64, 6, (24, 24, 24, 48))
     assert not dg.config_supported("wilson", "f64", 1, 64, 6, (32, 32, 32, 32))
     assert not dg.config_supported("brillouin", "f32", 1, 64, 6, (32, 32, 32, 32))
+    assert dg.config_supported("staggered", "f32", 6, 64, 6, (32, 32, 32, 32))
+    assert not dg.config_supported("staggered", "f32", 3, 64, 6, (32, 32, 32, 32))
+    assert not dg.config_supported("staggered", "f64", 2, 64, 6, (32, 32, 32, 32))
 
 
 def test_binding_rejects_mismatched_tensors(dg, monkeypatch):

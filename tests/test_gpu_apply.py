@@ -141,25 +141,27 @@ def test_wilson_xrow_shapes(dg, prec):
                     assert rel_l2(got, want) <= TOL[prec], (L, Nv, R, block, dagger)
 
 
+@pytest.mark.parametrize("op,mass", [("wilson", 0.121), ("staggered", 0.07)])
 @pytest.mark.parametrize("prec", ["f32", "bf16", "f16"])
-def test_wilson_xlast_shapes(dg, prec):
+def test_xlast_shapes(dg, op, mass, prec):
     """Variant 6 (x hops last, by lane exchange of the site's own spinor):
     rows of 32, 16, 8 and 4 sites (one to eight rows per warp, rows of one
     warp in different planes when Lx Ly is not a multiple of 32), Nv that
     leaves a partial group, both link formats, D and D^+."""
+    Rs = (1, 2) if op == "wilson" else (1, 2, 4)
     for L, Nv in (((32, 2, 2, 3), 3), ((16, 2, 3, 5), 5), ((8, 2, 2, 10), 4), ((4, 4, 2, 3), 2)):
-        V, psi = inputs("wilson", L, Nv, "f32", 275)
+        V, psi = inputs(op, L, Nv, "f32", 275)
         Vr, pr = rounded_for_oracle(V, psi, prec)
-        D = dg.Dirac("wilson", L, Nv, 0.121, prec)
+        D = dg.Dirac(op, L, Nv, mass, prec)
         D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
         xi = D.pack(torch.from_numpy(psi.astype(np.complex64)).cuda())
         for dag in (False, True):
-            want = oracle.apply("wilson", Vr, pr, oracle.kappa_to_m0(0.121), dagger=dag)
+            want = oracle.apply(op, Vr, pr, m0_of(op, mass), dagger=dag)
             for fmt in (0, 1):
                 D.set_link_format(fmt)
-                for R in (1, 2):
+                for R in Rs:
                     for block in (32, 64):
-                        assert dg.config_supported("wilson", prec, R, block, 6, L)
+                        assert dg.config_supported(op, prec, R, block, 6, L)
                         for tc in (0, 2):
                             D.set_kernel_config(R, block, 6)
                             D.set_site_order(tc)
