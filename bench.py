@@ -193,7 +193,7 @@ def other_format_time(dg, torch, D, x, y, w, steps, warmup, fmt):
     except dg.DiracError as e:
         return {"fmt": other, "unavailable": str(e)}
     R, B, variant = D.kernel_config()
-    if not (variant == 1 or (w["op"] == "wilson" and variant == 6) or (w["op"] == "brillouin" and variant == 0)):
+    if not (variant == 1 or (w["op"] != "brillouin" and variant == 6) or (w["op"] == "brillouin" and variant == 0)):
         D.set_kernel_config(2, 64, 1)
         D.set_site_order(min(8, w["L"][3]))
     _, per = time_kernel(torch, lambda: D.apply(x, out=y), steps, warmup)
