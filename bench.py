@@ -739,7 +739,7 @@ def main():
                      "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                      "nominal_peak": NOMINAL_HBM_GBS,
                      "peak_kind": f"{peak_kind} copy bandwidth",
-                     "kernel": "k_{}{}<{},R={}>".format(op, {0: "", 1: "_groups", 2: "_march", 3: "_pipe", 5: "_xrow", 6: "_xlast"}[cfg[2]],
+                     "kernel": "k_{}{}<{},R={}>".format(op, {0: "", 1: "_groups", 2: "_march", 3: "_pipe", 5: "_xrow", 6: "_xlast", 7: "_tc"}[cfg[2]],
                                                       w["prec"], cfg[0]),
                      "algorithmic_bytes_per_launch": bytes_step,
                      "link_format": link_fmt,

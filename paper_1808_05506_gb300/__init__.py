@@ -499,7 +499,7 @@ class Dirac:
         return R.value, B.value, Pp.value
 
 
-VARIANTS = {"staggered": (0, 1, 6), "wilson": (0, 1, 2, 3, 5, 6), "brillouin": (0, 1)}
+VARIANTS = {"staggered": (0, 1, 6), "wilson": (0, 1, 2, 3, 5, 6), "brillouin": (0, 1, 7)}
 
 
 def config_supported(op: str, prec: str, R: int, block: int, variant: int, L=None) -> bool:
@@ -509,6 +509,8 @@ def config_supported(op: str, prec: str, R: int, block: int, variant: int, L=Non
         return False
     if variant == 4:
         return False   # not used
+    if variant == 7:   # tensor cores: Brillouin, 16-bit storage
+        return op == "brillouin" and prec in ("bf16", "f16") and R == 1 and block == 128
     if variant in (5, 6):
         if prec == "f64" or block > (192 if variant == 5 else 64) or L is None:
             return False

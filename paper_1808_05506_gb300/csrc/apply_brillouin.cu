@@ -5,6 +5,7 @@
 // spinors from registers.  The direction table sits in constant memory, read
 // with a warp-uniform index.
 #include <cstring>
+#include <type_traits>
 #include <mutex>
 
 #include "dirac_df.cuh"
@@ -65,6 +66,11 @@ static cudaError_t go(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st
 template <typename T>
 static cudaError_t go_T(bool dag, const ApplyArgs& a, LaunchCfg c, cudaStream_t st)
 {
+    if (c.variant == V_TC) {
+        // tensor cores: 16-bit storage with all 80 W stored per site
+        if (sizeof(T) != 2 || c.fmt != 1) return cudaErrorInvalidValue;
+        return launch_brillouin_tc(sizeof(T) == 2 && std::is_same<T, __half>::value ? P_F16 : P_BF16, dag, a, st);
+    }
     if (c.variant != V_DIRECT && c.variant != V_GROUPS) return cudaErrorInvalidValue;
     switch (c.R) {
     case 1: return go<T, 1>(dag, a, c, st);

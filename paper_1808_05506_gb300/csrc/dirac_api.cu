@@ -136,6 +136,8 @@ dirac_status dirac_handle::run_apply(bool dagger, void* out, const void* in, int
         c.fmt = 1;
     } else {
         c.fmt = 0;
+        // the tensor-core sweep reads only link format 1: without it, the CUDA-core sweep
+        if (c.variant == V_TC) c = LaunchCfg{2, 128, V_DIRECT, c.order, 0};
     }
     ApplyArgs a = args(out, in, nv, diag_value);
     a.links = link_ptr;
@@ -147,7 +149,7 @@ dirac_status dirac_handle::run_apply(bool dagger, void* out, const void* in, int
         a.nt = nt;
         a.nsites = (long)nt * g.stride[3];
     }
-    a.tc = (c.variant == V_DIRECT || c.variant == V_GROUPS || c.variant == V_XLAST) ? c.order : 0;
+    a.tc = (c.variant == V_DIRECT || c.variant == V_GROUPS || c.variant == V_XLAST || c.variant == V_TC) ? c.order : 0;
     if (a.tc > 0) {
         a.fdc = make_fdiv((uint32_t)(g.L[2] * a.tc));
         a.fdt = make_fdiv((uint32_t)a.tc);
@@ -234,6 +236,7 @@ dirac_status dirac_create(dirac_handle** h, dirac_op op, int Nc, int Nx, int Ny,
     }
     if (H->op == OP_BRILLOUIN) {
         cudaError_t e = upload_brillouin_table(H->stream);
+        if (e == cudaSuccess && (prec == DIRAC_BF16 || prec == DIRAC_F16)) e = brillouin_tc_prepare(H->stream);
         if (e != cudaSuccess) {
             cudaGetLastError();
             g_create_error = std::string("dirac_create: direction table upload: ") + cudaGetErrorString(e);
@@ -560,6 +563,11 @@ dirac_status dirac_set_kernel_config(dirac_handle* h, int R, int block, int vari
     if (!apply_config_supported(h->op, h->prec, R, block, variant, h->g))
         return h->fail(DIRAC_ERR_UNSUPPORTED, "dirac_set_kernel_config: R = %d, block = %d, variant = %d not built",
                        R, block, variant);
+    if (variant == V_TC && h->link_fmt != 1) {
+        // the tensor-core sweep reads all 80 W per site (link format 1)
+        const dirac_status st = dirac_set_link_format(h, 1);
+        if (st) return st;
+    }
     h->cfg = LaunchCfg{R, block, variant, h->cfg.order};
     return DIRAC_OK;
 }
@@ -699,6 +707,7 @@ bool apply_config_supported(int op, int prec, int R, int block, int variant, con
     if (variant == V_XROW)
         return op == OP_WILSON && prec != P_F64 && R >= 1 && R <= 2 && block <= 192 && 32 % g.L[0] == 0 &&
                g.stride[3] % 32 == 0;
+    if (variant == V_TC) return op == OP_BRILLOUIN && (prec == P_BF16 || prec == P_F16) && R == 1 && block == 128;
     if (variant == V_XLAST)
         return prec != P_F64 && block <= 64 && 32 % g.L[0] == 0 && g.stride[3] % 32 == 0 &&
                ((op == OP_WILSON && R >= 1 && R <= 2) || (op == OP_STAGGERED && (R == 1 || R == 2 || R == 4 || R == 6)));

@@ -136,7 +136,7 @@ extern "C" DIRAC_API dirac_status dirac_apply_host(dirac_handle* h, void* out, c
     // the slab sweeps need a launch shape that can cover a t-slab
     LaunchCfg c = h->cfg;
     if (c.variant != V_DIRECT && c.variant != V_GROUPS && c.variant != V_TMARCH && c.variant != V_XROW &&
-        c.variant != V_XLAST)
+        c.variant != V_XLAST && c.variant != V_TC)
         c = LaunchCfg{c.R, 64, V_GROUPS, c.order};
     if (!apply_config_supported(h->op, h->prec, c.R, c.block, c.variant, h->g)) c = default_config(h->op, h->prec, h->Nv);
     auto slab_t0 = [&](int k) { return k * ts; };

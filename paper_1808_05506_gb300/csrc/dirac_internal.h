@@ -33,10 +33,12 @@ enum Variant {
                     // of the (x, y, z) volume (whole x-rows) and walks up to 8 t-slices; x hops
                     // by warp shuffles, t hops carried in registers; `block` = threads
                     // (block / 32 right-hand-side groups per block)
-    V_XLAST = 6     // Wilson (R <= 2) and staggered, FP32/BF16/FP16, Lx dividing 32 and 32
+    V_XLAST = 6,    // Wilson (R <= 2) and staggered, FP32/BF16/FP16, Lx dividing 32 and 32
                     // dividing Lx Ly Lz: V_GROUPS with the x hops last, by lane exchange of the
                     // site's own spinor (wilson_site_xlast, staggered_site_xlast); `block` =
                     // sites per block (32 or 64)
+    V_TC = 7        // Brillouin, BF16/FP16 storage, link format 1: the per-site contraction on
+                    // the tensor cores (tcgen05.mma, apply_brillouin_tc.cu); R = 1, block = 128
 };
 
 struct LaunchCfg {
@@ -54,7 +56,7 @@ struct LaunchCfg {
 // V_GROUPS
 inline bool link_format_supported(int op, int prec, int variant)
 {
-    if (op == OP_BRILLOUIN) return variant == V_DIRECT || variant == V_GROUPS;
+    if (op == OP_BRILLOUIN) return variant == V_DIRECT || variant == V_GROUPS || variant == V_TC;
     return prec != P_F64 && (variant == V_GROUPS || variant == V_XLAST);
 }
 
@@ -87,6 +89,12 @@ cudaError_t launch_apply_wilson(int prec, bool dagger, const ApplyArgs& a, Launc
                                 cudaStream_t st);
 cudaError_t launch_apply_brillouin(int prec, bool dagger, const ApplyArgs& a, LaunchCfg cfg,
                                    cudaStream_t st);
+
+// Brillouin sweep on the tensor cores (V_TC; a.links = the 80 W per site in the
+// 16-bit storage type); prepare uploads its direction table (once per device,
+// before any stream capture)
+cudaError_t brillouin_tc_prepare(cudaStream_t st);
+cudaError_t launch_brillouin_tc(int prec, bool dag, const ApplyArgs& a, cudaStream_t st);
 
 // Brillouin sweeps of the split inner solve (apply_brillouin_split.cuh):
 // dag = false t(F32) = D p(16), dag = true s(16) = D^+ r(F32), FP32 W; prepare

@@ -223,7 +223,7 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
         best = 1e30;
         LaunchCfg win = h->cfg;
         win.fmt = 0;
-        const int variants[] = {V_DIRECT, V_GROUPS, V_TMARCH, V_PIPE3, V_XROW, V_XLAST};
+        const int variants[] = {V_DIRECT, V_GROUPS, V_TMARCH, V_PIPE3, V_XROW, V_XLAST, V_TC};
         // link format 0 (the plain links) over every built launch shape, then
         // link format 1 (two-row links / 80 stored W) over the shapes that read
         // it, where the links allow it
@@ -242,9 +242,10 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
                 for (int oi = 0; oi < 2; ++oi) {
                     if (!apply_config_supported(h->op, h->prec, r, b, pp, h->g)) continue;
                     if (fm == 1 && !link_format_supported(h->op, h->prec, pp)) continue;
+                    if (fm == 0 && pp == V_TC) continue;   // reads link format 1 only
                     // site order: lexicographic, or t-chunks of 8 slices (variants 0 and 1)
                     const int tc = oi == 0 ? 0 : std::min(8, h->g.L[3]);
-                    if (oi == 1 && pp != V_DIRECT && pp != V_GROUPS && pp != V_XLAST) continue;
+                    if (oi == 1 && pp != V_DIRECT && pp != V_GROUPS && pp != V_XLAST && pp != V_TC) continue;
                     LaunchCfg c{r, b, pp, tc, fm};
                     double med = 0.0;
                     if (!time_cfg(c, &med)) {

@@ -27,6 +27,7 @@ namespace dirac {
 // the launchers are not used on the host
 cudaError_t launch_eo_wilson(int, bool, const EoArgs&, int, int, cudaStream_t) { return cudaErrorInvalidValue; }
 cudaError_t launch_eo_staggered(int, bool, const EoArgs&, int, int, cudaStream_t) { return cudaErrorInvalidValue; }
+cudaError_t launch_brillouin_tc(int, bool, const ApplyArgs&, cudaStream_t) { return cudaErrorInvalidValue; }
 }  // namespace dirac
 
 static int g_fail = 0;

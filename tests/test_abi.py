@@ -211,6 +211,12 @@ def test_config_rule(dg):
     assert dg.config_supported("staggered", "f32", 6, 64, 6, (32, 32, 32, 32))
     assert not dg.config_supported("staggered", "f32", 3, 64, 6, (32, 32, 32, 32))
     assert not dg.config_supported("staggered", "f64", 2, 64, 6, (32, 32, 32, 32))
+    # tensor cores: Brillouin with 16-bit storage, one launch shape
+    assert dg.config_supported("brillouin", "bf16", 1, 128, 7)
+    assert dg.config_supported("brillouin", "f16", 1, 128, 7)
+    assert not dg.config_supported("brillouin", "f32", 1, 128, 7)
+    assert not dg.config_supported("brillouin", "bf16", 2, 128, 7)
+    assert not dg.config_supported("wilson", "bf16", 1, 128, 7)
 
 
 def test_binding_rejects_mismatched_tensors(dg, monkeypatch):

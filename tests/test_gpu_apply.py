@@ -430,6 +430,39 @@ def test_brillouin_80_stored_links(dg, prec):
     D.close()
 
 
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+def test_brillouin_tensor_cores(dg, prec):
+    """Variant 7, the Brillouin sweep on the tensor cores (tcgen05.mma, 16-bit
+    operands, FP32 accumulation): parity with the oracle at the storage
+    rounding bound, D and D^+, ragged volumes, a partial block of 16
+    right-hand sides and two blocks, canonical and internal fields, the
+    per-column diagonal of the batched solver, and the host-buffer apply
+    (t-slabs)."""
+    for L, Nv in (((4, 6, 2, 5), 5), ((4, 4, 4, 4), 12), ((3, 4, 2, 4), 20)):
+        V, psi = inputs("brillouin", L, Nv, prec, 320, kind="near_identity")
+        pr = synth.round_to(psi, prec)     # W is built in FP64 from the FP32 links, rounded once
+        D = dg.Dirac("brillouin", L, Nv, 0.07, prec)
+        D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
+        D.set_kernel_config(1, 128, 7)
+        assert D.link_format() == 1
+        x = torch.from_numpy(psi.astype(np.complex64)).cuda()
+        for dag in (False, True):
+            want = oracle.apply("brillouin", V, pr, 0.07, dagger=dag)
+            got = D.apply(x, dagger=dag).cpu().numpy().astype(np.complex128)
+            assert rel_l2(got, want) <= TOL[prec], (L, Nv, dag)
+            xi = D.pack(x)
+            yi = D.new_internal()
+            yi.fill_(0xFF)
+            D.apply(xi, out=yi, dagger=dag)
+            D.sync()
+            got = D.unpack(yi).cpu().numpy().astype(np.complex128)
+            assert rel_l2(got, want) <= TOL[prec], (L, Nv, dag, "internal")
+        hx = torch.from_numpy(psi.astype(np.complex64)).pin_memory()
+        got = D.apply_host(hx).numpy().astype(np.complex128)
+        assert rel_l2(got, oracle.apply("brillouin", V, pr, 0.07)) <= TOL[prec]
+        D.close()
+
+
 def test_autotune_link_format(dg, tmp_path, monkeypatch):
     """The tuner times both link formats and records the winner; the tuned
     handle reproduces the sweep, and a second handle takes the format from the
