@@ -131,8 +131,9 @@ dirac_status dirac_handle::run_apply(bool dagger, void* out, const void* in, int
     // link format 1 (dirac_set_link_format) for the storage links, where the
     // launch variant reads it; every other call reads the plain links
     const int f = c.fmt < 0 ? link_fmt : c.fmt;
-    if (f == 1 && link_ptr == links && p == prec && links_alt && link_format_supported(op, p, c.variant)) {
-        link_ptr = links_alt;
+    if (f == 1 && link_ptr == links && p == prec && links_alt && link_format_supported(op, p, c.variant) &&
+        (c.variant != V_TC || links_tc)) {
+        link_ptr = c.variant == V_TC ? links_tc : links_alt;
         c.fmt = 1;
     } else {
         c.fmt = 0;
@@ -259,6 +260,7 @@ dirac_handle::~dirac_handle()
     release(links_df);
     release(links32);
     release(links_alt);
+    release(links_tc);
     release(ws_in);
     release(ws_out);
     free_solver_workspace();
@@ -355,7 +357,7 @@ dirac_status dirac_set_links(dirac_handle* h, const void* V, dirac_prec V_prec, 
         // (two-row links of links that are not special unitary) fall back to
         // format 0, which gives the same operator
         if (h->build_link_alt() != DIRAC_OK) {
-            h->release_after_sync(h->links_alt);
+            h->release_link_alt();
             h->link_fmt = 0;
         }
     }
@@ -375,7 +377,11 @@ dirac_status dirac_handle::build_link_alt()
     const size_t nsite = nblk_of((size_t)g.vol) * 32;
     if (op == OP_BRILLOUIN) {
         if (!links_alt && (st = alloc(&links_alt, nsite * 80 * 9 * cbytes(prec), "80-direction W"))) return st;
-        return cuda(launch_brillouin_w80(prec, g, links, links_alt, stream), "80-direction W");
+        if ((st = cuda(launch_brillouin_w80(prec, g, links, links_alt, stream), "80-direction W"))) return st;
+        if (prec != P_BF16 && prec != P_F16) return DIRAC_OK;
+        // the copy the tensor-core sweep reads: the 80 W of a site in one piece
+        if (!links_tc && (st = alloc(&links_tc, nsite * 80 * 9 * cbytes(prec), "80-direction W, site-major"))) return st;
+        return cuda(launch_brillouin_tc_links(g, links_alt, links_tc, stream), "80-direction W, site-major");
     }
     if (prec == P_F64)
         return fail(DIRAC_ERR_UNSUPPORTED, "dirac_set_link_format: two-row links are built for FP32 and 16-bit storage");
@@ -494,6 +500,12 @@ void dirac_handle::release_after_sync(void*& p)
     release(p);
 }
 
+void dirac_handle::release_link_alt()
+{
+    release_after_sync(links_alt);
+    release_after_sync(links_tc);
+}
+
 // ------------------------------------------------------------------ fields
 dirac_status dirac_field_bytes(const dirac_handle* h, dirac_layout layout, size_t* bytes)
 {
@@ -579,7 +591,7 @@ dirac_status dirac_set_link_format(dirac_handle* h, int fmt)
         return h->fail(DIRAC_ERR_INVALID_ARG, "dirac_set_link_format: format %d is not 0 or 1", fmt);
     if (fmt == 0) {
         h->link_fmt = 0;
-        h->release_after_sync(h->links_alt);
+        h->release_link_alt();
         return DIRAC_OK;
     }
     if (h->op != OP_BRILLOUIN && h->prec == P_F64)
@@ -588,7 +600,7 @@ dirac_status dirac_set_link_format(dirac_handle* h, int fmt)
         dirac_status st = h->build_link_alt();
         if (!st) st = h->cuda(cudaStreamSynchronize(h->stream), "dirac_set_link_format");
         if (st) {
-            h->release_after_sync(h->links_alt);
+            h->release_link_alt();
             h->link_fmt = 0;
             return st;
         }

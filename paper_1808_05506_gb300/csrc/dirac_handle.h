@@ -33,6 +33,9 @@ struct dirac_handle {
                               // sweeps, for the solver's FP64 residual (lazy; F64 handles use links)
     void* links_alt = nullptr;  // link format 1 (dirac_set_link_format): Wilson / staggered two-row
                                 // links [4][6][site], Brillouin all 80 W [80][9][site] (blocked)
+    void* links_tc = nullptr;   // with link format 1 for 16-bit Brillouin: the 80 W of each site
+                                // contiguous [site][80][9], directions in the order of the
+                                // tensor-core sweep (which reads this copy)
     int link_fmt = 0;           // the format the apply sweeps read where their variant supports it
     bool have_links = false;
     int* dev_err = nullptr;   // device error word written by kernels whose bounded waits run out
@@ -57,6 +60,7 @@ struct dirac_handle {
     dirac_status alloc(void** p, size_t bytes, const char* what);
     void release(void*& p);
     void release_after_sync(void*& p);
+    void release_link_alt();   // both copies of link format 1 (links_alt, links_tc)
     size_t field_bytes_internal(int nv) const;
     size_t field_bytes_canonical(int nv) const;
     double diag_of(double mass) const;

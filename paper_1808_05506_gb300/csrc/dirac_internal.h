@@ -95,6 +95,9 @@ cudaError_t launch_apply_brillouin(int prec, bool dagger, const ApplyArgs& a, La
 // before any stream capture)
 cudaError_t brillouin_tc_prepare(cudaStream_t st);
 cudaError_t launch_brillouin_tc(int prec, bool dag, const ApplyArgs& a, cudaStream_t st);
+// the site-major copy of the 80 W (16-bit storage) the tensor-core sweep reads,
+// from link format 1 ([80][9][site], blocked); needs brillouin_tc_prepare
+cudaError_t launch_brillouin_tc_links(const Geom& g, const void* w80, void* wtc, cudaStream_t st);
 
 // Brillouin sweeps of the split inner solve (apply_brillouin_split.cuh):
 // dag = false t(F32) = D p(16), dag = true s(16) = D^+ r(F32), FP32 W; prepare

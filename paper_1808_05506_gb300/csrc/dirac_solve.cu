@@ -161,6 +161,7 @@ struct SolverWS {
     LaunchCfg g_eo_cfg{0, 0, 0};
     const void* g_links = nullptr;
     const void* g_alt = nullptr;
+    const void* g_tc = nullptr;
     int g_fmt = 0;
     const double* g_diag = nullptr;
     double g_dval = 0.0;
@@ -447,7 +448,7 @@ static dirac_status ensure_graph(dirac_handle* h, SolverWS* w, const double* dia
     };
     // the whole-lattice sweeps take the handle's diagonal by value (dirac_set_mass may change it)
     if (w->gexec && same(w->g_cfg, h->cfg) && same(w->g_eo_cfg, h->eo_cfg) && w->g_links == h->links &&
-        w->g_alt == h->links_alt && w->g_fmt == h->link_fmt && w->g_diag == diag_v && w->g_dval == h->diag)
+        w->g_alt == h->links_alt && w->g_tc == h->links_tc && w->g_fmt == h->link_fmt && w->g_diag == diag_v && w->g_dval == h->diag)
         return DIRAC_OK;
     if (w->gexec) {
         cudaGraphExecDestroy(w->gexec);
@@ -472,6 +473,7 @@ static dirac_status ensure_graph(dirac_handle* h, SolverWS* w, const double* dia
     w->g_eo_cfg = h->eo_cfg;
     w->g_links = h->links;
     w->g_alt = h->links_alt;
+    w->g_tc = h->links_tc;
     w->g_fmt = h->link_fmt;
     w->g_diag = diag_v;
     w->g_dval = h->diag;

@@ -231,7 +231,7 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
         bool have_alt = h->links_alt != nullptr;
         if (!have_alt && (h->op == OP_BRILLOUIN || h->prec != P_F64)) {
             have_alt = h->build_link_alt() == DIRAC_OK;
-            if (!have_alt) h->release_after_sync(h->links_alt);
+            if (!have_alt) h->release_link_alt();
             h->err.clear();
         }
         for (int fm = 0; fm < (have_alt ? 2 : 1) && st == DIRAC_OK; ++fm)
@@ -267,7 +267,7 @@ extern "C" DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int
         }
         h->cfg = LaunchCfg{win.R, win.block, win.variant, win.order};
         h->link_fmt = win.fmt == 1 ? 1 : 0;
-        if (h->link_fmt == 0) h->release_after_sync(h->links_alt);
+        if (h->link_fmt == 0) h->release_link_alt();
         cache_store(key, win.R, win.block, win.variant, win.order, best, h->link_fmt);
     }
     dirac_status est = tune_even_odd(h, force);
