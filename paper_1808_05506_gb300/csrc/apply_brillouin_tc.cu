@@ -42,10 +42,18 @@
 //   warp 4      one thread issues the MMA chains and commits them to the
 //               barriers that free the A slot and the B entry and hand
 //               completed accumulators to the epilogue;
-//   warps 5-12  two groups of four, filling alternate A slots (the loads of a
-//               fill are issued before waiting for its slot to be free);
-//   warps 13-20 the B blocks of each site from its 80 W, the links of the next
-//               site loaded while the current one is built.
+//   warps 5-12  fill the A slots two x-positions at a time (adjacent lanes
+//               load the adjacent 16-byte pieces of the two sites, one 32-byte
+//               sector), the loads issued before waiting for the slots;
+//   warps 13-20 the B blocks of each site from its 80 W (thread = direction x
+//               colour row, both re/im rows), the links of the next site loaded
+//               while the current one is built; the blocks for d_x = -1, 0 go
+//               first, so that the entry they complete is ready while the one
+//               for d_x = +1 still waits for its entry to be free.
+// The B entries C_j(d) W are formed in the storage arithmetic (packed 16-bit
+// multiplies, rounded to nearest): C_0 = -lambda_k / 2 is a power of two, so
+// that product is exact; rho_k is rounded to the storage type first, which
+// keeps the rho classes within two units in the last place of C_j W.
 // The padding of K, the d = 0 entries of B, the entries of the classes that
 // vanish for a direction (d_mu = 0) and the rows of absent right-hand sides
 // stay zero from the start.
@@ -73,15 +81,15 @@ constexpr uint32_t TC_SBO = (TC_KS / 8) * 128;          // bytes between 8-row g
 constexpr uint32_t TC_ASLOT = (TC_M / 8) * TC_SBO;      // one A slot (22528 B)
 constexpr uint32_t TC_BBLK = (TC_N / 8) * TC_SBO;       // one site's block of B (11264 B)
 constexpr uint32_t TC_BENT = 3 * TC_BBLK;               // one B entry (33792 B)
-constexpr int TC_NS = 3;                                // A slots
-constexpr int TC_NR = 4;                                // B entries
+constexpr int TC_NS = 4;                                // A slots
+constexpr int TC_NR = 3;                                // B entries
 constexpr int TC_NACC = 16;                             // accumulators (512 columns)
 constexpr int TC_TS = 25;                               // staged row stride (floats): classes 1..4
 constexpr uint32_t TC_TBUF = TC_M * TC_TS * 4;          // one staging buffer (6400 B)
 constexpr uint32_t TC_A_OFF = 0;
-constexpr uint32_t TC_B_OFF = TC_A_OFF + TC_NS * TC_ASLOT;   // 67584
-constexpr uint32_t TC_T_OFF = TC_B_OFF + TC_NR * TC_BENT;    // 202752
-constexpr uint32_t TC_BAR_OFF = TC_T_OFF + 2 * TC_TBUF;      // 215552
+constexpr uint32_t TC_B_OFF = TC_A_OFF + TC_NS * TC_ASLOT;   // 90112
+constexpr uint32_t TC_T_OFF = TC_B_OFF + TC_NR * TC_BENT;    // 191488
+constexpr uint32_t TC_BAR_OFF = TC_T_OFF + 2 * TC_TBUF;      // 204288
 // barriers: full / empty A slot, full / empty B entry, full / empty accumulator, drain
 constexpr int TC_BAR_FA = 0, TC_BAR_EA = TC_NS, TC_BAR_FB = 2 * TC_NS, TC_BAR_EB = 2 * TC_NS + TC_NR,
               TC_BAR_FC = 2 * TC_NS + 2 * TC_NR, TC_BAR_EC = TC_BAR_FC + TC_NACC, TC_BAR_DR = TC_BAR_EC + TC_NACC,
@@ -90,8 +98,9 @@ constexpr size_t TC_SMEM = TC_BAR_OFF + 8 * TC_NBARS + 16;
 constexpr int TC_EPI_WARPS = 4, TC_MMA_WARP = 4, TC_GATHER_WARP0 = 5, TC_B_WARP0 = 13, TC_WARPS = 21;
 constexpr int TC_THREADS = TC_WARPS * 32;
 constexpr int TC_BTHREADS = (TC_WARPS - TC_B_WARP0) * 32;    // 256 B builders, 240 with work
-constexpr int TC_GROUNDS = 14;                          // gather rounds: 2 x 8 rhs x 7 x 4 directions
-constexpr int TC_GPT = (TC_GROUNDS + 3) / 4;            // gather rounds per thread (4 warps per group)
+constexpr int TC_GTHREADS = (TC_B_WARP0 - TC_GATHER_WARP0) * 32;   // 256 gatherers
+constexpr int TC_GROUNDS = 28;                          // gather rounds of a pair: 2 x 8 rhs x 14 x 2 directions
+constexpr int TC_GPT = (TC_GROUNDS + 7) / 8;            // gather rounds per thread (8 warps)
 constexpr int TC_MAX_WAIT = 1 << 24;                    // bounded mbarrier wait: polls ...
 constexpr unsigned long long TC_MAX_NS = 500000000ull;  // ... and half a second
 constexpr uint32_t TC_SUSPEND_NS = 20000;               // suspend-time hint of one poll
@@ -131,7 +140,7 @@ __device__ __forceinline__ unsigned long long tc_clock_ns()
 // TC_MAX_WAIT polls and TC_MAX_NS nanoseconds, and only while no other role of
 // the CTA has given up (*abort); true if it completed.  A wait that runs out
 // sets *abort, so that every other role stops at its next wait.
-__device__ __noinline__ bool tc_wait(uint32_t bar, uint32_t parity, volatile int* abort)
+__device__ __noinline__ bool tc_wait_slow(uint32_t bar, uint32_t parity, volatile int* abort)
 {
     const unsigned long long t0 = tc_clock_ns();
     for (int it = 0; it < TC_MAX_WAIT; ++it) {
@@ -146,6 +155,43 @@ __device__ __noinline__ bool tc_wait(uint32_t bar, uint32_t parity, volatile int
     }
     *abort = 1;
     return false;
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity, volatile int* abort)
+{
+    uint32_t done;
+    asm volatile("{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    return done ? true : tc_wait_slow(bar, parity, abort);
+}
+
+// shared memory by 32-bit address (an immediate offset where the call gives one)
+template <int OFF = 0> __device__ __forceinline__ void tc_sts32(uint32_t a, uint32_t v)
+{
+    asm volatile("st.shared.u32 [%0+%2], %1;" ::"r"(a), "r"(v), "n"(OFF));
+}
+__device__ __forceinline__ void tc_sts64(uint32_t a, uint32_t v0, uint32_t v1)
+{
+    asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(a), "r"(v0), "r"(v1));
+}
+__device__ __forceinline__ float tc_ldsf(uint32_t a)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void tc_stsf(uint32_t a, float v) { asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v)); }
+
+// packed 16-bit product, rounded to nearest
+__device__ __forceinline__ uint32_t tc_mul2(uint32_t x, uint32_t y, __nv_bfloat16*)
+{
+    const __nv_bfloat162 r = __hmul2(*reinterpret_cast<const __nv_bfloat162*>(&x), *reinterpret_cast<const __nv_bfloat162*>(&y));
+    return *reinterpret_cast<const uint32_t*>(&r);
+}
+__device__ __forceinline__ uint32_t tc_mul2(uint32_t x, uint32_t y, __half*)
+{
+    const __half2 r = __hmul2(*reinterpret_cast<const __half2*>(&x), *reinterpret_cast<const __half2*>(&y));
+    return *reinterpret_cast<const uint32_t*>(&r);
 }
 
 __device__ __forceinline__ void tc_bar_init(uint32_t bar, uint32_t count)
@@ -231,31 +277,37 @@ __device__ __forceinline__ long tc_site_at(long base, int q, int Lx)
     return base + x;
 }
 
-// Gather group gg (warps 5 + 4 gg .. 8 + 4 gg) fills the slots f with f % 2 == gg.
-// Per thread the rounds wr = warp + 4 k: lane bits 0..2 give the rhs vv & 7 and
-// bits 3..4 the rest index r & 3, so the 32 stores of a warp fall on 32
-// different banks.
+// Gatherers (warps 5-12): the fills of a row are position -1, then the pairs
+// (0, 1), (2, 3), ..., and what is left; lane bit 0 picks the position of the
+// pair, bits 1..3 the rhs vv & 7 and bit 4 the rest index r & 1, rounds
+// wr = warp + 8 k the rest (vv / 8 = wr & 1, r / 2 = wr / 2).
 template <typename T>
-__device__ void tc_gather_role(const ApplyArgs& a, int nvb, unsigned char* As, uint32_t bars, volatile int* abort,
-                               int gg, int gwarp, int lane)
+__device__ void tc_gather_role(const ApplyArgs& a, int nvb, uint32_t As, uint32_t bars, volatile int* abort, int gwarp,
+                               int lane)
 {
     const int Lx = a.g.L[0];
     const long nitems = (a.nsites / Lx) * (long)nvb;
+    const size_t nblk = nblk_of((size_t)a.g.vol);
+    const int po = lane & 1;
     int g_r[TC_GPT], g_vv[TC_GPT];
+    uint32_t g_sb[TC_GPT][3];   // slot offset of (spin 0, rhs vv) at the K of colour c
 #pragma unroll
     for (int k = 0; k < TC_GPT; ++k) {
-        const int wr = gwarp + 4 * k;
-        g_r[k] = wr < TC_GROUNDS ? 4 * (wr >> 1) + (lane >> 3) : 27;   // 27: none
-        g_vv[k] = (lane & 7) + 8 * (wr & 1);
+        const int wr = gwarp + 8 * k;
+        g_r[k] = wr < TC_GROUNDS ? 2 * (wr >> 1) + (lane >> 4) : 27;   // 27: none
+        g_vv[k] = ((lane >> 1) & 7) + 8 * (wr & 1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) g_sb[k][c] = tc_off(g_vv[k], 6 * (g_r[k] < 27 ? g_r[k] : 0) + 2 * c);
     }
-    long f = 0;
+    long f0 = 0;
     bool ok = true;
-    for (long item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+    for (long item = blockIdx.x; item < nitems && ok; item += gridDim.x, f0 += Lx + 2) {
         const TcRow R = tc_row(a, item, nvb);
         long fwd[4], bwd[4];
         int xc[4];
         site_offsets(a.g, R.base, fwd, bwd, xc);
         long g_off[TC_GPT];
+        size_t g_v[TC_GPT];
         bool g_on[TC_GPT];
 #pragma unroll
         for (int k = 0; k < TC_GPT; ++k) {
@@ -264,43 +316,51 @@ __device__ void tc_gather_role(const ApplyArgs& a, int nvb, unsigned char* As, u
             g_off[k] = (dy > 0 ? fwd[1] : (dy < 0 ? bwd[1] : 0)) + (dz > 0 ? fwd[2] : (dz < 0 ? bwd[2] : 0)) +
                        (dt > 0 ? fwd[3] : (dt < 0 ? bwd[3] : 0));
             g_on[k] = r < 27 && R.vb0 + g_vv[k] < a.Nv;
+            g_v[k] = (size_t)(R.vb0 + g_vv[k]) * nblk;
         }
-        for (int q = -1; q <= Lx; ++q, ++f) {
-            if ((int)(f & 1) != gg) continue;
-            const long sq = tc_site_at(R.base, q, Lx);
+        for (int p = -1; p <= Lx && ok;) {
+            const int np = (p >= 0 && p + 1 <= Lx) ? 2 : 1;   // positions in this fill
+            const bool lane_on = po < np;
+            const long sq = tc_site_at(R.base, p + po, Lx);
             uint4 w[TC_GPT][3];
 #pragma unroll
             for (int k = 0; k < TC_GPT; ++k) {
-                if (!g_on[k]) continue;
+                if (!(g_on[k] && lane_on)) continue;
                 const long nb = sq + g_off[k];
-#pragma unroll
-                for (int kk = 0; kk < 3; ++kk)
-                    w[k][kk] = ld_ro(reinterpret_cast<const uint4*>(a.in) + blk_index(a.g.vol, 3, R.vb0 + g_vv[k], kk, nb));
+                const uint4* q = reinterpret_cast<const uint4*>(a.in) + (g_v[k] + (size_t)(nb >> 5)) * 96 + (nb & 31);
+                w[k][0] = ld_ro(q);
+                w[k][1] = ld_ro(q + 32);
+                w[k][2] = ld_ro(q + 64);
             }
-            const int slot = (int)(f % TC_NS);
-            if (f >= TC_NS && !tc_wait(bars + 8u * (TC_BAR_EA + slot), (uint32_t)((f / TC_NS - 1) & 1), abort)) {
-                ok = false;
-                break;
-            }
-            unsigned char* S = As + (uint32_t)slot * TC_ASLOT;
+            const long F = f0 + p + 1;   // fill of position p
+            for (int j = 0; j < np && ok; ++j)
+                if (F + j >= TC_NS)
+                    ok = tc_wait(bars + 8u * (TC_BAR_EA + (int)((F + j) % TC_NS)), (uint32_t)(((F + j) / TC_NS - 1) & 1), abort);
+            if (!ok) break;
+            const uint32_t S = As + (uint32_t)((F + po) % TC_NS) * TC_ASLOT;
 #pragma unroll
             for (int k = 0; k < TC_GPT; ++k) {
-                if (!g_on[k]) continue;
+                if (!(g_on[k] && lane_on)) continue;
                 const uint32_t wv[12] = {w[k][0].x, w[k][0].y, w[k][0].z, w[k][0].w, w[k][1].x, w[k][1].y,
                                          w[k][1].z, w[k][1].w, w[k][2].x, w[k][2].y, w[k][2].z, w[k][2].w};
 #pragma unroll
-                for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        *reinterpret_cast<uint32_t*>(S + tc_off(sp * TC_VB + g_vv[k], 6 * g_r[k] + 2 * c)) = wv[3 * sp + c];
+                for (int c = 0; c < 3; ++c) {
+                    // rows spin * 16 + vv: 2 spin 8-row groups further down
+                    const uint32_t at = S + g_sb[k][c];
+                    tc_sts32<0>(at, wv[c]);
+                    tc_sts32<2 * TC_SBO>(at, wv[3 + c]);
+                    tc_sts32<4 * TC_SBO>(at, wv[6 + c]);
+                    tc_sts32<6 * TC_SBO>(at, wv[9 + c]);
+                }
             }
             tc_fence_async();
-            tc_arrive(bars + 8u * (TC_BAR_FA + slot));
+            for (int j = 0; j < np; ++j) tc_arrive(bars + 8u * (TC_BAR_FA + (int)((F + j) % TC_NS)));
+            p += np;
         }
     }
     // tail: the last releases of the slots arrive before the CTA may exit
-    if (ok && gg == 0) {
-        for (long g = f - TC_NS; g < f; ++g)
+    if (ok && gwarp == 0 && lane == 0) {
+        for (long g = f0 - TC_NS; g < f0; ++g)
             if (g >= 0 && !tc_wait(bars + 8u * (TC_BAR_EA + (int)(g % TC_NS)), (uint32_t)((g / TC_NS) & 1), abort)) break;
     }
 }
@@ -320,114 +380,101 @@ __device__ __forceinline__ uint32_t tc_b_count(int x, int g, int Lx)
 // three consecutive words (colours c' = 0, 1, 2 of one direction) of one row of
 // a B block: 6 r + 2 c' are element offsets along K, so for even r the first two
 // words share an aligned 8-byte pair, for odd r the last two
-__device__ __forceinline__ void tc_st3(unsigned char* p, uint32_t ka, uint32_t kb, bool odd, uint32_t w0, uint32_t w1,
+__device__ __forceinline__ void tc_st3(uint32_t at, uint32_t ka, uint32_t kb, bool odd, uint32_t w0, uint32_t w1,
                                        uint32_t w2)
 {
     if (!odd) {
-        *reinterpret_cast<uint2*>(p + ka) = make_uint2(w0, w1);
-        *reinterpret_cast<uint32_t*>(p + kb) = w2;
+        tc_sts64(at + ka, w0, w1);
+        tc_sts32(at + kb, w2);
     } else {
-        *reinterpret_cast<uint32_t*>(p + ka) = w0;
-        *reinterpret_cast<uint2*>(p + kb) = make_uint2(w1, w2);
+        tc_sts32(at + ka, w0);
+        tc_sts64(at + kb, w1, w2);
     }
 }
 
-// B builders (warps 13-20): thread t < 240 owns output row n0 = t % 6 (colour
-// n0 / 2, re/im n0 % 2) of the directions t / 6 and t / 6 + 40, whose W rows it
-// reads from the site-major copy (a warp's loads for a site fall on two lines).  Site x's block
-// for d_x = g - 1 goes to sub-block 2 - g of the entry of fill f0 + x + g.
-// Only the classes that do not vanish for a direction are written, the rho
-// classes as one rounded product with the sign bits of both halves flipped
-// where C_{1+mu} < 0 (rounding to nearest is odd in its argument).
+// B builders (warps 13-20): thread t < 240 owns direction t / 3 (order of
+// c_tc_dirs) and colour row c = t % 3, both its re and im rows; it reads the
+// three words W_d(x)[c][c'] from the site-major copy (a warp's loads for a
+// site are about 100 consecutive words).  Site x's block for d_x = g - 1 goes
+// to sub-block 2 - g of the entry of fill f0 + x + g.  Only the classes that do
+// not vanish for the direction are written, the rho classes as one product
+// with the sign bits of both halves flipped where C_{1+mu} < 0 (rounding to
+// nearest is odd in its argument).
 template <typename T, bool DAG>
-__device__ void tc_b_role(const ApplyArgs& a, int nvb, unsigned char* Bs, uint32_t bars, volatile int* abort, int btid)
+__device__ void tc_b_role(const ApplyArgs& a, int nvb, uint32_t Bs, uint32_t bars, volatile int* abort, int btid)
 {
     const int Lx = a.g.L[0];
     const long nitems = (a.nsites / Lx) * (long)nvb;
     const bool on = btid < 240;
-    const int n0 = btid % 6, d0 = on ? btid / 6 : 0;
-    uint32_t rowoff[5];
+    const int d = on ? btid / 3 : 0, c = btid % 3;
+    const TcDir D = c_tc_dirs[d];
+    const int g_own = D.g, nz = D.nz, neg = DAG ? (D.neg ^ 0xF) : D.neg;
+    const bool odd = D.r & 1;
+    const uint32_t sub = (uint32_t)(2 - D.g) * TC_BBLK;
+    const uint32_t ka = sub + tc_off(0, 6 * D.r), kb = sub + tc_off(0, odd ? 6 * D.r + 2 : 6 * D.r + 4);
+    const uint32_t c0x2 = pack2(cx<float>{D.c0, D.c0}, (T*)nullptr);
+    const uint32_t rhox2 = pack2(cx<float>{D.rho, D.rho}, (T*)nullptr);
+    uint32_t rowoff[2][5];   // rows 6 j + 2 c + ri
 #pragma unroll
-    for (int j = 0; j < 5; ++j) rowoff[j] = tc_off(n0 + 6 * j, 0);
-    int u_w[2];           // W element (direction, row n0 / 2, column 0) within a site
-    uint32_t u_ka[2], u_kb[2];
-    int u_bits[2];        // g | odd r << 2 | nz << 3 | neg << 7
-    float u_c0[2], u_rho[2];
+    for (int ri = 0; ri < 2; ++ri)
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int d = d0 + 40 * k;
-        const TcDir D = c_tc_dirs[d];
-        const int neg = DAG ? (D.neg ^ 0xF) : D.neg;
-        const uint32_t sub = (uint32_t)(2 - D.g) * TC_BBLK;
-        const int kk = 6 * D.r;
-        const bool odd = D.r & 1;
-        u_ka[k] = sub + tc_off(0, kk);
-        u_kb[k] = sub + tc_off(0, odd ? kk + 2 : kk + 4);
-        u_bits[k] = D.g | ((int)odd << 2) | (D.nz << 3) | (neg << 7);
-        u_c0[k] = D.c0;
-        u_rho[k] = D.rho;
-        u_w[k] = 9 * d + 3 * (n0 >> 1);
-    }
-    auto load = [&](long s, uint32_t (&w)[2][3]) {   // W_d(x) row n0 / 2 of both directions
+        for (int j = 0; j < 5; ++j) rowoff[ri][j] = tc_off(6 * j + 2 * c + ri, 0);
+    const int woff = 9 * d + 3 * c;
+    auto load = [&](long s, uint32_t (&w)[3]) {
         if (!on) return;
-        const uint32_t* W = reinterpret_cast<const uint32_t*>(a.links) + (size_t)s * 720;
-#pragma unroll
-        for (int k = 0; k < 2; ++k)
-#pragma unroll
-            for (int cp = 0; cp < 3; ++cp) w[k][cp] = ld_ro(W + u_w[k] + cp);
+        const uint32_t* W = reinterpret_cast<const uint32_t*>(a.links) + (size_t)s * 720 + woff;
+        w[0] = ld_ro(W);
+        w[1] = ld_ro(W + 1);
+        w[2] = ld_ro(W + 2);
     };
-    const int ri = n0 & 1;
-    uint32_t wn[2][3] = {{0u, 0u, 0u}, {0u, 0u, 0u}};
+    uint32_t wn[3] = {0u, 0u, 0u};
     if ((long)blockIdx.x < nitems) load(tc_row(a, blockIdx.x, nvb).base, wn);
     long f0 = 0;
     bool ok = true;
     for (long item = blockIdx.x; item < nitems && ok; item += gridDim.x, f0 += Lx + 2) {
         const TcRow R = tc_row(a, item, nvb);
         for (int x = 0; x < Lx; ++x) {
-            uint32_t wc[2][3];
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-#pragma unroll
-                for (int cp = 0; cp < 3; ++cp) wc[k][cp] = wn[k][cp];
+            const uint32_t wc[3] = {wn[0], wn[1], wn[2]};
             // the links of the next site, in flight while this one is built
             if (x + 1 < Lx) load(R.base + x + 1, wn);
             else if (item + (long)gridDim.x < nitems) load(tc_row(a, item + gridDim.x, nvb).base, wn);
-            unsigned char* eb[3];
+            // the blocks for g = 0, 1, 2 in turn, each after its entry is free
+            // (the entries of g = 0, 1 were already free for site x - 1)
 #pragma unroll
             for (int g = 0; g < 3; ++g) {
                 const long F = f0 + x + g;
-                if (ok && F >= TC_NR)
-                    ok = tc_wait(bars + 8u * (TC_BAR_EB + (int)(F % TC_NR)), (uint32_t)((F / TC_NR - 1) & 1), abort);
-                eb[g] = Bs + (uint32_t)(F % TC_NR) * TC_BENT;
-            }
-            if (!ok) break;
-            if (on) {
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const int bits = u_bits[k], g = bits & 3;
-                    unsigned char* base = g == 0 ? eb[0] : (g == 1 ? eb[1] : eb[2]);
-                    uint32_t p0[3], p1[3];
+                if ((g == 2 || x == 0) && F >= TC_NR &&
+                    !tc_wait(bars + 8u * (TC_BAR_EB + (int)(F % TC_NR)), (uint32_t)((F / TC_NR - 1) & 1), abort)) {
+                    ok = false;
+                    break;
+                }
+                if (on && g == g_own) {
+                    const uint32_t base = Bs + (uint32_t)(F % TC_NR) * TC_BENT;
+                    uint32_t p0[2][3], p1[2][3];
 #pragma unroll
                     for (int cp = 0; cp < 3; ++cp) {
-                        const cx<float> wv = unpack2(wc[k][cp], (T*)nullptr);
-                        const cx<float> e = ri ? cx<float>{wv.im, wv.re} : cx<float>{wv.re, -wv.im};
-                        p0[cp] = pack2(cx<float>{u_c0[k] * e.re, u_c0[k] * e.im}, (T*)nullptr);
-                        p1[cp] = pack2(cx<float>{u_rho[k] * e.re, u_rho[k] * e.im}, (T*)nullptr);
+                        const uint32_t e0 = wc[cp] ^ 0x80000000u;          // (re, -im)
+                        const uint32_t e1 = __byte_perm(wc[cp], 0, 0x1032); // (im, re)
+                        p0[0][cp] = tc_mul2(e0, c0x2, (T*)nullptr);
+                        p0[1][cp] = tc_mul2(e1, c0x2, (T*)nullptr);
+                        p1[0][cp] = tc_mul2(e0, rhox2, (T*)nullptr);
+                        p1[1][cp] = tc_mul2(e1, rhox2, (T*)nullptr);
                     }
-                    const bool odd = (bits >> 2) & 1;
-                    tc_st3(base + rowoff[0], u_ka[k], u_kb[k], odd, p0[0], p0[1], p0[2]);
 #pragma unroll
-                    for (int mu = 0; mu < 4; ++mu) {
-                        if (!((bits >> (3 + mu)) & 1)) continue;
-                        const uint32_t m = ((bits >> (7 + mu)) & 1) ? 0x80008000u : 0u;
-                        tc_st3(base + rowoff[1 + mu], u_ka[k], u_kb[k], odd, p1[0] ^ m, p1[1] ^ m, p1[2] ^ m);
+                    for (int ri = 0; ri < 2; ++ri) {
+                        tc_st3(base + rowoff[ri][0], ka, kb, odd, p0[ri][0], p0[ri][1], p0[ri][2]);
+#pragma unroll
+                        for (int mu = 0; mu < 4; ++mu) {
+                            if (!((nz >> mu) & 1)) continue;
+                            const uint32_t m = ((neg >> mu) & 1) ? 0x80008000u : 0u;
+                            tc_st3(base + rowoff[ri][1 + mu], ka, kb, odd, p1[ri][0] ^ m, p1[ri][1] ^ m, p1[ri][2] ^ m);
+                        }
                     }
+                    tc_fence_async();
                 }
+                tc_arrive_n(bars + 8u * (TC_BAR_FB + (int)(F % TC_NR)), tc_b_count(x, g, Lx));
             }
-            tc_fence_async();
-#pragma unroll
-            for (int g = 0; g < 3; ++g)
-                tc_arrive_n(bars + 8u * (TC_BAR_FB + (int)((f0 + x + g) % TC_NR)), tc_b_count(x, g, Lx));
+            if (!ok) break;
         }
     }
     // tail: the last releases of the entries arrive before the CTA may exit
@@ -500,42 +547,63 @@ __device__ void tc_mma_role(const ApplyArgs& a, int nvb, uint32_t a_base, uint32
 // through shared memory to the spins that need them, and each (spin, rhs)
 // forms T_0 + sum_mu gamma_mu T_{1+mu} (chiral basis: gamma_1, gamma_2 couple
 // spin s to 3 - s, gamma_3, gamma_4 to s ^ 2), adds the diagonal and stores.
+// psi(x) for the diagonal is loaded one site ahead.
 template <typename T>
-__device__ void tc_epi_role(const ApplyArgs& a, int nvb, float* Ts, uint32_t tmem, uint32_t bars, volatile int* abort,
+__device__ void tc_epi_role(const ApplyArgs& a, int nvb, uint32_t Ts, uint32_t tmem, uint32_t bars, volatile int* abort,
                             int tid)
 {
+    static_assert(Store<T>::CPV == 4, "16-bit fields");
     const int Lx = a.g.L[0];
     const long nitems = (a.nsites / Lx) * (long)nvb;
+    const size_t nblk = nblk_of((size_t)a.g.vol);
     const int sp = tid >> 5, lane = tid & 31, vv = lane & 15;
+    const bool lane_on = lane < TC_VB;
     const uint32_t zero = 0u;
     // factors of the couplings: gamma_1 (-i / +i), gamma_2 (-1 / +1), gamma_3 (-i / +i)
     const float s1 = sp < 2 ? -1.f : 1.f;
     const float s2 = (sp == 0 || sp == 3) ? -1.f : 1.f;
-    const int sa = 3 - sp, sb = sp ^ 2;
-    // psi(x) of the next site for the diagonal, loaded one site ahead
-    auto load_own = [&](const TcRow& R, int x, uint32_t (&w)[3]) {
-        const int v = R.vb0 + vv;
-        if (lane >= TC_VB || v >= a.Nv) return;
+    // complex 3 sp + c of rhs v at site s: ((v nblk + s / 32) 3 + i / 4) 128 + (s % 32) 4 + i % 4
+    uint32_t ioff[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            w[c] = ld_ro(reinterpret_cast<const uint32_t*>(a.in) + tc_out_index<T>(a.g.vol, v, 3 * sp + c, R.base + x));
+    for (int c = 0; c < 3; ++c) ioff[c] = (uint32_t)(((3 * sp + c) >> 2) * 128 + ((3 * sp + c) & 3));
+    // staged rows: own (written), spin 3 - sp and spin sp ^ 2 (read)
+    const uint32_t t_own = (uint32_t)((sp * TC_VB + vv) * TC_TS * 4);
+    const uint32_t t_a = (uint32_t)(((3 - sp) * TC_VB + vv) * TC_TS * 4);
+    const uint32_t t_b = (uint32_t)(((sp ^ 2) * TC_VB + vv) * TC_TS * 4);
+    const uint32_t* in = reinterpret_cast<const uint32_t*>(a.in);
+    auto site_part = [](long s) { return (size_t)(s >> 5) * 384 + (size_t)(s & 31) * 4; };
+    auto load_own = [&](const TcRow& R, long s, uint32_t (&w)[3]) {
+        const int v = R.vb0 + vv;
+        if (!lane_on || v >= a.Nv) return;
+        const uint32_t* q = in + (size_t)v * nblk * 384 + site_part(s);
+        w[0] = ld_ro(q + ioff[0]);
+        w[1] = ld_ro(q + ioff[1]);
+        w[2] = ld_ro(q + ioff[2]);
     };
     uint32_t own_n[3] = {0u, 0u, 0u};
-    if ((long)blockIdx.x < nitems) load_own(tc_row(a, blockIdx.x, nvb), 0, own_n);
+    if ((long)blockIdx.x < nitems) {
+        const TcRow R0 = tc_row(a, blockIdx.x, nvb);
+        load_own(R0, R0.base, own_n);
+    }
     long i = 0;
     bool ok = true;
     for (long item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
         const TcRow R = tc_row(a, item, nvb);
         const int v = R.vb0 + vv;
-        const float dg = (v < a.Nv) ? (a.diag_vf ? a.diag_vf[v] : (a.diag_v ? (float)a.diag_v[v] : a.diagf)) : 0.f;
+        const bool v_on = lane_on && v < a.Nv;
+        const float dg = v_on ? (a.diag_vf ? a.diag_vf[v] : (a.diag_v ? (float)a.diag_v[v] : a.diagf)) : 0.f;
+        uint32_t* out = reinterpret_cast<uint32_t*>(a.out) + (size_t)(v_on ? v : 0) * nblk * 384;
         for (int x = 0; x < Lx; ++x, ++i) {
             const uint32_t own[3] = {own_n[0], own_n[1], own_n[2]};
-            if (x + 1 < Lx) load_own(R, x + 1, own_n);
-            else if (item + (long)gridDim.x < nitems) load_own(tc_row(a, item + gridDim.x, nvb), 0, own_n);
+            if (x + 1 < Lx) load_own(R, R.base + x + 1, own_n);
+            else if (item + (long)gridDim.x < nitems) {
+                const TcRow Rn = tc_row(a, item + gridDim.x, nvb);
+                load_own(Rn, Rn.base, own_n);
+            }
             const int ac = (int)(i % TC_NACC);
             bool w_ok = tc_wait(bars + 8u * (TC_BAR_FC + ac), (uint32_t)((i / TC_NACC) & 1), abort);
             w_ok = __all_sync(0xffffffffu, w_ok);
-            float* Tb = Ts + (i & 1) * (TC_TBUF / 4);
+            const uint32_t Tb = Ts + (uint32_t)(i & 1) * TC_TBUF;
             uint32_t r[32];
             if (w_ok) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -555,31 +623,31 @@ __device__ void tc_epi_role(const ApplyArgs& a, int nvb, float* Ts, uint32_t tme
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 tc_arrive(bars + 8u * (TC_BAR_EC + ac));
-                if (lane < TC_VB) {
+                if (lane_on) {
 #pragma unroll
-                    for (int n = 6; n < 30; ++n) Tb[(sp * TC_VB + lane) * TC_TS + n - 6] = __uint_as_float(r[n]);
+                    for (int n = 6; n < 30; ++n) tc_stsf(Tb + t_own + 4u * (n - 6), __uint_as_float(r[n]));
                 }
             }
             if (!tc_epi_and(w_ok)) {
                 ok = false;
                 break;
             }
-            if (lane < TC_VB && v < a.Nv) {
-                const long s = R.base + x;
-                const float* ta = Tb + (sa * TC_VB + vv) * TC_TS;
-                const float* tb = Tb + (sb * TC_VB + vv) * TC_TS;
+            if (v_on) {
+                const size_t sp_idx = site_part(R.base + x);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     // T_0[sp] + s1 i T_1[3 - sp] + s2 T_2[3 - sp] + s2 i T_3[sp ^ 2] + T_4[sp ^ 2]
-                    const float t1r = ta[2 * c], t1i = ta[2 * c + 1], t2r = ta[6 + 2 * c], t2i = ta[6 + 2 * c + 1];
-                    const float t3r = tb[12 + 2 * c], t3i = tb[12 + 2 * c + 1], t4r = tb[18 + 2 * c], t4i = tb[18 + 2 * c + 1];
+                    const float t1r = tc_ldsf(Tb + t_a + 8u * c), t1i = tc_ldsf(Tb + t_a + 8u * c + 4);
+                    const float t2r = tc_ldsf(Tb + t_a + 24u + 8u * c), t2i = tc_ldsf(Tb + t_a + 28u + 8u * c);
+                    const float t3r = tc_ldsf(Tb + t_b + 48u + 8u * c), t3i = tc_ldsf(Tb + t_b + 52u + 8u * c);
+                    const float t4r = tc_ldsf(Tb + t_b + 72u + 8u * c), t4i = tc_ldsf(Tb + t_b + 76u + 8u * c);
                     cx<float> o{__uint_as_float(r[2 * c]), __uint_as_float(r[2 * c + 1])};
                     o.re += -s1 * t1i + s2 * t2r - s2 * t3i + t4r;
                     o.im += s1 * t1r + s2 * t2i + s2 * t3r + t4i;
                     const cx<float> pc = unpack2(own[c], (T*)nullptr);
                     o.re = fmaf(dg, pc.re, o.re);
                     o.im = fmaf(dg, pc.im, o.im);
-                    st_one<T>(a.out, tc_out_index<T>(a.g.vol, v, 3 * sp + c, s), o);
+                    st_cs(out + sp_idx + ioff[c], pack2(o, (T*)nullptr));
                 }
             }
         }
@@ -608,7 +676,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_brillouin_tc(ApplyArgs a, int
     }
     if (tid == 0) {
         for (int s = 0; s < TC_NS; ++s) {
-            tc_bar_init(bars + 8u * (TC_BAR_FA + s), 128);   // one gather group
+            tc_bar_init(bars + 8u * (TC_BAR_FA + s), TC_GTHREADS);   // the gatherers
             tc_bar_init(bars + 8u * (TC_BAR_EA + s), 1);     // one commit
         }
         for (int b = 0; b < TC_NR; ++b) {
@@ -640,14 +708,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_brillouin_tc(ApplyArgs a, int
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-    if (warp < TC_EPI_WARPS) tc_epi_role<T>(a, nvb, Ts, tmem, bars, abort, tid);
+    if (warp < TC_EPI_WARPS) tc_epi_role<T>(a, nvb, smem_u32(Ts), tmem, bars, abort, tid);
     else if (warp == TC_MMA_WARP) {
         if (lane == 0) tc_mma_role<T>(a, nvb, smem_u32(As), smem_u32(Bs), tmem, bars, abort);
     } else if (warp < TC_B_WARP0) {
-        const int gw = warp - TC_GATHER_WARP0;
-        tc_gather_role<T>(a, nvb, As, bars, abort, gw >> 2, gw & 3, lane);
+        tc_gather_role<T>(a, nvb, smem_u32(As), bars, abort, warp - TC_GATHER_WARP0, lane);
     } else {
-        tc_b_role<T, DAG>(a, nvb, Bs, bars, abort, tid - TC_B_WARP0 * 32);
+        tc_b_role<T, DAG>(a, nvb, smem_u32(Bs), bars, abort, tid - TC_B_WARP0 * 32);
     }
 
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -671,7 +738,7 @@ cudaError_t tc_go(bool dag, const ApplyArgs& a, cudaStream_t st)
     if (e != cudaSuccess) return e;
     const int nvb = (a.Nv + TC_VB - 1) / TC_VB;
     const long nitems = (a.nsites / a.g.L[0]) * (long)nvb;
-    // one CTA per SM: ~211 KB of shared memory and all 512 tensor-memory columns
+    // one CTA per SM: ~200 KB of shared memory and all 512 tensor-memory columns
     const long grid = std::min<long>(nitems, nsm);
     if (grid <= 0) return cudaSuccess;
     kern<<<(unsigned)grid, TC_THREADS, TC_SMEM, st>>>(a, nvb);
