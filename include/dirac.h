@@ -156,7 +156,7 @@ DIRAC_API dirac_status dirac_apply(dirac_handle* h, void* out, const void* in, d
  *             calling thread; they must not overlap (INVALID_ARG), device
  *             pointers are rejected (INVALID_ARG).
  * Launch shape: the handle's kernel configuration when it is variant 0, 1, 2,
- * 5 or 6 (the ones that can sweep a t-slab), else variant 1 with the same R.
+ * 5, 6 or 7 (the ones that can sweep a t-slab), else variant 1 with the same R.
  * Holds two staging buffers per direction of one slab each (allocated on
  * the first call, kept in the handle) and the handle's apply workspace.
  * Requires dirac_set_links first.  Asynchronous: out is complete when the
@@ -377,7 +377,18 @@ DIRAC_API dirac_status dirac_get_residual_arithmetic(const dirac_handle* h, int*
  *               last by lane exchange: each site's own spinor, loaded once,
  *               serves the diagonal term and both x hops, so two of the nine
  *               spinor loads and one of the eight link loads per site
- *               disappear; 32 or 64 sites per block.
+ *               disappear; 32 or 64 sites per block;
+ *            7: (Brillouin, BF16/FP16 storage, R = 1, block = 128) the sweep on
+ *               the tensor cores (tcgen05.mma, 16-bit operands, FP32
+ *               accumulation in tensor memory): per site the colour sums
+ *               T_j = sum_d C_j(d) W_d(x) psi(x + d) of the five coefficient
+ *               classes (C_0 = -lambda_k / 2, C_{1+mu} = rho_k d_mu) are one
+ *               real matrix product, the spin matrices and the diagonal are
+ *               applied afterwards; one CTA per SM walks x-rows (about 200 KB
+ *               of shared memory, all 512 tensor-memory columns).  The C_j W
+ *               are rounded to the storage type (rho_k first rounded to it),
+ *               so results differ from variants 0 and 1 by a few units of
+ *               the storage rounding.  Selecting it selects link format 1.
  * UNSUPPORTED for other values. */
 DIRAC_API dirac_status dirac_set_kernel_config(dirac_handle* h, int R, int block, int variant);
 
@@ -413,10 +424,11 @@ DIRAC_API dirac_status dirac_get_site_order(const dirac_handle* h, int* tchunk);
  *          (W_{-dir}(x) precomputed, copied without rounding): twice the W
  *          bytes, local reads only.
  * Format 1 is read by the launch variants that support it (Wilson and
- * staggered: variants 1 and 6; Brillouin: variants 0 and 1) in the apply
+ * staggered: variants 1 and 6; Brillouin: variants 0, 1 and 7) in the apply
  * and in the whole-lattice inner sweeps of the solvers; other variants and
- * the even-odd sweeps read the plain links.  The
- * format-1 copy (Wilson/staggered: 4 x 6 complex per site; Brillouin: 80 x 9)
+ * the even-odd sweeps read the plain links; variant 7 reads only format 1.
+ * The format-1 copy (Wilson/staggered: 4 x 6 complex per site; Brillouin:
+ * 80 x 9, and for BF16/FP16 a second, site-major copy that variant 7 reads)
  * is held by the handle and rebuilt by dirac_set_links; links that fail the
  * check there switch the handle back to format 0 (dirac_get_link_format
  * reports it).  Called before dirac_set_links, fmt 1 is recorded and built
@@ -435,16 +447,17 @@ DIRAC_API dirac_status dirac_get_link_format(const dirac_handle* h, int* fmt);
  * variable DIRAC_TUNE_CACHE naming a writable file, results are cached per
  * (operator, precision, lattice, Nv, GPU name) and reused unless force != 0.
  * It also times link format 1 (dirac_set_link_format) on the shapes that read
- * it, when the links allow it, and keeps the faster format.
+ * it (variant 7 only there), when the links allow it, and keeps the faster
+ * format.
  * Synchronous.  R, block, variant, ms (host, may be NULL) receive the choice
  * and its median time per sweep in milliseconds (from the cache when reused). */
 DIRAC_API dirac_status dirac_autotune(dirac_handle* h, int force, int* R, int* block, int* variant, double* ms);
 
 /* Wait for the handle's stream and report kernel-side failures: returns
  * DIRAC_TIMEOUT (and clears the record) if a kernel recorded that a bounded
- * device-side wait ran out since the last call (none of the current sweeps
- * waits on other threads' data), else DIRAC_OK or the CUDA error of the
- * stream. */
+ * device-side wait ran out since the last call (the tensor-core sweep,
+ * variant 7, waits on its own CTA's barriers for at most half a second per
+ * wait), else DIRAC_OK or the CUDA error of the stream. */
 DIRAC_API dirac_status dirac_sync(dirac_handle* h);
 
 /* One-line description of the last error on h (or of the last failed
