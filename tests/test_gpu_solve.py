@@ -199,6 +199,41 @@ def test_brillouin_split_inner_fields(dg, prec):
         assert oracle_residual("brillouin", V, xi, bi, m).max() <= 1e-10
 
 
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+def test_solve_tensor_core_config(dg, prec):
+    """Solves of a 16-bit Brillouin handle configured for the tensor-core
+    sweep (launch variant 7): with split inner fields and with every inner
+    field in 16 bits (whose whole-lattice inner sweeps are the tensor-core
+    sweep, captured in the solver graph), then after new links (the
+    site-major W copy the sweep reads is rebuilt in place), and a batched
+    solve (per-column diagonal); all certified by the oracle."""
+    L, Nv = (4, 4, 2, 6), 3
+    V = links_for(prec, synth.gauge_links(L, 3, "near_identity", 390))
+    b = synth.spinor(L, Nv, 4, 3, 391)
+    D = dg.Dirac("brillouin", L, Nv, 0.06, prec)
+    D.set_links(torch.from_numpy(V.astype(np.complex64)).cuda())
+    D.set_kernel_config(1, 128, 7)
+    assert D.link_format() == 1
+    for mode in (1, 0):
+        D.set_inner_fields(mode)
+        x, res, st, status = D.solve(torch.from_numpy(b).cuda(), tol=1e-10, max_outer=80, max_inner=3000)
+        assert status == dg.OK, (mode, res, st)
+        assert oracle_residual("brillouin", V, x.cpu().numpy(), b, 0.06).max() <= 1e-10, mode
+    V2 = links_for(prec, synth.gauge_links(L, 3, "near_identity", 392))
+    D.set_links(torch.from_numpy(V2.astype(np.complex64)).cuda())
+    x, res, st, status = D.solve(torch.from_numpy(b).cuda(), tol=1e-10, max_outer=80, max_inner=3000)
+    assert status == dg.OK, (res, st)
+    assert oracle_residual("brillouin", V2, x.cpu().numpy(), b, 0.06).max() <= 1e-10
+    D.sync()
+    D.close()
+    masses = [0.05, 0.1, 0.2]
+    V, bs, xs, res, sys_stats, tot, status = _batched_case(dg, "brillouin", (4, 4, 2, 4), [1, 3, 2], masses, prec,
+                                                          4, 393, inner_fields=0, cfg=(1, 128, 7))
+    assert status == dg.OK, (sys_stats, tot)
+    for bi, xi, m in zip(bs, xs, masses):
+        assert oracle_residual("brillouin", V, xi, bi, m).max() <= 1e-10
+
+
 @pytest.mark.parametrize("op,masses", [("wilson", [0.120, 0.1225, 0.124]), ("brillouin", [0.05, 0.1, 0.2])])
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
 def test_solve_link_format_1(dg, op, masses, prec):
@@ -286,13 +321,15 @@ def test_solve_not_converged_status(dg):
     D.close()
 
 
-def _batched_case(dg, op, L, nv_list, masses, prec, window, seed, tol=1e-10, precond=1, inner_fields=1):
+def _batched_case(dg, op, L, nv_list, masses, prec, window, seed, tol=1e-10, precond=1, inner_fields=1, cfg=None):
     V = links_for(prec, synth.gauge_links(L, 3, "near_identity", seed))
     bs = [synth.spinor(L, nv, NS[op], 3, seed + 1 + i) for i, nv in enumerate(nv_list)]
     D = dg.Dirac(op, L, window, masses[0], prec)
     D.set_preconditioner(precond)
     D.set_inner_fields(inner_fields)
     D.set_links(torch.from_numpy(V.astype(np.complex64 if prec != "f64" else np.complex128)).cuda())
+    if cfg:
+        D.set_kernel_config(*cfg)
     xs, res, sys_stats, tot, status = D.solve_batched([torch.from_numpy(b).cuda() for b in bs], masses, tol=tol,
                                                       max_outer=40, max_inner=4000)
     D.close()
