@@ -764,6 +764,9 @@ def main():
         extra["brillouin_24x24x24x48_nv12_f32"] = sweep_rate(dg, torch, bw, 20, 3, compare_formats=True)
         extra["brillouin_24x24x24x48_nv12_bf16"] = sweep_rate(dg, torch, dict(bw, prec="bf16"), 20, 3,
                                                               compare_formats=True)
+        # the same BF16 sweep on the tensor cores (launch variant 7), which the tuner times but does not keep
+        extra["brillouin_24x24x24x48_nv12_bf16_tensor_cores"] = sweep_rate(dg, torch, dict(bw, prec="bf16"), 20, 3,
+                                                                           kernel=(1, 128, 7))
         extra["wilson_32x32x32x32_nv12_bf16"] = sweep_rate(dg, torch, dict(WORKLOAD, prec="bf16"), 200, 5,
                                                            compare_formats=True)
         # the paper's own lattice (non-power-of-two extents) and the FP64 sweeps
