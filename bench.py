@@ -266,7 +266,9 @@ def solve_times(dg, torch, L=(24, 24, 24, 48), Nv=12, m0=0.05, precs=("f32", "bf
         dt = time.perf_counter() - t0
         out[prec] = {"seconds": dt, "status": int(status), "max_rel_residual": float(res.max()),
                      "outer": st["outer_iterations"], "inner": st["inner_iterations"],
-                     "sweeps": st["sweeps"], "fp64_sweeps": st["fp64_sweeps"], "kernel": list(D.kernel_config())}
+                     "sweeps": st["sweeps"], "fp64_sweeps": st["fp64_sweeps"], "kernel": list(D.kernel_config()),
+                     "df_residual": st.get("df_residual"), "split_fields": st.get("split_fields"),
+                     "even_odd": st.get("even_odd")}
         D.close()
         del x
         torch.cuda.empty_cache()
