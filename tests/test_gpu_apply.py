@@ -434,11 +434,12 @@ def test_brillouin_80_stored_links(dg, prec):
 def test_brillouin_tensor_cores(dg, prec):
     """Variant 7, the Brillouin sweep on the tensor cores (tcgen05.mma, 16-bit
     operands, FP32 accumulation): parity with the oracle at the storage
-    rounding bound, D and D^+, ragged volumes, a partial block of 16
-    right-hand sides and two blocks, x-rows of length 2 to 4 (the ring of
+    rounding bound, D and D^+, ragged volumes, partial and full blocks of 16
+    right-hand sides, one and two blocks, x-rows of length 2 to 4 (the ring of
     A slots wraps around), canonical and internal fields, and the
     host-buffer apply (t-slabs)."""
-    for L, Nv in (((4, 6, 2, 5), 5), ((4, 4, 4, 4), 12), ((3, 4, 2, 4), 20), ((2, 3, 4, 3), 7)):
+    for L, Nv in (((4, 6, 2, 5), 5), ((4, 4, 4, 4), 12), ((3, 4, 2, 4), 20), ((2, 3, 4, 3), 7), ((4, 4, 2, 4), 16),
+                  ((3, 2, 2, 3), 32)):
         V, psi = inputs("brillouin", L, Nv, prec, 320, kind="near_identity")
         pr = synth.round_to(psi, prec)     # W is built in FP64 from the FP32 links, rounded once
         D = dg.Dirac("brillouin", L, Nv, 0.07, prec)
